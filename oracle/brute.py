@@ -1,0 +1,135 @@
+"""Literal MPIW by enumeration of every index vector k in {1..K}^n.
+
+TEST INFRASTRUCTURE ONLY.  This is Eq. (mp_iw) of the paper written out with
+no factorisation at all: for one model instance with n latents (every plate
+element of every level is its own latent with its own index k_i),
+
+    log r_k  = sum_i [ log p(z_i^{k_i} | z_pa(i)^{k_pa(i)}) + log p(x_i | z_i^{k_i})
+                       - log q_i(z_i^{k_i}) ]                          (Eq. rmp)
+    P_MP     = K^-n sum_k r_k                                          (Eq. Prmp)
+    w_i[k]   = sum_{k : k_i = k} r_k / sum_k r_k                       (Eq. mmp, m = 1[k_i = k])
+    m_i      = sum_k w_i[k] T(z_i^k)
+
+All densities come from scipy.stats / scipy.special (library routines that
+share nothing with either the oracle in C or the CUDA path).  Only feasible
+for n log2 K up to ~20.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+from scipy import special, stats
+
+Q_GAUSS, Q_GAMMA, Q_BETA = 0, 1, 2
+
+
+def _log_prior(lv, z, zp):
+    if lv.prior == 0:
+        return stats.norm.logpdf(z, 0.0, math.sqrt(lv.prior_a)).sum()
+    if lv.prior == 1:
+        return stats.norm.logpdf(z, zp, math.sqrt(lv.prior_a)).sum()
+    if lv.prior == 2:
+        D = lv.dim
+        return stats.norm.logpdf(z, zp[:D], np.exp(0.5 * zp[D:])).sum()
+    if lv.prior == 3:
+        return stats.gamma.logpdf(z, lv.prior_a, scale=1.0 / lv.prior_b).sum()
+    return stats.beta.logpdf(z, lv.prior_a, lv.prior_b).sum()
+
+
+def _log_lik(lv, e, z):
+    if lv.lik == 0:
+        return 0.0
+    x = np.asarray(lv.x[e], np.float64)
+    y = np.asarray(lv.y[e], np.float64)
+    s = x @ z
+    if lv.lik == 1:
+        return stats.norm.logpdf(y, s, math.sqrt(lv.lik_var)).sum()
+    if lv.lik == 2:
+        return (y * special.log_expit(s) + (1 - y) * special.log_expit(-s)).sum()
+    if lv.lik == 3:
+        return stats.poisson.logpmf(y, np.exp(s)).sum()
+    if lv.lik == 4:
+        return stats.poisson.logpmf(y, z[0]).sum()
+    return stats.bernoulli.logpmf(y, z[0]).sum()
+
+
+def _log_q(lv, qe, z):
+    a, b = np.asarray(qe[0], np.float64), np.asarray(qe[1], np.float64)
+    if lv.qfam == Q_GAUSS:
+        return stats.norm.logpdf(z, a, b).sum()
+    if lv.qfam == Q_GAMMA:
+        return stats.gamma.logpdf(z, a, scale=1.0 / b).sum()
+    return stats.beta.logpdf(z, a, b).sum()
+
+
+def _T(lv, z):
+    if lv.qfam == Q_GAUSS:
+        return np.stack([z, z * z])
+    if lv.qfam == Q_GAMMA:
+        return np.stack([z, np.log(z)])
+    return np.stack([np.log(z), np.log1p(-z)])
+
+
+def instance_latents(model, inst: int):
+    """(level, element) of every latent of one instance, parents before children."""
+    lat = [(0, inst)]
+    frontier = [inst]
+    for l in range(1, len(model.levels)):
+        par = model.levels[l].parent
+        nxt = [int(e) for e in np.nonzero(np.isin(par, frontier))[0]]
+        lat += [(l, e) for e in nxt]
+        frontier = nxt
+    return lat
+
+
+def estep_instance(model, q, z, K: int, inst: int = 0) -> dict:
+    """Enumerate all K^n index vectors of one instance.
+
+    q: per level [n, 2, dim] proposal parameters; z: per level [n, K, dim]
+    samples (the draws themselves, so the check does not depend on how they
+    were produced).  Returns log_pmp, and w / mom keyed by (level, element).
+    """
+    lat = instance_latents(model, inst)
+    idx = {le: i for i, le in enumerate(lat)}
+    n = len(lat)
+    unary = np.zeros((n, K))
+    pair = {}
+    for i, (l, e) in enumerate(lat):
+        lv = model.levels[l]
+        for k in range(K):
+            zk = np.asarray(z[l][e, k], np.float64)
+            u = _log_lik(lv, e, zk) - _log_q(lv, q[l][e], zk)
+            if l == 0:
+                u += _log_prior(lv, zk, None)
+            unary[i, k] = u
+        if l > 0:
+            p = int(lv.parent[e])
+            pi = idx[(l - 1, p)]
+            f = np.zeros((K, K))
+            for kp in range(K):
+                zp = np.asarray(z[l - 1][p, kp], np.float64)
+                for k in range(K):
+                    f[kp, k] = _log_prior(lv, np.asarray(z[l][e, k], np.float64), zp)
+            pair[i] = (pi, f)
+    logr = []
+    combos = list(itertools.product(range(K), repeat=n))
+    for kv in combos:
+        s = sum(unary[i, kv[i]] for i in range(n))
+        s += sum(f[kv[pi], kv[i]] for i, (pi, f) in pair.items())
+        logr.append(s)
+    logr = np.array(logr)
+    mx = logr.max()
+    terms = np.exp(logr - mx)
+    tot = math.fsum(terms)
+    log_pmp = mx + math.log(tot) - n * math.log(K)
+    combos = np.array(combos)
+    w, mom = {}, {}
+    for i, (l, e) in enumerate(lat):
+        wi = np.array([math.fsum(terms[combos[:, i] == k]) for k in range(K)]) / tot
+        w[(l, e)] = wi
+        lv = model.levels[l]
+        T = _T(lv, np.asarray(z[l][e], np.float64))      # [2, K, dim]
+        mom[(l, e)] = np.einsum("k,skd->sd", wi, T)
+    return {"log_pmp": log_pmp, "w": w, "mom": mom, "n": n}
