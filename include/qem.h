@@ -1,0 +1,202 @@
+/*
+ * qem.h -- C ABI of libqem: the QEM E-step (massively parallel importance
+ * weighting over a plated hierarchical model) and M-step on one GB300 GPU.
+ *
+ * Method: arXiv 2503.08264, "Massively Parallel Expectation Maximization For
+ * Approximate Posteriors".  Every entry point below cites the passage that
+ * defines the operation it performs.
+ *
+ * Conventions shared by every call
+ *  - Plain pointers and sizes only.  A pointer documented DEVICE must point to
+ *    memory of the CUDA device that was current when the plan was created; a
+ *    pointer documented HOST must point to host memory.  The caller owns every
+ *    buffer it passes; the plan owns only its internal workspace.
+ *  - All device work is enqueued on the plan's stream (qem_plan_opts.stream,
+ *    or the legacy default stream when NULL).  Calls are asynchronous unless
+ *    documented otherwise; inputs must stay valid until the stream reaches
+ *    the call's work.
+ *  - Errors are returned as qem_status; nothing is thrown across the ABI and
+ *    nothing aborts.  Argument errors are detected on the host before any
+ *    launch.  Asynchronous CUDA faults surface as QEM_ERR_CUDA at a later
+ *    call; numerical failures (non-finite log P_MP) as QEM_ERR_NUMERIC from
+ *    qem_log_pmp; an expired bounded device wait as QEM_ERR_TIMEOUT.
+ *  - Flat, level-major buffers.  A model has L levels; level l has n_l plate
+ *    elements of latent dimension D_l.  A "per-element" buffer of E values per
+ *    element stores level 0's n_0*E values, then level 1's, and so on;
+ *    qem_layout() returns each level's offset (in elements of the buffer's
+ *    type).
+ *      q_params     float  [n_l][2][D_l]       proposal parameters
+ *                                               Gaussian (loc, scale), Gamma (shape, rate), Beta (a, b)
+ *      moments      double [n_l][2][D_l]       E_w[T(z)]: Gaussian (z, z^2), Gamma (z, log z),
+ *                                               Beta (log z, log(1-z))
+ *      mean_params  double [n_l][2][D_l]       EMA state m_t, same statistics
+ *      eps          float  [n_l][K][nps_l]     supplied noise; nps = D (Gaussian),
+ *                                               D*(2*QEM_GAMMA_TRIES+1) (Gamma), twice that (Beta)
+ *      weights      float  [n_l][K]            marginal weight of every sample
+ */
+#ifndef QEM_H
+#define QEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QEM_MAX_LEVELS 4
+#define QEM_GAMMA_TRIES 8
+
+typedef enum {
+  QEM_OK = 0,
+  QEM_ERR_INVALID_ARG = 1,  /* a size, pointer or descriptor field is invalid          */
+  QEM_ERR_UNSUPPORTED = 2,  /* valid but not implemented (e.g. a dimension too large)   */
+  QEM_ERR_OOM = 3,          /* workspace allocation failed                              */
+  QEM_ERR_CUDA = 4,         /* a CUDA call or kernel failed                             */
+  QEM_ERR_NUMERIC = 5,      /* non-finite log P_MP or weights                            */
+  QEM_ERR_TIMEOUT = 6       /* a bounded device-side wait expired                       */
+} qem_status;
+
+/* How p(z_e | z_parent) is defined for the elements of a level (the model's
+ * prior factor in Eq. rmp; App. F gives the models).                        */
+enum {
+  QEM_PRIOR_STD_NORMAL = 0,       /* N(0, prior_a I)                               (level 0 only) */
+  QEM_PRIOR_NORMAL_FIXED_VAR = 1, /* N(z_parent, prior_a I), D_parent = D                         */
+  QEM_PRIOR_NORMAL_MEAN_LOGVAR = 2,/* N(z_parent[0:D], diag exp(z_parent[D:2D])), D_parent = 2D    */
+  QEM_PRIOR_GAMMA = 3,            /* Gamma(shape prior_a, rate prior_b)            (level 0 only) */
+  QEM_PRIOR_BETA = 4              /* Beta(prior_a, prior_b)                         (level 0 only) */
+};
+
+/* Likelihood of the observations of one element; s_n = z . x_n.            */
+enum {
+  QEM_LIK_NONE = 0,
+  QEM_LIK_GAUSS = 1,              /* y_n ~ N(s_n, lik_var)                      */
+  QEM_LIK_BERNOULLI_LOGIT = 2,    /* y_n ~ Bernoulli(sigmoid(s_n))              */
+  QEM_LIK_POISSON_LOG = 3,        /* y_n ~ Poisson(exp(s_n))                    */
+  QEM_LIK_POISSON_RATE = 4,       /* y_n ~ Poisson(z), D = 1                    */
+  QEM_LIK_BERNOULLI_PROB = 5      /* y_n ~ Bernoulli(z), D = 1                  */
+};
+
+/* Exponential-family proposal families with closed-form M-steps (Sec. 4).   */
+enum { QEM_Q_GAUSS = 0, QEM_Q_GAMMA = 1, QEM_Q_BETA = 2 };
+
+/* Arithmetic of the K x K log-factor contraction (the other steps are FP32
+ * with FP64 plate sums, root and moments in every mode).                    */
+enum {
+  QEM_PREC_FP32 = 0,    /* FP32 CUDA-core contraction                                   */
+  QEM_PREC_BF16 = 1,    /* tcgen05 BF16 operands, FP32 accumulation                      */
+  QEM_PREC_BF16X3 = 2   /* tcgen05 split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+};
+
+typedef struct {
+  int64_t n;            /* plate elements at this level over all instances (n_0 = instances) */
+  int dim;              /* latent dimension D (1..64)                                        */
+  int prior;            /* QEM_PRIOR_*                                                        */
+  double prior_a, prior_b;
+  int lik;              /* QEM_LIK_*                                                          */
+  double lik_var;       /* variance of QEM_LIK_GAUSS                                          */
+  int n_obs;            /* observations per element (0 with QEM_LIK_NONE)                     */
+  int qfam;             /* QEM_Q_*                                                            */
+  const int64_t* parent;/* HOST [n]: parent element at level-1, non-decreasing; NULL at level 0 */
+  const float* x;       /* DEVICE [n][n_obs][dim] covariates (read at every E-step)            */
+  const float* y;       /* DEVICE [n][n_obs] observations                                      */
+} qem_level_desc;
+
+typedef struct {
+  int n_levels;                         /* 1..QEM_MAX_LEVELS */
+  qem_level_desc levels[QEM_MAX_LEVELS];
+} qem_model_desc;
+
+typedef struct {
+  int K;                /* samples per latent, 1..4096                                       */
+  int precision;        /* QEM_PREC_*                                                        */
+  int tile;             /* 0: tuned default; otherwise a contraction tile preset             */
+  void* stream;         /* cudaStream_t the plan's work is enqueued on (NULL: default stream) */
+  double var_floor;     /* Gaussian M-step variance floor factor (0: 1e-10)                   */
+  double timeout_s;     /* bound of every device-side wait (0: 2 s)                           */
+} qem_plan_opts;
+
+typedef struct qem_plan_s* qem_plan_t;
+
+/* Human-readable name of a status code (static storage). */
+const char* qem_status_string(qem_status s);
+
+/* Build a plan: validate the model (parents non-decreasing and in range, prior
+ * and dimension compatible with the parent level), copy its plate structure
+ * to the device and allocate the workspace (the only allocation the library
+ * makes; no later call allocates).  The model's x and y pointers are kept and
+ * read by every E-step.  *out is set to NULL on failure.                    */
+qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_plan_t* out);
+
+/* Release the plan and its workspace (synchronises the plan's stream). NULL is a no-op. */
+qem_status qem_plan_destroy(qem_plan_t plan);
+
+/* Bytes of device workspace the plan holds. */
+qem_status qem_workspace_size(const qem_plan_t plan, size_t* bytes);
+
+/* Offsets of level `level` inside the flat buffers (see the file comment):
+ * q_off (q_params, moments and mean_params), eps_off (eps), w_off (weights). */
+qem_status qem_layout(const qem_plan_t plan, int level, int64_t* q_off, int64_t* eps_off, int64_t* w_off);
+
+/* Total lengths of the flat buffers: q_len (q_params / moments / mean_params),
+ * eps_len (eps), w_len (weights), n_inst (log_pmp).                          */
+qem_status qem_sizes(const qem_plan_t plan, int64_t* q_len, int64_t* eps_len, int64_t* w_len, int64_t* n_inst);
+
+/* E-step (Alg. 1 "z ~ Q_t; m = MPIW(z, Q_t)"; Eq. mp_iw; Sec. 7 for the
+ * plate-tree recursion).  Draws K samples per latent from the proposal
+ * q_params (DEVICE float, layout above), forms the K_parent x K_child
+ * log-factor tiles, contracts them leaves-to-root in log space into
+ * log P_MP, runs the adjoint of that contraction root-to-leaves for the
+ * marginal weight of every sample, and writes
+ *   moments  DEVICE double [q_len]  E_w[T(z)] per element and dimension
+ *   log_pmp  DEVICE double [n_inst] log P_MP of every instance (nullable)
+ * eps: DEVICE float [eps_len] supplied noise, or NULL to draw it in-kernel
+ * from the counter-based stream keyed by (seed, iter).                     */
+qem_status qem_estep(qem_plan_t plan, const float* q_params, const float* eps, uint64_t seed,
+                     uint64_t iter, double* moments, double* log_pmp);
+
+/* M-step with EMA (Alg. 1 "m_t = lambda m_hat + (1-lambda) m_{t-1}" followed by
+ * the next iteration's "Q = set_exp_family_params(m_t)"; Eq. ema; App. B).
+ *   moments      DEVICE double [q_len]  this iteration's E-step estimate m_hat
+ *   mean_params  DEVICE double [q_len]  in: m_{t-1}; out: m_t
+ *   q_params     DEVICE float  [q_len]  out: parameters matched to m_t
+ * lambda is the weight of the new estimate; with sched_p in (0,1) it is
+ * replaced by t^-sched_p (the schedule of Thm. 1, 1-lambda(t) in its
+ * notation); t >= 1 is the iteration number.  moments may be NULL to only set
+ * q_params from mean_params (Alg. 1's initial M-step).                       */
+qem_status qem_mstep(qem_plan_t plan, const double* moments, double* mean_params, float* q_params,
+                     double lambda, double sched_p, int64_t t);
+
+/* Mean parameters of given proposal parameters (Alg. 1 "m_0 = initial values"):
+ *   q_params DEVICE float [q_len] in, mean_params DEVICE double [q_len] out.  */
+qem_status qem_mean_params(qem_plan_t plan, const float* q_params, double* mean_params);
+
+/* Copy log P_MP of the last E-step to HOST double [n_inst].  Synchronises the
+ * plan's stream; returns QEM_ERR_NUMERIC if any value is not finite, and
+ * QEM_ERR_TIMEOUT if a device wait of that E-step expired.                  */
+qem_status qem_log_pmp(qem_plan_t plan, double* host_out);
+
+/* Copy the marginal weights of the last E-step (the per-sample posterior
+ * weights of Eq. mmp, each element's K weights sum to one) to DEVICE float
+ * [w_len], asynchronously on the plan's stream.                              */
+qem_status qem_weights(qem_plan_t plan, float* weights);
+
+/* Copy the samples of the last E-step to DEVICE float [sum_l n_l*K*D_l]
+ * (level-major, [n_l][K][D_l] per level), asynchronously.                   */
+qem_status qem_samples(qem_plan_t plan, float* z);
+
+/* Run T iterations of QEM (Alg. 1) on the device, the E-step and M-step of
+ * every iteration enqueued back to back (captured once as a CUDA graph and
+ * replayed):
+ *   mean_params   DEVICE double [q_len]  in: m_0; out: m_T
+ *   q_params      DEVICE float  [q_len]  out: parameters matched to m_T
+ *   moments       DEVICE double [q_len]  scratch for each iteration's estimate
+ *   log_pmp_trace DEVICE double [T][n_inst] log P_MP of every iteration (nullable)
+ * Iteration t draws its noise from the stream keyed by (seed, t).           */
+qem_status qem_run(qem_plan_t plan, int64_t T, double lambda, double sched_p, uint64_t seed,
+                   double* mean_params, float* q_params, double* moments, double* log_pmp_trace);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QEM_H */

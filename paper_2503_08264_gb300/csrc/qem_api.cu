@@ -1,0 +1,421 @@
+// libqem host side: plan construction (validation, plate CSR, workspace) and
+// the C-ABI entry points declared in include/qem.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qem_internal.cuh"
+#include "qem_tc.cuh"
+
+using namespace qem;
+
+namespace {
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Carver {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += align256(sizeof(T) * count);
+    return count ? p : nullptr;
+  }
+};
+
+int noise_per_sample(const qem_level_desc& d) {
+  if (d.qfam == QEM_Q_GAUSS) return d.dim;
+  const int blk = 2 * QEM_GAMMA_TRIES + 1;
+  return d.dim * blk * (d.qfam == QEM_Q_GAMMA ? 1 : 2);
+}
+
+qem_status validate(const qem_model_desc* desc, const qem_plan_opts* o) {
+  if (!desc || !o) return QEM_ERR_INVALID_ARG;
+  if (desc->n_levels < 1 || desc->n_levels > QEM_MAX_LEVELS) return QEM_ERR_INVALID_ARG;
+  if (o->K < 1 || o->K > 4096) return QEM_ERR_INVALID_ARG;
+  if (o->precision < QEM_PREC_FP32 || o->precision > QEM_PREC_BF16X3) return QEM_ERR_INVALID_ARG;
+  if (o->var_floor < 0 || o->timeout_s < 0) return QEM_ERR_INVALID_ARG;
+  const int L = desc->n_levels;
+  for (int l = 0; l < L; ++l) {
+    const qem_level_desc& d = desc->levels[l];
+    if (d.n < 0 || d.dim < 1 || d.n_obs < 0) return QEM_ERR_INVALID_ARG;
+    if (d.dim > kMaxDim) return QEM_ERR_UNSUPPORTED;
+    if (d.qfam < QEM_Q_GAUSS || d.qfam > QEM_Q_BETA) return QEM_ERR_INVALID_ARG;
+    if (d.lik < QEM_LIK_NONE || d.lik > QEM_LIK_BERNOULLI_PROB) return QEM_ERR_INVALID_ARG;
+    if (d.lik == QEM_LIK_NONE && d.n_obs != 0) return QEM_ERR_INVALID_ARG;
+    if (d.lik != QEM_LIK_NONE && d.n_obs > 0 && d.n > 0 && (!d.x || !d.y)) return QEM_ERR_INVALID_ARG;
+    if (d.n_obs > 4096 || (size_t)d.n_obs * d.dim > 8192) return QEM_ERR_UNSUPPORTED;
+    if (d.lik == QEM_LIK_GAUSS && !(d.lik_var > 0)) return QEM_ERR_INVALID_ARG;
+    if ((d.lik == QEM_LIK_POISSON_RATE && (d.qfam != QEM_Q_GAMMA || d.dim != 1)) ||
+        (d.lik == QEM_LIK_BERNOULLI_PROB && (d.qfam != QEM_Q_BETA || d.dim != 1)))
+      return QEM_ERR_INVALID_ARG;
+    if (L > 1 && d.qfam != QEM_Q_GAUSS) return QEM_ERR_UNSUPPORTED;
+    if (l == 0) {
+      if (d.parent) return QEM_ERR_INVALID_ARG;
+      if (d.prior == QEM_PRIOR_STD_NORMAL) {
+        if (!(d.prior_a > 0) || d.qfam != QEM_Q_GAUSS) return QEM_ERR_INVALID_ARG;
+      } else if (d.prior == QEM_PRIOR_GAMMA) {
+        if (!(d.prior_a > 0 && d.prior_b > 0) || d.qfam != QEM_Q_GAMMA) return QEM_ERR_INVALID_ARG;
+      } else if (d.prior == QEM_PRIOR_BETA) {
+        if (!(d.prior_a > 0 && d.prior_b > 0) || d.qfam != QEM_Q_BETA) return QEM_ERR_INVALID_ARG;
+      } else {
+        return QEM_ERR_INVALID_ARG;
+      }
+    } else {
+      const qem_level_desc& p = desc->levels[l - 1];
+      if (d.prior == QEM_PRIOR_NORMAL_FIXED_VAR) {
+        if (p.dim != d.dim || !(d.prior_a > 0)) return QEM_ERR_INVALID_ARG;
+      } else if (d.prior == QEM_PRIOR_NORMAL_MEAN_LOGVAR) {
+        if (p.dim != 2 * d.dim) return QEM_ERR_INVALID_ARG;
+      } else {
+        return QEM_ERR_INVALID_ARG;
+      }
+      if (d.n > 0) {
+        if (!d.parent) return QEM_ERR_INVALID_ARG;
+        int64_t prev = 0;
+        for (int64_t e = 0; e < d.n; ++e) {
+          const int64_t pe = d.parent[e];
+          if (pe < 0 || pe >= p.n || pe < prev) return QEM_ERR_INVALID_ARG;
+          prev = pe;
+        }
+      }
+    }
+  }
+  return QEM_OK;
+}
+
+qem_status from_cuda(cudaError_t e) { return e == cudaSuccess ? QEM_OK : QEM_ERR_CUDA; }
+
+#define QEM_TRY(expr)                          \
+  do {                                         \
+    cudaError_t _e = (expr);                   \
+    if (_e != cudaSuccess) return QEM_ERR_CUDA; \
+  } while (0)
+
+// The E-step body (Eq. mp_iw over the plate tree), enqueued on the plan's stream.
+qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* moments, double* user_lp,
+                      double* trace) {
+  cudaStream_t s = P->stream;
+  const int L = P->L, K = P->K;
+  for (int l = 0; l < L; ++l)
+    QEM_TRY(launch_sample_local(P->lv[l], K, q + P->q_off[l], eps ? eps + P->eps_off[l] : nullptr, P->ctl, s));
+  for (int l = 0; l + 1 < L; ++l) QEM_TRY(launch_parent_params(P->lv[l], P->lv[l + 1], K, s));
+  for (int l = L - 1; l >= 1; --l) {
+    const bool has_children = l + 1 < L;
+    QEM_TRY(launch_finalize(P->lv[l], K, has_children, s));
+    if (P->precision == QEM_PREC_FP32)
+      QEM_TRY(launch_fwd_simt(P->lv[l], P->lv[l - 1], K, s));
+    else
+      QEM_TRY(tc_forward(P, l));
+    QEM_TRY(launch_plate_sum(P->lv[l - 1], P->lv[l], K, s));
+  }
+  QEM_TRY(launch_root(P->lv[0], K, L > 1, P->log_pmp, user_lp, trace, P->ctl, s));
+  for (int l = 1; l < L; ++l) {
+    if (P->precision == QEM_PREC_FP32)
+      QEM_TRY(launch_adj_simt(P->lv[l], P->lv[l - 1], K, s));
+    else
+      QEM_TRY(tc_adjoint(P, l));
+  }
+  for (int l = 0; l < L; ++l) QEM_TRY(launch_moments(P->lv[l], K, moments + P->q_off[l], s));
+  return QEM_OK;
+}
+
+qem_status mstep_body(qem_plan_t P, const double* moments, double* m, float* q, double lambda, double sched_p,
+                      long long t_host) {
+  for (int l = 0; l < P->L; ++l)
+    QEM_TRY(launch_mstep(P->lv[l], moments ? moments + P->q_off[l] : nullptr, m + P->q_off[l], q + P->q_off[l],
+                         lambda, sched_p, P->var_floor, t_host, P->ctl, P->stream));
+  return QEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qem_status_string(qem_status s) {
+  switch (s) {
+    case QEM_OK: return "QEM_OK";
+    case QEM_ERR_INVALID_ARG: return "QEM_ERR_INVALID_ARG: invalid size, pointer or descriptor field";
+    case QEM_ERR_UNSUPPORTED: return "QEM_ERR_UNSUPPORTED: valid request that is not implemented";
+    case QEM_ERR_OOM: return "QEM_ERR_OOM: workspace allocation failed";
+    case QEM_ERR_CUDA: return "QEM_ERR_CUDA: a CUDA call or kernel failed";
+    case QEM_ERR_NUMERIC: return "QEM_ERR_NUMERIC: non-finite log P_MP or weights";
+    case QEM_ERR_TIMEOUT: return "QEM_ERR_TIMEOUT: a bounded device wait expired";
+  }
+  return "QEM_ERR_UNKNOWN";
+}
+
+qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_plan_t* out) {
+  if (!out) return QEM_ERR_INVALID_ARG;
+  *out = nullptr;
+  qem_status st = validate(desc, opts);
+  if (st != QEM_OK) return st;
+  qem_plan_s* P = new (std::nothrow) qem_plan_s();
+  if (!P) return QEM_ERR_OOM;
+  P->L = desc->n_levels;
+  P->K = opts->K;
+  P->precision = opts->precision;
+  P->tile = opts->tile;
+  P->stream = (cudaStream_t)opts->stream;
+  P->var_floor = opts->var_floor > 0 ? opts->var_floor : 1e-10;
+  P->timeout_s = opts->timeout_s > 0 ? opts->timeout_s : 2.0;
+  if (cudaGetDevice(&P->device) != cudaSuccess) {
+    delete P;
+    return QEM_ERR_CUDA;
+  }
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, P->device);
+  P->num_sms = v;
+  cudaDeviceGetAttribute(&v, cudaDevAttrClockRate, P->device);
+  P->clock_khz = v > 0 ? v : 2000000;
+
+  const int L = P->L, K = P->K;
+  // offsets of the flat user buffers
+  long long qo = 0, eo = 0, wo = 0, zo = 0;
+  for (int l = 0; l < L; ++l) {
+    const qem_level_desc& d = desc->levels[l];
+    P->q_off[l] = qo;
+    P->eps_off[l] = eo;
+    P->w_off[l] = wo;
+    P->z_off[l] = zo;
+    qo += d.n * 2 * d.dim;
+    eo += d.n * (long long)K * noise_per_sample(d);
+    wo += d.n * (long long)K;
+    zo += d.n * (long long)K * d.dim;
+  }
+  P->q_len = qo;
+  P->eps_len = eo;
+  P->w_len = wo;
+  P->z_len = zo;
+
+  // children CSR offsets of every level that has a next level
+  std::vector<std::vector<long long>> child_off(L);
+  for (int l = 0; l + 1 < L; ++l) {
+    const qem_level_desc& c = desc->levels[l + 1];
+    std::vector<long long>& co = child_off[l];
+    co.assign((size_t)desc->levels[l].n + 1, 0);
+    for (int64_t e = 0; e < c.n; ++e) co[(size_t)c.parent[e] + 1] += 1;
+    for (size_t i = 1; i < co.size(); ++i) co[i] += co[i - 1];
+  }
+
+  // two passes: size, then carve
+  for (int pass = 0; pass < 2; ++pass) {
+    Carver cv;
+    if (pass == 1) {
+      if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
+        delete P;
+        return QEM_ERR_OOM;
+      }
+      cv.base = (char*)P->ws;
+    }
+    P->ctl = cv.take<Ctl>(1);
+    P->log_pmp = cv.take<double>((size_t)desc->levels[0].n);
+    for (int l = 0; l < L; ++l) {
+      const qem_level_desc& d = desc->levels[l];
+      LevelView& lv = P->lv[l];
+      const size_t nK = (size_t)d.n * K;
+      const bool has_children = l + 1 < L;
+      lv.n = d.n;
+      lv.D = d.dim;
+      lv.prior = d.prior;
+      lv.prior_a = (float)d.prior_a;
+      lv.prior_b = (float)d.prior_b;
+      lv.lik = d.lik;
+      lv.lik_var = (float)d.lik_var;
+      lv.n_obs = d.lik == QEM_LIK_NONE ? 0 : d.n_obs;
+      lv.qfam = d.qfam;
+      lv.nps = noise_per_sample(d);
+      lv.level = l;
+      lv.x = d.x;
+      lv.y = d.y;
+      lv.Dc = has_children ? desc->levels[l + 1].dim : 0;
+      lv.parent = l > 0 ? cv.take<long long>((size_t)d.n) : nullptr;
+      lv.child_off = has_children ? cv.take<long long>((size_t)d.n + 1) : nullptr;
+      lv.z = cv.take<float>(nK * d.dim);
+      lv.loc = cv.take<float>(nK);
+      lv.htil = has_children ? cv.take<float>(nK) : lv.loc;
+      lv.hsum = has_children ? cv.take<double>(nK) : nullptr;
+      lv.off = has_children ? cv.take<double>((size_t)d.n) : nullptr;
+      lv.lt = l > 0 ? cv.take<float>(nK) : nullptr;
+      lv.w = cv.take<float>(nK);
+      lv.pm = has_children ? cv.take<float>(nK * lv.Dc) : nullptr;
+      lv.pp = has_children ? cv.take<float>(nK * lv.Dc) : nullptr;
+      lv.pc = has_children ? cv.take<float>(nK) : nullptr;
+    }
+    size_t tc_bytes = 0;
+    st = tc_plan_reserve(P, desc, pass == 1 ? cv.base + cv.off : nullptr, &tc_bytes);
+    if (st != QEM_OK) {
+      if (P->ws) cudaFree(P->ws);
+      delete P;
+      return st;
+    }
+    cv.off += align256(tc_bytes);
+    if (pass == 0) P->ws_bytes = std::max<size_t>(cv.off, 256);
+  }
+  // upload the plate structure
+  cudaError_t ce = cudaMemsetAsync(P->ctl, 0, sizeof(Ctl), P->stream);
+  for (int l = 0; l < L && ce == cudaSuccess; ++l) {
+    const qem_level_desc& d = desc->levels[l];
+    if (l > 0 && d.n > 0)
+      ce = cudaMemcpyAsync((void*)P->lv[l].parent, d.parent, sizeof(long long) * (size_t)d.n, cudaMemcpyHostToDevice,
+                           P->stream);
+    if (ce == cudaSuccess && l + 1 < L)
+      ce = cudaMemcpyAsync((void*)P->lv[l].child_off, child_off[l].data(), sizeof(long long) * child_off[l].size(),
+                           cudaMemcpyHostToDevice, P->stream);
+    if (ce == cudaSuccess && P->lv[l].hsum)
+      ce = cudaMemsetAsync(P->lv[l].hsum, 0, sizeof(double) * (size_t)d.n * K, P->stream);
+  }
+  size_t smem = 0;
+  for (int l = 0; l < L; ++l) smem = std::max(smem, sample_local_smem(P->lv[l]));
+  if (ce == cudaSuccess) ce = configure_sample_local(smem);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->stream);
+  if (ce == cudaSuccess) {
+    st = tc_plan_init(P, desc);
+    if (st != QEM_OK) {
+      cudaFree(P->ws);
+      delete P;
+      return st;
+    }
+  }
+  if (ce != cudaSuccess) {
+    cudaFree(P->ws);
+    delete P;
+    return QEM_ERR_CUDA;
+  }
+  *out = P;
+  return QEM_OK;
+}
+
+qem_status qem_plan_destroy(qem_plan_t P) {
+  if (!P) return QEM_OK;
+  cudaError_t e = cudaStreamSynchronize(P->stream);
+  tc_plan_release(P);
+  if (P->ws) cudaFree(P->ws);
+  delete P;
+  return e == cudaSuccess ? QEM_OK : QEM_ERR_CUDA;
+}
+
+qem_status qem_workspace_size(const qem_plan_t P, size_t* bytes) {
+  if (!P || !bytes) return QEM_ERR_INVALID_ARG;
+  *bytes = P->ws_bytes;
+  return QEM_OK;
+}
+
+qem_status qem_layout(const qem_plan_t P, int level, int64_t* q_off, int64_t* eps_off, int64_t* w_off) {
+  if (!P || level < 0 || level >= P->L) return QEM_ERR_INVALID_ARG;
+  if (q_off) *q_off = P->q_off[level];
+  if (eps_off) *eps_off = P->eps_off[level];
+  if (w_off) *w_off = P->w_off[level];
+  return QEM_OK;
+}
+
+qem_status qem_sizes(const qem_plan_t P, int64_t* q_len, int64_t* eps_len, int64_t* w_len, int64_t* n_inst) {
+  if (!P) return QEM_ERR_INVALID_ARG;
+  if (q_len) *q_len = P->q_len;
+  if (eps_len) *eps_len = P->eps_len;
+  if (w_len) *w_len = P->w_len;
+  if (n_inst) *n_inst = P->lv[0].n;
+  return QEM_OK;
+}
+
+qem_status qem_estep(qem_plan_t P, const float* q_params, const float* eps, uint64_t seed, uint64_t iter,
+                     double* moments, double* log_pmp) {
+  if (!P || !q_params || !moments) return QEM_ERR_INVALID_ARG;
+  QEM_TRY(launch_set_ctl(P->ctl, seed, iter, 1, -1, P->stream));
+  return estep_body(P, q_params, eps, moments, log_pmp, nullptr);
+}
+
+qem_status qem_mstep(qem_plan_t P, const double* moments, double* mean_params, float* q_params, double lambda,
+                     double sched_p, int64_t t) {
+  if (!P || !mean_params || !q_params) return QEM_ERR_INVALID_ARG;
+  if (!(lambda >= 0.0 && lambda <= 1.0) || !(sched_p >= 0.0 && sched_p < 1.0) || t < 1) return QEM_ERR_INVALID_ARG;
+  return mstep_body(P, moments, mean_params, q_params, lambda, sched_p, t);
+}
+
+qem_status qem_mean_params(qem_plan_t P, const float* q_params, double* mean_params) {
+  if (!P || !q_params || !mean_params) return QEM_ERR_INVALID_ARG;
+  for (int l = 0; l < P->L; ++l)
+    QEM_TRY(launch_mean_params(P->lv[l], q_params + P->q_off[l], mean_params + P->q_off[l], P->stream));
+  return QEM_OK;
+}
+
+qem_status qem_log_pmp(qem_plan_t P, double* host_out) {
+  if (!P || !host_out) return QEM_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEM_ERR_CUDA;
+  Ctl c;
+  if (cudaMemcpy(&c, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return QEM_ERR_CUDA;
+  if (P->lv[0].n > 0 &&
+      cudaMemcpy(host_out, P->log_pmp, sizeof(double) * (size_t)P->lv[0].n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return QEM_ERR_CUDA;
+  if (c.err & ERR_TIMEOUT) return QEM_ERR_TIMEOUT;
+  for (long long i = 0; i < P->lv[0].n; ++i)
+    if (!std::isfinite(host_out[i])) return QEM_ERR_NUMERIC;
+  if (c.err & ERR_NUMERIC) return QEM_ERR_NUMERIC;
+  return QEM_OK;
+}
+
+qem_status qem_weights(qem_plan_t P, float* weights) {
+  if (!P || !weights) return QEM_ERR_INVALID_ARG;
+  for (int l = 0; l < P->L; ++l) {
+    const size_t nK = (size_t)P->lv[l].n * P->K;
+    if (nK)
+      QEM_TRY(cudaMemcpyAsync(weights + P->w_off[l], P->lv[l].w, sizeof(float) * nK, cudaMemcpyDeviceToDevice,
+                              P->stream));
+  }
+  return QEM_OK;
+}
+
+qem_status qem_samples(qem_plan_t P, float* z) {
+  if (!P || !z) return QEM_ERR_INVALID_ARG;
+  for (int l = 0; l < P->L; ++l) {
+    const size_t cnt = (size_t)P->lv[l].n * P->K * P->lv[l].D;
+    if (cnt)
+      QEM_TRY(cudaMemcpyAsync(z + P->z_off[l], P->lv[l].z, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, P->stream));
+  }
+  return QEM_OK;
+}
+
+qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint64_t seed, double* mean_params,
+                   float* q_params, double* moments, double* log_pmp_trace) {
+  if (!P || T < 0 || !mean_params || !q_params || !moments) return QEM_ERR_INVALID_ARG;
+  if (!(lambda >= 0.0 && lambda <= 1.0) || !(sched_p >= 0.0 && sched_p < 1.0)) return QEM_ERR_INVALID_ARG;
+  cudaStream_t s = P->stream;
+  cudaStream_t own = nullptr;
+  if (s == nullptr) {  // legacy stream cannot be captured: use a private stream and finish synchronously
+    if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) return QEM_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return QEM_ERR_CUDA;
+    P->stream = own;
+  }
+  qem_status st = QEM_OK;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  do {
+    if (launch_set_ctl(P->ctl, seed, 1, 1, log_pmp_trace ? 0 : -1, P->stream) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
+    st = mstep_body(P, nullptr, mean_params, q_params, lambda, sched_p, 1);  // Q_1 = set(m_0)
+    if (st != QEM_OK || T == 0) break;
+    if (cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
+    qem_status sb = estep_body(P, q_params, nullptr, moments, nullptr, log_pmp_trace);
+    if (sb == QEM_OK) sb = mstep_body(P, moments, mean_params, q_params, lambda, sched_p, 0);
+    if (sb == QEM_OK && launch_advance_ctl(P->ctl, P->lv[0].n, P->stream) != cudaSuccess) sb = QEM_ERR_CUDA;
+    cudaError_t ec = cudaStreamEndCapture(P->stream, &g);
+    if (sb != QEM_OK || ec != cudaSuccess) { st = sb != QEM_OK ? sb : QEM_ERR_CUDA; break; }
+    if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
+    for (int64_t t = 0; t < T; ++t)
+      if (cudaGraphLaunch(ge, P->stream) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
+  } while (0);
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  if (own) {
+    if (cudaStreamSynchronize(own) != cudaSuccess && st == QEM_OK) st = QEM_ERR_CUDA;
+    cudaStreamDestroy(own);
+    P->stream = nullptr;
+  }
+  return st;
+}
+
+}  // extern "C"

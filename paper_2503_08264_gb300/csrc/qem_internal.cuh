@@ -1,0 +1,177 @@
+// Internal declarations of libqem: the plan, the per-level device views and
+// the device helpers every kernel file uses.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qem.h"
+
+namespace qem {
+
+constexpr int kMaxDim = 64;
+constexpr float kLog2Pi = 1.8378770664093453f;
+constexpr double kLog2PiD = 1.8378770664093454835606594728112;
+
+// Error bits raised by kernels in the plan's control block.
+enum : int { ERR_NUMERIC = 1, ERR_TIMEOUT = 2, ERR_INTERNAL = 4 };
+
+// Device control block: written by tiny kernels so that a captured graph can
+// advance the iteration without re-capture.
+struct Ctl {
+  unsigned long long seed;
+  unsigned long long iter;     // noise stream iteration
+  long long t;                 // EMA iteration number (>= 1)
+  long long trace_row;         // row of the log P_MP trace to write (-1: none)
+  int err;                     // ERR_* bits
+  int pad;
+};
+
+// Device view of one level of the plan (all pointers device).
+struct LevelView {
+  long long n;        // elements
+  int D;              // latent dim
+  int prior;          // QEM_PRIOR_*
+  float prior_a, prior_b;
+  int lik;
+  float lik_var;
+  int n_obs;
+  int qfam;
+  int nps;            // noise numbers per sample
+  int level;          // index of this level
+  const float* x;     // [n][n_obs][D]
+  const float* y;     // [n][n_obs]
+  const long long* parent;     // [n] (level > 0)
+  const long long* child_off;  // [n+1] offsets of children at level+1 (if any)
+  // workspace
+  float* z;           // [n][K][D]
+  float* loc;         // [n][K]  log lik - log q (+ log prior at level 0)
+  float* htil;        // [n][K]  loc + children's sum - off  (relative local factor)
+  double* hsum;       // [n][K]  sum over children of their log mean-exp (FP64)
+  double* off;        // [n]     constant removed from htil
+  float* lt;          // [n][K]  (level > 0) relative log mean_k exp S_e[kp][k], per parent sample kp
+  float* w;           // [n][K]  marginal weights
+  // conditional parameters of this level's children given each of its samples
+  float* pm;          // [n][K][Dc] child-prior mean
+  float* pp;          // [n][K][Dc] -0.5 * child-prior precision
+  float* pc;          // [n][K]     child-prior log normaliser
+  int Dc;             // dimension of the children (0: none)
+};
+
+struct TcBuffers;  // tensor-core operand buffers (qem_tc.cu)
+
+}  // namespace qem
+
+struct qem_plan_s {
+  int L = 0;
+  int K = 0;
+  int precision = 0;
+  int tile = 0;
+  cudaStream_t stream = nullptr;
+  double var_floor = 1e-10;
+  double timeout_s = 2.0;
+  int device = 0;
+  int num_sms = 0;
+  long long clock_khz = 0;
+  qem::LevelView lv[QEM_MAX_LEVELS];
+  long long q_off[QEM_MAX_LEVELS], eps_off[QEM_MAX_LEVELS], w_off[QEM_MAX_LEVELS], z_off[QEM_MAX_LEVELS];
+  long long q_len = 0, eps_len = 0, w_len = 0, z_len = 0;
+  double* log_pmp = nullptr;   // [n_inst] of the last E-step
+  qem::Ctl* ctl = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  qem::TcBuffers* tc = nullptr;
+};
+
+namespace qem {
+
+// ---------------------------------------------------------------------------
+// Counter-based noise: Philox4x32-10 (Salmon et al., SC'11) with the counter
+// layout key = seed, ctr = (sample lo, sample hi, level<<24 | idx/4, iter).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// -2 log u for u = (x + 0.5) 2^-32, accurate at both ends of (0, 1).
+__device__ __forceinline__ float neg2_log_unit(uint32_t x) {
+  if (x < 0x80000000u) return -2.f * logf(((float)x + 0.5f) * 2.3283064365386963e-10f);
+  const float one_minus_u = ((float)(0xFFFFFFFFu - x) + 0.5f) * 2.3283064365386963e-10f;
+  return -2.f * log1pf(-one_minus_u);
+}
+
+__device__ __forceinline__ float unit_of(uint32_t x) { return ((float)x + 0.5f) * 2.3283064365386963e-10f; }
+
+// Four N(0,1) numbers of block `blk` of one sample (Box-Muller on (u0,u1), (u2,u3)).
+__device__ __forceinline__ float4 normal4(unsigned long long seed, unsigned long long iter, int level,
+                                          unsigned long long sample, uint32_t blk) {
+  const uint4 r = philox4x32_10(
+      make_uint4((uint32_t)sample, (uint32_t)(sample >> 32), ((uint32_t)level << 24) | blk, (uint32_t)iter),
+      make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  float s0, c0, s1, c1;
+  sincospif(2.f * unit_of(r.y), &s0, &c0);
+  sincospif(2.f * unit_of(r.w), &s1, &c1);
+  const float r0 = sqrtf(neg2_log_unit(r.x)), r1 = sqrtf(neg2_log_unit(r.z));
+  return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+}
+
+// One noise number of index idx (normal or uniform slot, as the family's layout says).
+__device__ __forceinline__ float noise_at(unsigned long long seed, unsigned long long iter, int level,
+                                          unsigned long long sample, int idx, int qfam) {
+  const uint4 r = philox4x32_10(
+      make_uint4((uint32_t)sample, (uint32_t)(sample >> 32), ((uint32_t)level << 24) | (uint32_t)(idx >> 2),
+                 (uint32_t)iter),
+      make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const uint32_t v[4] = {r.x, r.y, r.z, r.w};
+  const int j = idx & 3;
+  bool uni = false;
+  if (qfam != QEM_Q_GAUSS) {
+    const int blk = 2 * QEM_GAMMA_TRIES + 1, rr = idx % blk;
+    uni = (rr == blk - 1) || (rr & 1);
+  }
+  if (uni) return unit_of(v[j]);
+  const float rad = sqrtf(neg2_log_unit(v[j & 2]));
+  float s, c;
+  sincospif(2.f * unit_of(v[(j & 2) + 1]), &s, &c);
+  return (j & 1) ? rad * s : rad * c;
+}
+
+// Bounded spin on a flag (for device-side waits): returns false on expiry.
+__device__ __forceinline__ bool spin_until_ge(const volatile int* flag, int target, long long max_cycles) {
+  const long long t0 = clock64();
+  while (*flag < target) {
+    if (clock64() - t0 > max_cycles) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (qem_simt.cu / qem_tc.cu).
+cudaError_t launch_set_ctl(Ctl* ctl, unsigned long long seed, unsigned long long iter, long long t,
+                           long long trace_row, cudaStream_t s);
+cudaError_t launch_advance_ctl(Ctl* ctl, long long n_inst, cudaStream_t s);
+cudaError_t launch_sample_local(const LevelView& v, int K, const float* q, const float* eps, const Ctl* ctl,
+                                cudaStream_t s);
+cudaError_t launch_parent_params(const LevelView& parent, const LevelView& child, int K, cudaStream_t s);
+cudaError_t launch_finalize(const LevelView& v, int K, bool has_children, cudaStream_t s);
+cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
+cudaError_t launch_plate_sum(const LevelView& parent, const LevelView& child, int K, cudaStream_t s);
+cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* log_pmp, double* user_out,
+                        double* trace, Ctl* ctl, cudaStream_t s);
+cudaError_t launch_adj_simt(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
+cudaError_t launch_moments(const LevelView& v, int K, double* mom, cudaStream_t s);
+cudaError_t launch_mstep(const LevelView& v, const double* mom, double* m, float* q, double lambda,
+                         double sched_p, double var_floor, long long t_host, const Ctl* ctl, cudaStream_t s);
+size_t sample_local_smem(const LevelView& v);
+cudaError_t configure_sample_local(size_t smem);
+cudaError_t launch_mean_params(const LevelView& v, const float* q, double* m, cudaStream_t s);
+
+}  // namespace qem

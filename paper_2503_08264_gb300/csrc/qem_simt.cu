@@ -1,0 +1,709 @@
+// libqem CUDA-core kernels: sampling and local factors, the FP32 log-factor
+// contraction (forward log-mean-exp and its adjoint), plate sums, the root,
+// moments and the M-step.  Every kernel cites the passage of arXiv
+// 2503.08264 it realises.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "qem_internal.cuh"
+
+namespace qem {
+
+// ---------------------------------------------------------------------------
+// Control block kernels (let a captured graph advance the iteration).
+__global__ void k_set_ctl(Ctl* ctl, unsigned long long seed, unsigned long long iter, long long t,
+                          long long trace_row) {
+  ctl->seed = seed;
+  ctl->iter = iter;
+  ctl->t = t;
+  ctl->trace_row = trace_row;
+}
+
+__global__ void k_advance_ctl(Ctl* ctl) {
+  ctl->iter += 1;
+  ctl->t += 1;
+  if (ctl->trace_row >= 0) ctl->trace_row += 1;
+}
+
+cudaError_t launch_set_ctl(Ctl* ctl, unsigned long long seed, unsigned long long iter, long long t,
+                           long long trace_row, cudaStream_t s) {
+  k_set_ctl<<<1, 1, 0, s>>>(ctl, seed, iter, t, trace_row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_ctl(Ctl* ctl, long long, cudaStream_t s) {
+  k_advance_ctl<<<1, 1, 0, s>>>(ctl);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Gamma / Beta draws from noise (Marsaglia & Tsang 2000; Beta = G1/(G1+G2)).
+// Accept/reject decisions are taken in FP64.
+struct NoiseSrc {
+  const float* eps;   // this sample's supplied noise, or nullptr
+  unsigned long long seed, iter, sample;
+  int level, qfam;
+  __device__ float operator()(int idx) const {
+    return eps ? eps[idx] : noise_at(seed, iter, level, sample, idx, qfam);
+  }
+};
+
+__device__ double gamma_variate(double a, const NoiseSrc& ns, int base) {
+  const double ab = a < 1.0 ? a + 1.0 : a;
+  const double d = ab - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+  double g = d;
+  for (int t = 0; t < QEM_GAMMA_TRIES; ++t) {
+    const double xn = ns(base + 2 * t), u = ns(base + 2 * t + 1);
+    double v = 1.0 + c * xn;
+    if (v <= 0.0) continue;
+    v = v * v * v;
+    if (log(u) < 0.5 * xn * xn + d - d * v + d * log(v)) {
+      g = d * v;
+      break;
+    }
+  }
+  if (a < 1.0) g *= pow((double)ns(base + 2 * QEM_GAMMA_TRIES), 1.0 / a);
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// K1/K2: draw z ~ Q and evaluate the local factor of every sample
+// (Alg. 1 "z ~ Q_t"; the P(x|z)/Q(z) part of r_k in Eq. rmp):
+//   loc[e][k] = sum_n log p(y_en | z_e^k, x_en) - log q(z_e^k) (+ log p(z) at level 0).
+// One block per element; its covariates and q parameters live in shared
+// memory; the block's samples are staged in shared memory so that noise loads
+// and sample stores are coalesced.
+constexpr int kSampleThreads = 128;
+
+__device__ __forceinline__ float softplusf(float s) { return fmaxf(s, 0.f) + log1pf(__expf(-fabsf(s))); }
+
+__global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, int K, const float* __restrict__ q,
+                                                                  const float* __restrict__ eps, const Ctl* ctl) {
+  extern __shared__ float sm[];
+  const long long e = blockIdx.x;
+  const int D = v.D, nobs = v.n_obs, zs_stride = D + 1;
+  float* xs = sm;                       // [nobs][D]
+  float* ys = xs + nobs * D;            // [nobs]
+  float* qs = ys + nobs;                // [2][D]
+  float* zs = qs + 2 * D;               // [blockDim][D+1]
+  for (int i = threadIdx.x; i < nobs * D; i += blockDim.x) xs[i] = v.x[e * nobs * D + i];
+  for (int i = threadIdx.x; i < nobs; i += blockDim.x) ys[i] = v.y[e * nobs + i];
+  for (int i = threadIdx.x; i < 2 * D; i += blockDim.x) qs[i] = q[e * 2 * D + i];
+  __syncthreads();
+  const unsigned long long seed = ctl->seed, iter = ctl->iter;
+  float sum_log_scale = 0.f;
+  if (v.qfam == QEM_Q_GAUSS)
+    for (int d = 0; d < D; ++d) sum_log_scale += logf(qs[D + d]);
+
+  for (int k0 = 0; k0 < K; k0 += blockDim.x) {
+    const int nk = min((int)blockDim.x, K - k0);
+    const int k = k0 + threadIdx.x;
+    const bool act = threadIdx.x < nk;
+    float* zr = zs + threadIdx.x * zs_stride;
+    float lq = 0.f;
+    if (v.qfam == QEM_Q_GAUSS) {
+      // noise -> zs (coalesced when supplied)
+      if (eps) {
+        const float* src = eps + (e * K + k0) * (long long)D;
+        for (int i = threadIdx.x; i < nk * D; i += blockDim.x) zs[(i / D) * zs_stride + (i % D)] = src[i];
+        __syncthreads();
+      } else if (act) {
+        const unsigned long long sample = (unsigned long long)e * K + k;
+        for (int d0 = 0; d0 < D; d0 += 4) {
+          const float4 g = normal4(seed, iter, v.level, sample, (uint32_t)(d0 >> 2));
+          zr[d0] = g.x;
+          if (d0 + 1 < D) zr[d0 + 1] = g.y;
+          if (d0 + 2 < D) zr[d0 + 2] = g.z;
+          if (d0 + 3 < D) zr[d0 + 3] = g.w;
+        }
+      }
+      if (act) {
+        float ss = 0.f;
+        for (int d = 0; d < D; ++d) {
+          const float ep = zr[d];
+          ss = fmaf(ep, ep, ss);
+          zr[d] = fmaf(qs[D + d], ep, qs[d]);
+        }
+        lq = -0.5f * ss - sum_log_scale - 0.5f * D * kLog2Pi;
+      }
+    } else if (act) {
+      const unsigned long long sample = (unsigned long long)e * K + k;
+      NoiseSrc ns{eps ? eps + (e * K + k) * (long long)v.nps : nullptr, seed, iter, sample, v.level, v.qfam};
+      const int blk = 2 * QEM_GAMMA_TRIES + 1;
+      double lqd = 0.0;
+      for (int d = 0; d < D; ++d) {
+        const double a = qs[d], b = qs[D + d];
+        double zz;
+        if (v.qfam == QEM_Q_GAMMA) {
+          zz = gamma_variate(a, ns, d * blk) / b;
+          lqd += a * log(b) - lgamma(a) + (a - 1.0) * log(zz) - b * zz;
+        } else {
+          const double g1 = gamma_variate(a, ns, (2 * d) * blk), g2 = gamma_variate(b, ns, (2 * d + 1) * blk);
+          zz = g1 / (g1 + g2);
+          lqd += (a - 1.0) * log(zz) + (b - 1.0) * log1p(-zz) - (lgamma(a) + lgamma(b) - lgamma(a + b));
+        }
+        zr[d] = (float)zz;
+      }
+      lq = (float)lqd;
+    }
+    if (act) {
+      float ll = 0.f;
+      for (int n = 0; n < nobs; ++n) {
+        float s = 0.f;
+        const float* xn = xs + n * D;
+        for (int d = 0; d < D; ++d) s = fmaf(zr[d], xn[d], s);
+        const float yv = ys[n];
+        switch (v.lik) {
+          case QEM_LIK_GAUSS: {
+            const float r = yv - s;
+            ll += -0.5f * logf(2.f * 3.14159265358979f * v.lik_var) - r * r / (2.f * v.lik_var);
+            break;
+          }
+          case QEM_LIK_BERNOULLI_LOGIT: ll += yv * s - softplusf(s); break;
+          case QEM_LIK_POISSON_LOG: ll += yv * s - expf(s) - lgammaf(yv + 1.f); break;
+          case QEM_LIK_POISSON_RATE: ll += yv * logf(zr[0]) - zr[0] - lgammaf(yv + 1.f); break;
+          case QEM_LIK_BERNOULLI_PROB: ll += yv * logf(zr[0]) + (1.f - yv) * log1pf(-zr[0]); break;
+          default: break;
+        }
+      }
+      float lp = 0.f;
+      if (v.level == 0) {
+        switch (v.prior) {
+          case QEM_PRIOR_STD_NORMAL: {
+            float ss = 0.f;
+            for (int d = 0; d < D; ++d) ss = fmaf(zr[d], zr[d], ss);
+            lp = -0.5f * ss / v.prior_a - 0.5f * D * logf(2.f * 3.14159265358979f * v.prior_a);
+            break;
+          }
+          case QEM_PRIOR_GAMMA: {
+            const double a0 = v.prior_a, b0 = v.prior_b;
+            double acc = 0.0;
+            for (int d = 0; d < D; ++d)
+              acc += a0 * log(b0) - lgamma(a0) + (a0 - 1.0) * log((double)zr[d]) - b0 * zr[d];
+            lp = (float)acc;
+            break;
+          }
+          case QEM_PRIOR_BETA: {
+            const double a0 = v.prior_a, b0 = v.prior_b;
+            double acc = 0.0;
+            for (int d = 0; d < D; ++d)
+              acc += (a0 - 1.0) * log((double)zr[d]) + (b0 - 1.0) * log1p(-(double)zr[d]) -
+                     (lgamma(a0) + lgamma(b0) - lgamma(a0 + b0));
+            lp = (float)acc;
+            break;
+          }
+          default: break;
+        }
+      }
+      v.loc[e * K + k] = ll - lq + lp;
+    }
+    __syncthreads();
+    // coalesced store of the block's samples
+    float* dst = v.z + (e * K + k0) * (long long)D;
+    for (int i = threadIdx.x; i < nk * D; i += blockDim.x) dst[i] = zs[(i / D) * zs_stride + (i % D)];
+    __syncthreads();
+  }
+}
+
+size_t sample_local_smem(const LevelView& v) {
+  return sizeof(float) * (size_t)(v.n_obs * v.D + v.n_obs + 2 * v.D + kSampleThreads * (v.D + 1));
+}
+
+cudaError_t configure_sample_local(size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_sample_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_sample_local(const LevelView& v, int K, const float* q, const float* eps, const Ctl* ctl,
+                                cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  const size_t smem = sample_local_smem(v);
+  k_sample_local<<<(unsigned)v.n, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Conditional parameters of a child given each parent sample: the child prior
+// p(z_c | z_p^kp) = N(mean, diag(1/prec)) written as
+//   log p = pc + sum_d pp_d (z_d - pm_d)^2,  pp = -prec/2.
+// (App. F: N(z_parent, v I) and N(mu, diag exp(psi)).)
+__global__ void k_parent_params(LevelView par, int child_prior, float child_var, int Dc, int K) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // parent sample (p, kp)
+  if (i >= par.n * K) return;
+  const float* zp = par.z + i * par.D;
+  float* pm = par.pm + i * Dc;
+  float* pp = par.pp + i * Dc;
+  if (child_prior == QEM_PRIOR_NORMAL_FIXED_VAR) {
+    for (int d = 0; d < Dc; ++d) {
+      pm[d] = zp[d];
+      pp[d] = -0.5f / child_var;
+    }
+    par.pc[i] = -0.5f * Dc * logf(2.f * 3.14159265358979f * child_var);
+  } else {
+    float c = -0.5f * Dc * kLog2Pi;
+    for (int d = 0; d < Dc; ++d) {
+      const float lv = zp[Dc + d];
+      pm[d] = zp[d];
+      pp[d] = -0.5f * expf(-lv);
+      c -= 0.5f * lv;
+    }
+    par.pc[i] = c;
+  }
+}
+
+cudaError_t launch_parent_params(const LevelView& parent, const LevelView& child, int K, cudaStream_t s) {
+  const long long tot = parent.n * K;
+  if (tot == 0 || child.n == 0) return cudaSuccess;
+  k_parent_params<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(parent, child.prior, child.prior_a, child.D, K);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Relative local factor of an element with children: htil = loc + H - c,
+// c = max_k H[k] kept in FP64 (off), so the FP32 contraction sees values of
+// moderate size; c re-enters at the parent's plate sum.
+__global__ void k_finalize(LevelView v, int K) {
+  const long long e = blockIdx.x;
+  __shared__ double red[32];
+  double mx = -INFINITY;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, v.hsum[e * K + k]);
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -INFINITY;
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  const double c = isfinite(red[0]) ? red[0] : 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) v.htil[e * K + k] = (float)((double)v.loc[e * K + k] + (v.hsum[e * K + k] - c));
+  if (threadIdx.x == 0) v.off[e] = c;
+}
+
+cudaError_t launch_finalize(const LevelView& v, int K, bool has_children, cudaStream_t s) {
+  if (v.n == 0 || !has_children) return cudaSuccess;
+  k_finalize<<<(unsigned)v.n, 256, 0, s>>>(v, K);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K3 (FP32): forward contraction of one plate element (Eq. Prmp summed over
+// the child index, Sec. 7):
+//   lt[e][kp] = log (1/K) sum_k exp( log p(z_e^k | z_p^kp) + htil[e][k] )
+// One thread per parent sample kp; the element's child samples stream
+// through shared memory in chunks; online max-shifted sum per row.
+constexpr int kRowTile = 128;
+constexpr int kChunk = 32;
+
+template <int MAXD>
+__global__ void __launch_bounds__(kRowTile) k_fwd_simt(LevelView v, LevelView par, int K, int n_rt) {
+  __shared__ float zs[kChunk * MAXD];
+  __shared__ float hs[kChunk];
+  const long long e = blockIdx.x / n_rt;
+  const int kp = (blockIdx.x % n_rt) * blockDim.x + threadIdx.x;
+  const int D = v.D;
+  const long long p = v.parent[e];
+  const bool act = kp < K;
+  float pm[MAXD], pp[MAXD], pc = 0.f;
+#pragma unroll
+  for (int d = 0; d < MAXD; ++d) {
+    pm[d] = 0.f;
+    pp[d] = 0.f;
+    if (act && d < D) {
+      pm[d] = par.pm[(p * K + kp) * D + d];
+      pp[d] = par.pp[(p * K + kp) * D + d];
+    }
+  }
+  if (act) pc = par.pc[p * K + kp];
+  float m = -INFINITY, s = 0.f;
+  for (int k0 = 0; k0 < K; k0 += kChunk) {
+    const int nk = min(kChunk, K - k0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kChunk * MAXD; i += blockDim.x) {
+      const int j = i / MAXD, d = i % MAXD;
+      zs[i] = (j < nk && d < D) ? v.z[(e * K + k0 + j) * D + d] : 0.f;
+    }
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) hs[i] = v.htil[e * K + k0 + i];
+    __syncthreads();
+    if (!act) continue;
+    float val[kChunk];
+    float cm = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+      float a = -INFINITY;
+      if (j < nk) {
+        a = pc + hs[j];
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) {
+          const float t = zs[j * MAXD + d] - pm[d];
+          a = fmaf(pp[d], t * t, a);
+        }
+      }
+      val[j] = a;
+      cm = fmaxf(cm, a);
+    }
+    if (cm == -INFINITY) continue;
+    if (cm > m) {
+      s *= expf(m - cm);
+      m = cm;
+    }
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) s += expf(val[j] - m);
+  }
+  if (act) v.lt[e * K + kp] = m + logf(s) - logf((float)K);
+}
+
+template <int MAXD>
+static cudaError_t fwd_simt_dispatch(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
+  const int thr = K >= kRowTile ? kRowTile : ((K + 31) / 32) * 32;
+  const int n_rt = (K + thr - 1) / thr;
+  k_fwd_simt<MAXD><<<(unsigned)(v.n * n_rt), thr, 0, s>>>(v, par, K, n_rt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  if (v.D <= 4) return fwd_simt_dispatch<4>(v, par, K, s);
+  if (v.D <= 8) return fwd_simt_dispatch<8>(v, par, K, s);
+  if (v.D <= 20) return fwd_simt_dispatch<20>(v, par, K, s);
+  if (v.D <= 32) return fwd_simt_dispatch<32>(v, par, K, s);
+  return fwd_simt_dispatch<64>(v, par, K, s);
+}
+
+// ---------------------------------------------------------------------------
+// Plate sum (Sec. 7: the child's factor enters the parent's as a sum over the
+// plate): hsum_p[kp] = sum_{e in children(p)} (lt[e][kp] + off[e]) in FP64,
+// in a fixed order (deterministic).  One thread per (parent, kp); the
+// children of a parent are split into 8 interleaved slices reduced in order.
+__global__ void k_plate_sum(LevelView par, LevelView ch, int K) {
+  __shared__ double red[8][33];
+  const long long p = blockIdx.x;
+  const int kp = blockIdx.y * 32 + threadIdx.x;
+  const long long c0 = par.child_off[p], c1 = par.child_off[p + 1];
+  double acc = 0.0;
+  if (kp < K) {
+    for (long long c = c0 + threadIdx.y; c < c1; c += 8)
+      acc += (double)ch.lt[c * K + kp] + (ch.off ? ch.off[c] : 0.0);
+  }
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && kp < K) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
+    par.hsum[p * K + kp] = t;
+  }
+}
+
+cudaError_t launch_plate_sum(const LevelView& parent, const LevelView& child, int K, cudaStream_t s) {
+  if (parent.n == 0) return cudaSuccess;
+  dim3 grid((unsigned)parent.n, (unsigned)((K + 31) / 32));
+  k_plate_sum<<<grid, dim3(32, 8), 0, s>>>(parent, child, K);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K4: root of each instance (Eq. Prmp after all children are summed out):
+//   a[k] = log p(z_0^k) + log lik - log q + H[k],
+//   log P_MP = log (1/K) sum_k exp a[k],   w_0[k] = exp(a[k] - log sum exp a)   (FP64).
+__global__ void k_root(LevelView v, int K, int has_children, double* log_pmp, double* user_out, double* trace,
+                       Ctl* ctl) {
+  const long long i = blockIdx.x;
+  __shared__ double red[32];
+  __shared__ double bc;
+  auto a_of = [&](int k) -> double {
+    return (double)v.loc[i * K + k] + (has_children ? v.hsum[i * K + k] : 0.0);
+  };
+  double mx = -INFINITY;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, a_of(k));
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = -INFINITY;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) m = fmax(m, red[j]);
+    bc = m;
+  }
+  __syncthreads();
+  const double m = bc;
+  double sacc = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) sacc += exp(a_of(k) - m);
+  for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sacc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += red[j];
+    const double lse = m + log(t);
+    bc = lse;
+    const double lp = lse - log((double)K);
+    log_pmp[i] = lp;
+    if (user_out) user_out[i] = lp;
+    if (trace && ctl->trace_row >= 0) trace[ctl->trace_row * gridDim.x + i] = lp;
+    if (!isfinite(lp)) atomicOr(&ctl->err, ERR_NUMERIC);
+  }
+  __syncthreads();
+  const double lse = bc;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) v.w[i * K + k] = (float)exp(a_of(k) - lse);
+}
+
+cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* log_pmp, double* user_out,
+                        double* trace, Ctl* ctl, cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  k_root<<<(unsigned)v.n, 256, 0, s>>>(v, K, has_children ? 1 : 0, log_pmp, user_out, trace, ctl);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K5 (FP32): adjoint of the contraction = marginal weights (Eq. mmp with the
+// indicator moment; Sec. 3.2's source-term trick in closed form):
+//   w_e[k] = sum_kp w_p[kp] exp( S_e[kp][k] - log sum_k' exp S_e[kp][k'] ).
+// One thread per child sample k; the parent's samples stream through shared
+// memory with the per-(e, kp) shift log w_p[kp] - lt[e][kp] - log K folded in.
+template <int MAXD>
+__global__ void __launch_bounds__(kRowTile) k_adj_simt(LevelView v, LevelView par, int K, int n_rt) {
+  __shared__ float pms[kChunk * MAXD];
+  __shared__ float pps[kChunk * MAXD];
+  __shared__ float pcs[kChunk];
+  const long long e = blockIdx.x / n_rt;
+  const int k = (blockIdx.x % n_rt) * blockDim.x + threadIdx.x;
+  const int D = v.D;
+  const long long p = v.parent[e];
+  const bool act = k < K;
+  float zr[MAXD];
+#pragma unroll
+  for (int d = 0; d < MAXD; ++d) zr[d] = (act && d < D) ? v.z[(e * K + k) * D + d] : 0.f;
+  const float hk = act ? v.htil[e * K + k] : 0.f;
+  const float logK = logf((float)K);
+  float acc = 0.f;
+  for (int k0 = 0; k0 < K; k0 += kChunk) {
+    const int nk = min(kChunk, K - k0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kChunk * MAXD; i += blockDim.x) {
+      const int j = i / MAXD, d = i % MAXD;
+      const bool ok = j < nk && d < D;
+      pms[i] = ok ? par.pm[(p * K + k0 + j) * D + d] : 0.f;
+      pps[i] = ok ? par.pp[(p * K + k0 + j) * D + d] : 0.f;
+    }
+    for (int j = threadIdx.x; j < kChunk; j += blockDim.x) {
+      float sh = -INFINITY;
+      if (j < nk) {
+        const float wp = par.w[p * K + k0 + j];
+        if (wp > 0.f) sh = par.pc[p * K + k0 + j] + logf(wp) - v.lt[e * K + k0 + j] - logK;
+      }
+      pcs[j] = sh;
+    }
+    __syncthreads();
+    if (!act) continue;
+#pragma unroll 4
+    for (int j = 0; j < kChunk; ++j) {
+      const float c = pcs[j];
+      if (c == -INFINITY) continue;
+      float a = c + hk;
+#pragma unroll
+      for (int d = 0; d < MAXD; ++d) {
+        const float t = zr[d] - pms[j * MAXD + d];
+        a = fmaf(pps[j * MAXD + d], t * t, a);
+      }
+      acc += expf(a);
+    }
+  }
+  if (act) v.w[e * K + k] = acc;
+}
+
+template <int MAXD>
+static cudaError_t adj_simt_dispatch(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
+  const int thr = K >= kRowTile ? kRowTile : ((K + 31) / 32) * 32;
+  const int n_rt = (K + thr - 1) / thr;
+  k_adj_simt<MAXD><<<(unsigned)(v.n * n_rt), thr, 0, s>>>(v, par, K, n_rt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_simt(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  if (v.D <= 4) return adj_simt_dispatch<4>(v, par, K, s);
+  if (v.D <= 8) return adj_simt_dispatch<8>(v, par, K, s);
+  if (v.D <= 20) return adj_simt_dispatch<20>(v, par, K, s);
+  if (v.D <= 32) return adj_simt_dispatch<32>(v, par, K, s);
+  return adj_simt_dispatch<64>(v, par, K, s);
+}
+
+// ---------------------------------------------------------------------------
+// K6: moments m_e = sum_k w_e[k] T(z_e^k) (Eq. momone(z)), FP64 accumulation
+// in a fixed order.  Thread t of a block owns dimension t % D; consecutive
+// threads read consecutive floats of z.
+__global__ void k_moments(LevelView v, int K, double* mom) {
+  extern __shared__ double smd[];
+  const long long e = blockIdx.x;
+  const int D = v.D;
+  const int per = blockDim.x / D;
+  const int t = threadIdx.x;
+  double a0 = 0.0, a1 = 0.0;
+  if (t < per * D) {
+    const int d = t % D;
+    for (int k = t / D; k < K; k += per) {
+      const double wk = v.w[e * K + k];
+      const double zv = v.z[(e * K + k) * D + d];
+      if (v.qfam == QEM_Q_GAUSS) {
+        a0 += wk * zv;
+        a1 += wk * zv * zv;
+      } else if (v.qfam == QEM_Q_GAMMA) {
+        a0 += wk * zv;
+        a1 += wk * log(zv);
+      } else {
+        a0 += wk * log(zv);
+        a1 += wk * log1p(-zv);
+      }
+    }
+  }
+  smd[2 * t] = a0;
+  smd[2 * t + 1] = a1;
+  __syncthreads();
+  if (t < D) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int j = 0; j < per; ++j) {
+      s0 += smd[2 * (j * D + t)];
+      s1 += smd[2 * (j * D + t) + 1];
+    }
+    mom[(e * 2) * D + t] = s0;
+    mom[(e * 2 + 1) * D + t] = s1;
+  }
+}
+
+cudaError_t launch_moments(const LevelView& v, int K, double* mom, cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  const int per = 256 / v.D > 0 ? 256 / v.D : 1;
+  const int thr = per * v.D;
+  k_moments<<<(unsigned)v.n, thr, sizeof(double) * 2 * thr, s>>>(v, K, mom);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Special functions for the Gamma/Beta M-steps: digamma and trigamma from
+// their recurrences (psi(x) = psi(x+1) - 1/x, psi'(x) = psi'(x+1) + 1/x^2)
+// and asymptotic expansions in 1/x^2 with Bernoulli-number coefficients.
+__device__ double dev_digamma(double x) {
+  double r = 0.0;
+  for (; x < 8.0; x += 1.0) r -= 1.0 / x;
+  const double x2 = 1.0 / (x * x);
+  // -sum B_2n/(2n x^2n): B2/2=1/12, B4/4=-1/120, B6/6=1/252, B8/8=-1/240, B10/10=1/132, B12/12=-691/32760
+  const double ser = x2 * (1.0 / 12 - x2 * (1.0 / 120 - x2 * (1.0 / 252 - x2 * (1.0 / 240 - x2 * (1.0 / 132 - x2 * (691.0 / 32760))))));
+  return r + log(x) - 0.5 / x - ser;
+}
+
+__device__ double dev_trigamma(double x) {
+  double r = 0.0;
+  for (; x < 8.0; x += 1.0) r += 1.0 / (x * x);
+  const double x2 = 1.0 / (x * x);
+  // 1/x + 1/(2x^2) + sum B_2n / x^(2n+1)
+  const double ser = (x2 / x) * (1.0 / 6 - x2 * (1.0 / 30 - x2 * (1.0 / 42 - x2 * (1.0 / 30 - x2 * (5.0 / 66 - x2 * (691.0 / 2730))))));
+  return r + 1.0 / x + 0.5 * x2 + ser;
+}
+
+// K7: EMA of the mean parameters and the moment-matching M-step (Alg. 1,
+// Eq. ema, App. B): Gaussian mean/variance from (E z, E z^2) with a floor;
+// Gamma shape from log a - psi(a) = log E z - E log z (Newton from Minka's
+// closed-form start), rate = a / E z; Beta from psi(a) - psi(a+b) = E log z,
+// psi(b) - psi(a+b) = E log(1-z) (2-D Newton).
+__global__ void k_mstep(LevelView v, const double* __restrict__ mom, double* m, float* q, double lambda,
+                        double sched_p, double var_floor, long long t_host, const Ctl* ctl) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int D = v.D;
+  if (i >= v.n * D) return;
+  const long long e = i / D;
+  const int d = (int)(i % D);
+  const long long i0 = (e * 2) * D + d, i1 = (e * 2 + 1) * D + d;
+  double m0 = m[i0], m1 = m[i1];
+  if (mom) {
+    const double tt = (double)(t_host > 0 ? t_host : ctl->t);
+    const double lam = sched_p > 0.0 ? pow(tt, -sched_p) : lambda;
+    m0 = (1.0 - lam) * m0 + lam * mom[i0];
+    m1 = (1.0 - lam) * m1 + lam * mom[i1];
+    m[i0] = m0;
+    m[i1] = m1;
+  }
+  double qa, qb;
+  if (v.qfam == QEM_Q_GAUSS) {
+    double var = m1 - m0 * m0;
+    const double fl = var_floor * fmax(1.0, m0 * m0);
+    if (!(var > fl)) var = fl;
+    qa = m0;
+    qb = sqrt(var);
+  } else if (v.qfam == QEM_Q_GAMMA) {
+    const double s = log(m0) - m1;
+    double a = (3.0 - s + sqrt((s - 3.0) * (s - 3.0) + 24.0 * s)) / (12.0 * s);
+    for (int it = 0; it < 64; ++it) {
+      const double step = (log(a) - dev_digamma(a) - s) / (1.0 / a - dev_trigamma(a));
+      double an = a - step;
+      if (an <= 0.0) an = 0.5 * a;
+      const bool done = fabs(an - a) <= 1e-15 * a;
+      a = an;
+      if (done) break;
+    }
+    qa = a;
+    qb = a / m0;
+  } else {
+    const double A = exp(m0), B = exp(m1);
+    const double h = 0.5 / (1.0 - A - B);
+    double a = 0.5 + A * h, b = 0.5 + B * h;
+    for (int it = 0; it < 128; ++it) {
+      const double ps = dev_digamma(a + b), ts = dev_trigamma(a + b);
+      const double g1 = dev_digamma(a) - ps - m0, g2 = dev_digamma(b) - ps - m1;
+      const double h11 = dev_trigamma(a) - ts, h22 = dev_trigamma(b) - ts, h12 = -ts;
+      const double det = h11 * h22 - h12 * h12;
+      double da = (h22 * g1 - h12 * g2) / det, db = (h11 * g2 - h12 * g1) / det;
+      while (a - da <= 0.0 || b - db <= 0.0) {
+        da *= 0.5;
+        db *= 0.5;
+      }
+      const double rel = fabs(da) / a + fabs(db) / b;
+      a -= da;
+      b -= db;
+      if (rel < 1e-15) break;
+    }
+    qa = a;
+    qb = b;
+  }
+  q[i0] = (float)qa;
+  q[i1] = (float)qb;
+}
+
+cudaError_t launch_mstep(const LevelView& v, const double* mom, double* m, float* q, double lambda, double sched_p,
+                         double var_floor, long long t_host, const Ctl* ctl, cudaStream_t s) {
+  const long long tot = v.n * v.D;
+  if (tot == 0) return cudaSuccess;
+  k_mstep<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(v, mom, m, q, lambda, sched_p, var_floor, t_host, ctl);
+  return cudaGetLastError();
+}
+
+// Mean parameters of proposal parameters (Alg. 1's m_0; App. E's m = (mu, mu^2 + sigma^2)).
+__global__ void k_mean_params(LevelView v, const float* __restrict__ q, double* m) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int D = v.D;
+  if (i >= v.n * D) return;
+  const long long e = i / D;
+  const int d = (int)(i % D);
+  const long long i0 = (e * 2) * D + d, i1 = (e * 2 + 1) * D + d;
+  const double a = q[i0], b = q[i1];
+  if (v.qfam == QEM_Q_GAUSS) {
+    m[i0] = a;
+    m[i1] = a * a + b * b;
+  } else if (v.qfam == QEM_Q_GAMMA) {
+    m[i0] = a / b;
+    m[i1] = dev_digamma(a) - log(b);
+  } else {
+    m[i0] = dev_digamma(a) - dev_digamma(a + b);
+    m[i1] = dev_digamma(b) - dev_digamma(a + b);
+  }
+}
+
+cudaError_t launch_mean_params(const LevelView& v, const float* q, double* m, cudaStream_t s) {
+  const long long tot = v.n * v.D;
+  if (tot == 0) return cudaSuccess;
+  k_mean_params<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(v, q, m);
+  return cudaGetLastError();
+}
+
+}  // namespace qem

@@ -1,0 +1,19 @@
+// Tensor-core (tcgen05) contraction path of libqem: plan-time reservation of
+// the operand buffers and the forward / adjoint launches for one level.
+#pragma once
+
+#include "qem_internal.cuh"
+
+namespace qem {
+
+// Bytes of workspace the tensor-core path needs (base == nullptr: size only;
+// otherwise carve the buffers from base).
+qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base, size_t* bytes);
+// One-time set-up after the workspace exists (kernel attributes, constant operands).
+qem_status tc_plan_init(qem_plan_t P, const qem_model_desc* desc);
+void tc_plan_release(qem_plan_t P);
+// Forward contraction of level l (l >= 1) into lv[l].lt, and its adjoint into lv[l].w.
+cudaError_t tc_forward(qem_plan_t P, int l);
+cudaError_t tc_adjoint(qem_plan_t P, int l);
+
+}  // namespace qem

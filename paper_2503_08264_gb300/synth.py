@@ -140,7 +140,7 @@ def batched_three_level(n_inst: int = 256, D: int = 8, seed: int = 0,
     z_u ~ N(z_g, unit_var I); n_obs obs y ~ Poisson(exp(w.z_u)), w ~ N(0, I/D).
     """
     rng = np.random.default_rng(seed)
-    G = rng.integers(groups[0], groups[1] + 1, size=n_inst)
+    G = rng.integers(groups[0], groups[1] + 1, size=n_inst)       # may be 0: an empty plate
     gpar = np.repeat(np.arange(n_inst, dtype=np.int64), G)
     U = rng.integers(units[0], units[1] + 1, size=int(G.sum()))
     upar = np.repeat(np.arange(int(G.sum()), dtype=np.int64), U)
