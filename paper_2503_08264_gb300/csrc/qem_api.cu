@@ -238,6 +238,7 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
       lv.child_off = has_children ? cv.take<long long>((size_t)d.n + 1) : nullptr;
       lv.z = cv.take<float>(nK * d.dim);
       lv.loc = cv.take<float>(nK);
+      lv.cst = cv.take<double>((size_t)d.n);
       lv.htil = has_children ? cv.take<float>(nK) : lv.loc;
       lv.hsum = has_children ? cv.take<double>(nK) : nullptr;
       lv.off = has_children ? cv.take<double>((size_t)d.n) : nullptr;

@@ -45,7 +45,8 @@ struct LevelView {
   const long long* child_off;  // [n+1] offsets of children at level+1 (if any)
   // workspace
   float* z;           // [n][K][D]
-  float* loc;         // [n][K]  log lik - log q (+ log prior at level 0)
+  float* loc;         // [n][K]  sample-dependent part of log lik - log q (+ log prior at level 0)
+  double* cst;        // [n]     sample-independent part of the same (normalisers, lgamma(y+1), ...)
   float* htil;        // [n][K]  loc + children's sum - off  (relative local factor)
   double* hsum;       // [n][K]  sum over children of their log mean-exp (FP64)
   double* off;        // [n]     constant removed from htil

@@ -81,27 +81,66 @@ __device__ __forceinline__ float softplusf(float s) { return fmaxf(s, 0.f) + log
 __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, int K, const float* __restrict__ q,
                                                                   const float* __restrict__ eps, const Ctl* ctl) {
   extern __shared__ float sm[];
+  __shared__ double cred[kSampleThreads / 32];
+  __shared__ float fred[kSampleThreads / 32];
+  __shared__ double cst_sh;
   const long long e = blockIdx.x;
   const int D = v.D, nobs = v.n_obs, zs_stride = D + 1;
   float* xs = sm;                       // [nobs][D]
   float* ys = xs + nobs * D;            // [nobs]
-  float* qs = ys + nobs;                // [2][D]
+  float* s0s = ys + nobs;               // [nobs] reference point of the Poisson-log term
+  float* ey0s = s0s + nobs;             // [nobs] exp(s0)
+  float* qs = ey0s + nobs;              // [2][D]
   float* zs = qs + 2 * D;               // [blockDim][D+1]
   for (int i = threadIdx.x; i < nobs * D; i += blockDim.x) xs[i] = v.x[e * nobs * D + i];
-  for (int i = threadIdx.x; i < nobs; i += blockDim.x) ys[i] = v.y[e * nobs + i];
   for (int i = threadIdx.x; i < 2 * D; i += blockDim.x) qs[i] = q[e * 2 * D + i];
+  // Sample-independent part of the element's local factor, in FP64:
+  // likelihood normalisers, lgamma(y+1) and the Poisson reference terms.
+  double c = 0.0;
+  for (int n = threadIdx.x; n < nobs; n += blockDim.x) {
+    const float yv = v.y[e * nobs + n];
+    ys[n] = yv;
+    switch (v.lik) {
+      case QEM_LIK_GAUSS: c += -0.5 * log(2.0 * 3.141592653589793 * (double)v.lik_var); break;
+      case QEM_LIK_POISSON_LOG: {
+        // y s - e^s = [y s0 - e^s0] + y (s - s0) - e^s0 expm1(s - s0), s0 = log max(y, 1)
+        const float s0 = logf(fmaxf(yv, 1.f));
+        const double ey0 = exp((double)s0);
+        s0s[n] = s0;
+        ey0s[n] = (float)ey0;
+        c += (double)yv * s0 - ey0 - lgamma((double)yv + 1.0);
+        break;
+      }
+      case QEM_LIK_POISSON_RATE: c += -lgamma((double)yv + 1.0); break;
+      default: break;
+    }
+  }
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) cred[threadIdx.x >> 5] = c;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += cred[j];
+    if (v.qfam == QEM_Q_GAUSS) {  // -log q normaliser: sum log sigma + D/2 log 2 pi
+      for (int d = 0; d < D; ++d) t += log((double)qs[D + d]);
+      t += 0.5 * D * kLog2PiD;
+    }
+    if (v.level == 0) {
+      const double a0 = v.prior_a, b0 = v.prior_b;
+      if (v.prior == QEM_PRIOR_STD_NORMAL) t += -0.5 * D * log(2.0 * 3.141592653589793 * a0);
+      if (v.prior == QEM_PRIOR_GAMMA) t += D * (a0 * log(b0) - lgamma(a0));
+      if (v.prior == QEM_PRIOR_BETA) t += -D * (lgamma(a0) + lgamma(b0) - lgamma(a0 + b0));
+    }
+    cst_sh = t;
+  }
   const unsigned long long seed = ctl->seed, iter = ctl->iter;
-  float sum_log_scale = 0.f;
-  if (v.qfam == QEM_Q_GAUSS)
-    for (int d = 0; d < D; ++d) sum_log_scale += logf(qs[D + d]);
 
   for (int k0 = 0; k0 < K; k0 += blockDim.x) {
     const int nk = min((int)blockDim.x, K - k0);
     const int k = k0 + threadIdx.x;
     const bool act = threadIdx.x < nk;
     float* zr = zs + threadIdx.x * zs_stride;
-    float lq = 0.f;
+    float lq = 0.f;  // sample-dependent part of log q
     if (v.qfam == QEM_Q_GAUSS) {
       // noise -> zs (coalesced when supplied)
       if (eps) {
@@ -125,7 +164,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
           ss = fmaf(ep, ep, ss);
           zr[d] = fmaf(qs[D + d], ep, qs[d]);
         }
-        lq = -0.5f * ss - sum_log_scale - 0.5f * D * kLog2Pi;
+        lq = -0.5f * ss;
       }
     } else if (act) {
       const unsigned long long sample = (unsigned long long)e * K + k;
@@ -157,12 +196,16 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
         switch (v.lik) {
           case QEM_LIK_GAUSS: {
             const float r = yv - s;
-            ll += -0.5f * logf(2.f * 3.14159265358979f * v.lik_var) - r * r / (2.f * v.lik_var);
+            ll += -r * r / (2.f * v.lik_var);
             break;
           }
           case QEM_LIK_BERNOULLI_LOGIT: ll += yv * s - softplusf(s); break;
-          case QEM_LIK_POISSON_LOG: ll += yv * s - expf(s) - lgammaf(yv + 1.f); break;
-          case QEM_LIK_POISSON_RATE: ll += yv * logf(zr[0]) - zr[0] - lgammaf(yv + 1.f); break;
+          case QEM_LIK_POISSON_LOG: {
+            const float dl = s - s0s[n];
+            ll += yv * dl - ey0s[n] * expm1f(dl);
+            break;
+          }
+          case QEM_LIK_POISSON_RATE: ll += yv * logf(zr[0]) - zr[0]; break;
           case QEM_LIK_BERNOULLI_PROB: ll += yv * logf(zr[0]) + (1.f - yv) * log1pf(-zr[0]); break;
           default: break;
         }
@@ -173,23 +216,20 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
           case QEM_PRIOR_STD_NORMAL: {
             float ss = 0.f;
             for (int d = 0; d < D; ++d) ss = fmaf(zr[d], zr[d], ss);
-            lp = -0.5f * ss / v.prior_a - 0.5f * D * logf(2.f * 3.14159265358979f * v.prior_a);
+            lp = -0.5f * ss / v.prior_a;
             break;
           }
           case QEM_PRIOR_GAMMA: {
             const double a0 = v.prior_a, b0 = v.prior_b;
             double acc = 0.0;
-            for (int d = 0; d < D; ++d)
-              acc += a0 * log(b0) - lgamma(a0) + (a0 - 1.0) * log((double)zr[d]) - b0 * zr[d];
+            for (int d = 0; d < D; ++d) acc += (a0 - 1.0) * log((double)zr[d]) - b0 * zr[d];
             lp = (float)acc;
             break;
           }
           case QEM_PRIOR_BETA: {
             const double a0 = v.prior_a, b0 = v.prior_b;
             double acc = 0.0;
-            for (int d = 0; d < D; ++d)
-              acc += (a0 - 1.0) * log((double)zr[d]) + (b0 - 1.0) * log1p(-(double)zr[d]) -
-                     (lgamma(a0) + lgamma(b0) - lgamma(a0 + b0));
+            for (int d = 0; d < D; ++d) acc += (a0 - 1.0) * log((double)zr[d]) + (b0 - 1.0) * log1p(-(double)zr[d]);
             lp = (float)acc;
             break;
           }
@@ -204,10 +244,23 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
     for (int i = threadIdx.x; i < nk * D; i += blockDim.x) dst[i] = zs[(i / D) * zs_stride + (i % D)];
     __syncthreads();
   }
+  // Centre the element's sample-dependent factor on its maximum (the offset
+  // joins the FP64 constant), so every later FP32 step works near zero for
+  // the samples that carry weight.
+  float mx = -INFINITY;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmaxf(mx, v.loc[e * K + k]);
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) fred[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  float cmax = -INFINITY;
+  for (int j = 0; j < (int)(blockDim.x >> 5); ++j) cmax = fmaxf(cmax, fred[j]);
+  if (!isfinite(cmax)) cmax = 0.f;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) v.loc[e * K + k] -= cmax;
+  if (threadIdx.x == 0) v.cst[e] = cst_sh + (double)cmax;
 }
 
 size_t sample_local_smem(const LevelView& v) {
-  return sizeof(float) * (size_t)(v.n_obs * v.D + v.n_obs + 2 * v.D + kSampleThreads * (v.D + 1));
+  return sizeof(float) * (size_t)(v.n_obs * v.D + 3 * v.n_obs + 2 * v.D + kSampleThreads * (v.D + 1));
 }
 
 cudaError_t configure_sample_local(size_t smem) {
@@ -261,13 +314,14 @@ cudaError_t launch_parent_params(const LevelView& parent, const LevelView& child
 
 // ---------------------------------------------------------------------------
 // Relative local factor of an element with children: htil = loc + H - c,
-// c = max_k H[k] kept in FP64 (off), so the FP32 contraction sees values of
-// moderate size; c re-enters at the parent's plate sum.
+// c = max_k (loc + H)[k] kept in FP64 (off), so the FP32 contraction sees
+// values near zero for the samples that matter; c re-enters at the parent's
+// plate sum.
 __global__ void k_finalize(LevelView v, int K) {
   const long long e = blockIdx.x;
   __shared__ double red[32];
   double mx = -INFINITY;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, v.hsum[e * K + k]);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, (double)v.loc[e * K + k] + v.hsum[e * K + k]);
   for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
@@ -334,7 +388,7 @@ __global__ void __launch_bounds__(kRowTile) k_fwd_simt(LevelView v, LevelView pa
     for (int j = 0; j < kChunk; ++j) {
       float a = -INFINITY;
       if (j < nk) {
-        a = pc + hs[j];
+        a = hs[j];
 #pragma unroll
         for (int d = 0; d < MAXD; ++d) {
           const float t = zs[j * MAXD + d] - pm[d];
@@ -352,7 +406,7 @@ __global__ void __launch_bounds__(kRowTile) k_fwd_simt(LevelView v, LevelView pa
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) s += expf(val[j] - m);
   }
-  if (act) v.lt[e * K + kp] = m + logf(s) - logf((float)K);
+  if (act) v.lt[e * K + kp] = pc + (m + logf(s) - logf((float)K));
 }
 
 template <int MAXD>
@@ -385,7 +439,7 @@ __global__ void k_plate_sum(LevelView par, LevelView ch, int K) {
   double acc = 0.0;
   if (kp < K) {
     for (long long c = c0 + threadIdx.y; c < c1; c += 8)
-      acc += (double)ch.lt[c * K + kp] + (ch.off ? ch.off[c] : 0.0);
+      acc += (double)ch.lt[c * K + kp] + (ch.off ? ch.off[c] : 0.0) + ch.cst[c];
   }
   red[threadIdx.y][threadIdx.x] = acc;
   __syncthreads();
@@ -413,7 +467,7 @@ __global__ void k_root(LevelView v, int K, int has_children, double* log_pmp, do
   __shared__ double red[32];
   __shared__ double bc;
   auto a_of = [&](int k) -> double {
-    return (double)v.loc[i * K + k] + (has_children ? v.hsum[i * K + k] : 0.0);
+    return (double)v.loc[i * K + k] + v.cst[i] + (has_children ? v.hsum[i * K + k] : 0.0);
   };
   double mx = -INFINITY;
   for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, a_of(k));
