@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the QEM E-step hot path (arXiv 2503.08264) on GB300.
+
+One step = one iteration of Alg. 1 on the device: E-step (sample, local
+factors, K x K forward contraction, plate sums, root, adjoint, moments) then
+EMA + M-step, on a seeded synthetic workload.  The metric is E-step
+log-factor pairs per second, pairs = sum over non-root plate elements of
+K_parent * K_child.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload NAME] [--precision P]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
+
+Under torchrun (N > 1) every rank runs an independent instance of the
+workload (weak scaling, no collective on the data path); rank 0 prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2503_08264_gb300 import synth as S  # noqa: E402
+
+METRIC = "E-step K^2 x plate-elt log-factor pairs/s"
+UNIT = "pairs/s"
+
+# workload name -> (builder(seed), K, default precision)
+WORKLOADS = {
+    "hier_logistic_M5000_N10_K1024": (lambda seed: S.hier_logistic(M=5000, N=10, seed=seed), 1024, "fp32"),
+    "hier_logistic_M300_N5_K128": (lambda seed: S.hier_logistic(M=300, N=5, seed=seed), 128, "fp32"),
+    "batched_three_level_256_K256": (lambda seed: S.batched_three_level(n_inst=256, seed=seed), 256, "fp32"),
+}
+DEFAULT_WORKLOAD = "hier_logistic_M5000_N10_K1024"
+EMA_LAMBDA = 0.5
+
+
+def parse(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    p.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return p.parse_args(argv)
+
+
+# --------------------------------------------------------------------------- distributed helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return ws, rank, local
+
+
+def dist_init(ws: int, backend: str):
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(local_ms: float, local_units: float, ws: int, device=None):
+    """(max over ranks of the timed milliseconds, sum over ranks of the units)."""
+    if ws == 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="qem_clocks_", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for ln in f:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- roofline
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# Binding-unit model of each contraction path (per log-factor pair of one
+# launch): FP32 CUDA-core path = FP32 pipe (128 lanes/clk/SM), tensor-core
+# path = MUFU ex2 (1 exponential per pair; 32 per clk per SM on GB300).
+SMS = 152
+
+
+def roofline_for(kind: str, precision: str, D: int, pairs: float, ms: float, sm_max_mhz: float):
+    clk = (sm_max_mhz or 2070.0) * 1e6
+    if precision == "fp32":
+        ops_per_pair = 3 * D + 4          # (z-m), ^2, fma per dim; shift, exp, accumulate, max
+        peak = SMS * 128 * clk / ops_per_pair
+        model = f"FP32 pipe: {ops_per_pair} lane-ops/pair, 128 lanes/clk/SM x {SMS} SMs x {clk / 1e6:.0f} MHz"
+    else:
+        peak = SMS * 32 * clk
+        model = f"MUFU ex2: 1/pair, 32/clk/SM x {SMS} SMs x {clk / 1e6:.0f} MHz"
+    achieved = pairs / (ms * 1e-3)
+    return {"bound": "alu", "kernel": kind, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+            "frac": achieved / peak, "traffic": None, "model": model + " (derived from unit counts and max clock)"}
+
+
+# --------------------------------------------------------------------------- CPU oracle baseline
+def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7):
+    """Time the FP64 oracle E-step on a bounded sample of the workload (all host cores).
+
+    The sample keeps the workload's shapes (K, dimensions, observations per
+    element) and takes a prefix of its plate elements (2-level workloads) or a
+    smaller batch of instances (batched workloads), sized from a short
+    calibration run so that the timed run takes about target_s seconds."""
+    import numpy as np
+    from oracle import oracle as O
+    O.build()
+    builder, K, _ = WORKLOADS[workload]
+    full = builder(seed)
+    two_level = len(full.levels) == 2
+    total = full.levels[1].n if two_level else full.n_inst
+
+    def sub(count):
+        count = int(max(1, min(total, count)))
+        if two_level:
+            lv = full.levels[1]
+            users = S.Level(n=count, dim=lv.dim, prior=lv.prior, prior_a=lv.prior_a, lik=lv.lik,
+                            lik_var=lv.lik_var, n_obs=lv.n_obs, qfam=lv.qfam,
+                            parent=np.zeros(count, np.int64), x=lv.x[:count], y=lv.y[:count])
+            return S.Model([full.levels[0], users]), f"{count} of {total} plate elements"
+        return S.batched_three_level(n_inst=count, seed=seed), f"{count} of {total} instances"
+
+    calib = 4 if two_level else 1
+    model, _ = sub(calib)
+    t0 = time.perf_counter()
+    O.estep(model, S.initial_q(model), K, seed=1, it=1)
+    t = max(time.perf_counter() - t0, 1e-3)
+    model, desc = sub(calib * target_s / t)
+    t0 = time.perf_counter()
+    O.estep(model, S.initial_q(model), K, seed=1, it=1)
+    t = time.perf_counter() - t0
+    pairs = model.pairs(K)
+    return {"value": pairs / t, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"one FP64 E-step on {desc} of {workload} (counter-based noise), {t:.1f} s"}, model
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    builder, K, _ = WORKLOADS[args.workload]
+    # size one step's sample so that warmup + steps fit in about three minutes
+    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    base, model = cpu_oracle_sample(args.workload, per_step)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.estep(model, S.initial_q(model), K, seed=1, it=i + 1)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    pairs = model.pairs(K)
+    value = pairs * len(times) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "K": K, "sample": base["sample"]},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(ws, "nccl")
+    from paper_2503_08264_gb300 import qem  # fails loudly when libqem.so is missing
+
+    builder, K, default_prec = WORKLOADS[args.workload]
+    precision = args.precision or default_prec
+    model = builder(1000 + rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan = qem.Plan(model, K, precision=precision, stream=stream)
+        q0 = S.initial_q(model)
+        q_d = plan.flat(q0)
+        m_d = plan.mean_params(q_d)
+        mom_d = torch.empty(plan.q_len, dtype=torch.float64, device="cuda")
+        lp_d = torch.empty(plan.n_inst, dtype=torch.float64, device="cuda")
+    pairs = float(model.pairs(K))
+    seed = 12345 + rank
+
+    def step(t):
+        plan.estep(q_d, None, seed=seed, it=t, moments=mom_d, log_pmp=lp_d)
+        plan.mstep(mom_d, m_d, q_d, EMA_LAMBDA, t=t)
+
+    t_iter = 1
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(t_iter)
+            t_iter += 1
+    stream.synchronize()
+    plan.log_pmp()  # raises on a non-finite estimate or a device error
+    barrier(ws)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    plan.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(t_iter)
+            t_iter += 1
+        ev1.record(stream)
+    stream.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    local_ms = ev0.elapsed_time(ev1)
+    prof = plan.profile_read()
+    plan.profile(False)
+    lp_host = plan.log_pmp()
+    max_ms, tot_pairs = aggregate(local_ms, pairs * args.steps, ws, device="cuda")
+    value = tot_pairs / (max_ms * 1e-3)
+
+    # dominant kernel and its roofline (CUDA events on the plan's stream)
+    kind = max(prof, key=lambda k: prof[k][0])
+    k_ms, k_n = prof[kind]
+    gpu_launches = int(sum(n for _, n in prof.values()))
+    sm_max = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    D_child = model.levels[-1].dim
+    pairs_per_launch = pairs / max(1, (len(model.levels) - 1))
+    if kind in ("forward", "adjoint"):
+        roof = roofline_for(kind, precision, D_child, pairs_per_launch * k_n, k_ms, sm_max)
+    else:
+        roof = {"bound": "hbm", "kernel": kind, "achieved": None, "peak": measured_peaks().get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None}
+    roof["share_of_step"] = k_ms / local_ms if local_ms else None
+
+    # end to end through the C ABI with host buffers: the step's inputs are
+    # copied from pinned host memory each step and its results read back
+    e2e = None
+    if not args.no_e2e:
+        host_in = [t.cpu().pin_memory() for t in plan._keep if isinstance(t, torch.Tensor)]
+        dev_in = [t for t in plan._keep if isinstance(t, torch.Tensor)]
+        m_host = m_d.cpu().pin_memory()
+        mom_host = torch.empty_like(mom_d, device="cpu").pin_memory()
+        lp_host_t = torch.empty_like(lp_d, device="cpu").pin_memory()
+        m_back = torch.empty_like(m_d, device="cpu").pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host_in) + m_host.numel() * 8
+        d2h = mom_host.numel() * 8 + lp_host_t.numel() * 8 + m_back.numel() * 8
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                for h, d in zip(host_in, dev_in):
+                    d.copy_(h, non_blocking=True)
+                m_d.copy_(m_host, non_blocking=True)
+                plan.mstep(None, m_d, q_d, EMA_LAMBDA, t=t_iter)
+                step(t_iter)
+                t_iter += 1
+                mom_host.copy_(mom_d, non_blocking=True)
+                lp_host_t.copy_(lp_d, non_blocking=True)
+                m_back.copy_(m_d, non_blocking=True)
+            e1.record(stream)
+        stream.synchronize()
+        barrier(ws)
+        e_ms, e_pairs = aggregate(e0.elapsed_time(e1), pairs * args.steps, ws, device="cuda")
+        e2e = {"value": e_pairs / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if ws == 1 and rank == 0 and not args.no_cpu_baseline:
+        cpu, _ = cpu_oracle_sample(args.workload, args.cpu_seconds)
+
+    if rank == 0:
+        ws_bytes = plan.workspace_bytes
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16",
+                                                                   "bf16x3": "bf16x3"}[precision],
+                "data": "synthetic",
+                "config": {"workload": args.workload, "K": K, "pairs_per_step_per_gpu": pairs,
+                           "precision": precision, "noise": "in-kernel Philox4x32-10",
+                           "step": "qem_estep + qem_mstep (one Alg. 1 iteration)",
+                           "l2": f"working set {ws_bytes / 1e9:.2f} GB > 129 MB L2 (no flush)",
+                           "parallelism": f"replicas x{ws} (independent instances)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "clocks": clk, "kernels_ms": {k: round(v[0], 4) for k, v in prof.items()},
+                "log_pmp_last": float(lp_host[0])}
+        print(json.dumps(line))
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

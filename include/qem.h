@@ -196,6 +196,34 @@ qem_status qem_samples(qem_plan_t plan, float* z);
 qem_status qem_run(qem_plan_t plan, int64_t T, double lambda, double sched_p, uint64_t seed,
                    double* mean_params, float* q_params, double* moments, double* log_pmp_trace);
 
+/* Kernel classes of the per-kernel profiler. */
+enum {
+  QEM_K_SAMPLE = 0,      /* sampling and local factors                 */
+  QEM_K_PARENT = 1,      /* conditional parameters of children         */
+  QEM_K_FINALIZE = 2,    /* relative local factors of inner levels     */
+  QEM_K_FORWARD = 3,     /* forward K x K contraction                  */
+  QEM_K_PLATE_SUM = 4,   /* FP64 plate sums                            */
+  QEM_K_ROOT = 5,        /* root log P_MP and weights                  */
+  QEM_K_ADJOINT = 6,     /* adjoint K x K contraction (marginals)      */
+  QEM_K_MOMENTS = 7,     /* moments                                    */
+  QEM_K_MSTEP = 8,       /* EMA + M-step                               */
+  QEM_K_COUNT = 9
+};
+
+/* Per-kernel timing (tracing support, not part of the method): while enabled,
+ * every kernel the plan launches from qem_estep / qem_mstep is bracketed by
+ * CUDA events on the plan's stream.  on = 1 clears previous records and
+ * enables; on = 0 disables (records are kept).  qem_run is never profiled. */
+qem_status qem_profile_enable(qem_plan_t plan, int on);
+
+/* Accumulated device time (ms) and launch count of kernel class `kind`
+ * (QEM_K_*) over the records since the last enable.  Synchronises the plan's
+ * stream.  Either output pointer (HOST) may be NULL.                       */
+qem_status qem_profile_read(qem_plan_t plan, int kind, double* ms, int64_t* launches);
+
+/* Name of a kernel class (static storage), or NULL for an invalid class. */
+const char* qem_profile_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

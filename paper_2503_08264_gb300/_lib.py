@@ -55,7 +55,13 @@ SIGNATURES = {
     "qem_samples": (C.c_int, [C.c_void_p, C.c_void_p]),
     "qem_run": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_uint64, C.c_void_p, C.c_void_p,
                           C.c_void_p, C.c_void_p]),
+    "qem_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "qem_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "qem_profile_name": (C.c_char_p, [C.c_int]),
 }
+
+QEM_K_NAMES = ["sample_local", "parent_params", "finalize", "forward", "plate_sum", "root", "adjoint", "moments",
+               "mstep"]
 
 _lib = None
 

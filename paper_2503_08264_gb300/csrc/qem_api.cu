@@ -89,12 +89,49 @@ qem_status validate(const qem_model_desc* desc, const qem_plan_opts* o) {
   return QEM_OK;
 }
 
-qem_status from_cuda(cudaError_t e) { return e == cudaSuccess ? QEM_OK : QEM_ERR_CUDA; }
-
 #define QEM_TRY(expr)                          \
   do {                                         \
     cudaError_t _e = (expr);                   \
     if (_e != cudaSuccess) return QEM_ERR_CUDA; \
+  } while (0)
+
+// Per-kernel CUDA-event records of a plan (qem_profile_*).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  cudaEvent_t get() {
+    if (next == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[next++];
+  }
+  ~Prof() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+inline Prof* prof_of(qem_plan_t P) { return static_cast<Prof*>(P->prof); }
+
+// Launch `expr` (a cudaError_t expression), bracketed by events when profiling.
+#define QEM_LAUNCH(P, kind, expr)                                          \
+  do {                                                                     \
+    Prof* _pf = prof_of(P);                                                \
+    cudaEvent_t _a = nullptr, _b = nullptr;                                \
+    if (_pf && _pf->on) {                                                  \
+      _a = _pf->get();                                                     \
+      _b = _pf->get();                                                     \
+      if (_a) cudaEventRecord(_a, (P)->stream);                            \
+    }                                                                      \
+    QEM_TRY(expr);                                                         \
+    if (_a && _b) {                                                        \
+      cudaEventRecord(_b, (P)->stream);                                    \
+      _pf->recs.push_back({kind, _a, _b});                                 \
+    }                                                                      \
   } while (0)
 
 // The E-step body (Eq. mp_iw over the plate tree), enqueued on the plan's stream.
@@ -103,33 +140,35 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
   cudaStream_t s = P->stream;
   const int L = P->L, K = P->K;
   for (int l = 0; l < L; ++l)
-    QEM_TRY(launch_sample_local(P->lv[l], K, q + P->q_off[l], eps ? eps + P->eps_off[l] : nullptr, P->ctl, s));
-  for (int l = 0; l + 1 < L; ++l) QEM_TRY(launch_parent_params(P->lv[l], P->lv[l + 1], K, s));
+    QEM_LAUNCH(P, QEM_K_SAMPLE,
+               launch_sample_local(P->lv[l], K, q + P->q_off[l], eps ? eps + P->eps_off[l] : nullptr, P->ctl, s));
+  for (int l = 0; l + 1 < L; ++l) QEM_LAUNCH(P, QEM_K_PARENT, launch_parent_params(P->lv[l], P->lv[l + 1], K, s));
   for (int l = L - 1; l >= 1; --l) {
     const bool has_children = l + 1 < L;
-    QEM_TRY(launch_finalize(P->lv[l], K, has_children, s));
+    if (has_children) QEM_LAUNCH(P, QEM_K_FINALIZE, launch_finalize(P->lv[l], K, has_children, s));
     if (P->precision == QEM_PREC_FP32)
-      QEM_TRY(launch_fwd_simt(P->lv[l], P->lv[l - 1], K, s));
+      QEM_LAUNCH(P, QEM_K_FORWARD, launch_fwd_simt(P->lv[l], P->lv[l - 1], K, s));
     else
-      QEM_TRY(tc_forward(P, l));
-    QEM_TRY(launch_plate_sum(P->lv[l - 1], P->lv[l], K, s));
+      QEM_LAUNCH(P, QEM_K_FORWARD, tc_forward(P, l));
+    QEM_LAUNCH(P, QEM_K_PLATE_SUM, launch_plate_sum(P->lv[l - 1], P->lv[l], K, s));
   }
-  QEM_TRY(launch_root(P->lv[0], K, L > 1, P->log_pmp, user_lp, trace, P->ctl, s));
+  QEM_LAUNCH(P, QEM_K_ROOT, launch_root(P->lv[0], K, L > 1, P->log_pmp, user_lp, trace, P->ctl, s));
   for (int l = 1; l < L; ++l) {
     if (P->precision == QEM_PREC_FP32)
-      QEM_TRY(launch_adj_simt(P->lv[l], P->lv[l - 1], K, s));
+      QEM_LAUNCH(P, QEM_K_ADJOINT, launch_adj_simt(P->lv[l], P->lv[l - 1], K, s));
     else
-      QEM_TRY(tc_adjoint(P, l));
+      QEM_LAUNCH(P, QEM_K_ADJOINT, tc_adjoint(P, l));
   }
-  for (int l = 0; l < L; ++l) QEM_TRY(launch_moments(P->lv[l], K, moments + P->q_off[l], s));
+  for (int l = 0; l < L; ++l) QEM_LAUNCH(P, QEM_K_MOMENTS, launch_moments(P->lv[l], K, moments + P->q_off[l], s));
   return QEM_OK;
 }
 
 qem_status mstep_body(qem_plan_t P, const double* moments, double* m, float* q, double lambda, double sched_p,
                       long long t_host) {
   for (int l = 0; l < P->L; ++l)
-    QEM_TRY(launch_mstep(P->lv[l], moments ? moments + P->q_off[l] : nullptr, m + P->q_off[l], q + P->q_off[l],
-                         lambda, sched_p, P->var_floor, t_host, P->ctl, P->stream));
+    QEM_LAUNCH(P, QEM_K_MSTEP,
+               launch_mstep(P->lv[l], moments ? moments + P->q_off[l] : nullptr, m + P->q_off[l], q + P->q_off[l],
+                            lambda, sched_p, P->var_floor, t_host, P->ctl, P->stream));
   return QEM_OK;
 }
 
@@ -296,6 +335,7 @@ qem_status qem_plan_destroy(qem_plan_t P) {
   if (!P) return QEM_OK;
   cudaError_t e = cudaStreamSynchronize(P->stream);
   tc_plan_release(P);
+  delete prof_of(P);
   if (P->ws) cudaFree(P->ws);
   delete P;
   return e == cudaSuccess ? QEM_OK : QEM_ERR_CUDA;
@@ -387,6 +427,9 @@ qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint6
   if (!(lambda >= 0.0 && lambda <= 1.0) || !(sched_p >= 0.0 && sched_p < 1.0)) return QEM_ERR_INVALID_ARG;
   cudaStream_t s = P->stream;
   cudaStream_t own = nullptr;
+  Prof* pf = prof_of(P);
+  const bool prof_was_on = pf && pf->on;
+  if (pf) pf->on = false;
   if (s == nullptr) {  // legacy stream cannot be captured: use a private stream and finish synchronously
     if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) return QEM_ERR_CUDA;
     if (cudaDeviceSynchronize() != cudaSuccess) return QEM_ERR_CUDA;
@@ -416,7 +459,51 @@ qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint6
     cudaStreamDestroy(own);
     P->stream = nullptr;
   }
+  if (pf) pf->on = prof_was_on;
   return st;
+}
+
+static const char* kKindNames[QEM_K_COUNT] = {"sample_local", "parent_params", "finalize", "forward",
+                                              "plate_sum",    "root",          "adjoint",  "moments",
+                                              "mstep"};
+
+const char* qem_profile_name(int kind) { return kind >= 0 && kind < QEM_K_COUNT ? kKindNames[kind] : nullptr; }
+
+qem_status qem_profile_enable(qem_plan_t P, int on) {
+  if (!P) return QEM_ERR_INVALID_ARG;
+  Prof* pf = prof_of(P);
+  if (!pf) {
+    pf = new (std::nothrow) Prof();
+    if (!pf) return QEM_ERR_OOM;
+    P->prof = pf;
+  }
+  if (on) {
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEM_ERR_CUDA;
+    pf->recs.clear();
+    pf->next = 0;
+  }
+  pf->on = on != 0;
+  return QEM_OK;
+}
+
+qem_status qem_profile_read(qem_plan_t P, int kind, double* ms, int64_t* launches) {
+  if (!P || kind < 0 || kind >= QEM_K_COUNT) return QEM_ERR_INVALID_ARG;
+  Prof* pf = prof_of(P);
+  double tot = 0.0;
+  int64_t cnt = 0;
+  if (pf) {
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEM_ERR_CUDA;
+    for (const Prof::Rec& r : pf->recs) {
+      if (r.kind != kind) continue;
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return QEM_ERR_CUDA;
+      tot += t;
+      ++cnt;
+    }
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = cnt;
+  return QEM_OK;
 }
 
 }  // extern "C"

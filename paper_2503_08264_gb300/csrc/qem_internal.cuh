@@ -82,6 +82,7 @@ struct qem_plan_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   qem::TcBuffers* tc = nullptr;
+  void* prof = nullptr;        // per-kernel event records (qem_api.cu)
 };
 
 namespace qem {

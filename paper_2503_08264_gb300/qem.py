@@ -75,6 +75,21 @@ def qem_run(h, T: int, lam: float, sched_p: float, seed: int, mean_params, q_par
                              _ptr(trace)), "qem_run")
 
 
+def qem_profile_enable(h, on: bool) -> None:
+    L.check(L.load().qem_profile_enable(h, 1 if on else 0), "qem_profile_enable")
+
+
+def qem_profile_read(h, kind: int):
+    ms, n = C.c_double(), C.c_int64()
+    L.check(L.load().qem_profile_read(h, kind, C.byref(ms), C.byref(n)), "qem_profile_read")
+    return ms.value, n.value
+
+
+def qem_profile_name(kind: int) -> str:
+    r = L.load().qem_profile_name(kind)
+    return r.decode() if r else None
+
+
 # ---------------------------------------------------------------------------- owner object
 class Plan:
     """A libqem plan for one model: uploads the model's data to the device,
@@ -178,6 +193,13 @@ class Plan:
             moments = torch.empty(self.q_len, dtype=torch.float64, device=self.device)
         qem_run(self.h, T, lam, sched_p, seed, mean_params, q_params, moments, trace)
         return moments
+
+    def profile(self, on: bool = True) -> None:
+        qem_profile_enable(self.h, on)
+
+    def profile_read(self) -> dict:
+        """{kernel class: (total ms, launches)} since profiling was enabled."""
+        return {L.QEM_K_NAMES[k]: qem_profile_read(self.h, k) for k in range(len(L.QEM_K_NAMES))}
 
     def close(self):
         if getattr(self, "h", None):
