@@ -37,9 +37,9 @@ UNIT = "pairs/s"
 
 # workload name -> (builder(seed), K, default precision)
 WORKLOADS = {
-    "hier_logistic_M5000_N10_K1024": (lambda seed: S.hier_logistic(M=5000, N=10, seed=seed), 1024, "fp32"),
+    "hier_logistic_M5000_N10_K1024": (lambda seed: S.hier_logistic(M=5000, N=10, seed=seed), 1024, "bf16x3"),
     "hier_logistic_M300_N5_K128": (lambda seed: S.hier_logistic(M=300, N=5, seed=seed), 128, "fp32"),
-    "batched_three_level_256_K256": (lambda seed: S.batched_three_level(n_inst=256, seed=seed), 256, "fp32"),
+    "batched_three_level_256_K256": (lambda seed: S.batched_three_level(n_inst=256, seed=seed), 256, "bf16x3"),
 }
 DEFAULT_WORKLOAD = "hier_logistic_M5000_N10_K1024"
 EMA_LAMBDA = 0.5

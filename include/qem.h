@@ -207,7 +207,8 @@ enum {
   QEM_K_ADJOINT = 6,     /* adjoint K x K contraction (marginals)      */
   QEM_K_MOMENTS = 7,     /* moments                                    */
   QEM_K_MSTEP = 8,       /* EMA + M-step                               */
-  QEM_K_COUNT = 9
+  QEM_K_OPERANDS = 9,    /* tensor-core operand features / compaction  */
+  QEM_K_COUNT = 10
 };
 
 /* Per-kernel timing (tracing support, not part of the method): while enabled,
@@ -223,6 +224,17 @@ qem_status qem_profile_read(qem_plan_t plan, int kind, double* ms, int64_t* laun
 
 /* Name of a kernel class (static storage), or NULL for an invalid class. */
 const char* qem_profile_name(int kind);
+
+/* Diagnostic (validation of the tensor-core operand path, not part of the
+ * method): out = A * B^T computed by one tcgen05 MMA chain exactly as the
+ * contraction kernels issue it.
+ *   A    DEVICE bf16 [128 rows][fk] in the canonical K-major core-matrix
+ *        layout (element (r, c) at ((r/8)*(fk/8) + c/8)*64 + (r%8)*8 + c%8)
+ *   B    DEVICE bf16 [n rows][fk], same layout
+ *   out  DEVICE float [128][n] row-major
+ * fk in 16..128 and n in 16..256, both multiples of 16.  Synchronous on
+ * `stream`; allocates and frees a small control block.                      */
+qem_status qem_diag_tc_gemm(const void* A, const void* B, int fk, int n, float* out, void* stream);
 
 #ifdef __cplusplus
 }

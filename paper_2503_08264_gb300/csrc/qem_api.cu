@@ -146,18 +146,22 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
   for (int l = L - 1; l >= 1; --l) {
     const bool has_children = l + 1 < L;
     if (has_children) QEM_LAUNCH(P, QEM_K_FINALIZE, launch_finalize(P->lv[l], K, has_children, s));
-    if (P->precision == QEM_PREC_FP32)
+    if (P->precision == QEM_PREC_FP32) {
       QEM_LAUNCH(P, QEM_K_FORWARD, launch_fwd_simt(P->lv[l], P->lv[l - 1], K, s));
-    else
+    } else {
+      QEM_LAUNCH(P, QEM_K_OPERANDS, tc_features(P, l));
       QEM_LAUNCH(P, QEM_K_FORWARD, tc_forward(P, l));
+    }
     QEM_LAUNCH(P, QEM_K_PLATE_SUM, launch_plate_sum(P->lv[l - 1], P->lv[l], K, s));
   }
   QEM_LAUNCH(P, QEM_K_ROOT, launch_root(P->lv[0], K, L > 1, P->log_pmp, user_lp, trace, P->ctl, s));
   for (int l = 1; l < L; ++l) {
-    if (P->precision == QEM_PREC_FP32)
+    if (P->precision == QEM_PREC_FP32) {
       QEM_LAUNCH(P, QEM_K_ADJOINT, launch_adj_simt(P->lv[l], P->lv[l - 1], K, s));
-    else
+    } else {
+      QEM_LAUNCH(P, QEM_K_OPERANDS, tc_compact(P, l));
       QEM_LAUNCH(P, QEM_K_ADJOINT, tc_adjoint(P, l));
+    }
   }
   for (int l = 0; l < L; ++l) QEM_LAUNCH(P, QEM_K_MOMENTS, launch_moments(P->lv[l], K, moments + P->q_off[l], s));
   return QEM_OK;
@@ -465,7 +469,7 @@ qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint6
 
 static const char* kKindNames[QEM_K_COUNT] = {"sample_local", "parent_params", "finalize", "forward",
                                               "plate_sum",    "root",          "adjoint",  "moments",
-                                              "mstep"};
+                                              "mstep",        "operands"};
 
 const char* qem_profile_name(int kind) { return kind >= 0 && kind < QEM_K_COUNT ? kKindNames[kind] : nullptr; }
 

@@ -1,15 +1,940 @@
-// Tensor-core contraction path (placeholder until the tcgen05 kernels land).
+// Tensor-core (tcgen05) contraction path of libqem for sm_103a.
+//
+// The K_parent x K_child log-factor tile of one plate element (Eq. rmp; the
+// sum over the child index of Eq. Prmp, organised per Sec. 7) is a
+// low-rank bilinear form plus row and column terms:
+//   S[kp][k] = rowc[kp] + sum_f A[kp][f] B[k][f] + h[k].
+// The bilinear part and the column term run on the 5th-generation tensor
+// cores (BF16 operands, FP32 accumulation in TMEM); FP32 rounding is recovered
+// with a split-BF16 representation (x = hi + lo, products hi*hi + hi*lo +
+// lo*hi) and a three-way split of h.  All values are pre-scaled by log2(e) so
+// the epilogue applies ex2 directly.
+//   forward : lt[e][kp] = rowc[kp] + ln 2 * log2 sum_k 2^(A B^T + h)[kp][k] - ln K   (online max shift)
+//   adjoint : w[e][k]   = sum_kp 2^(B A^T + h + d)[k][kp],  d = log2 e (rowc + ln w_p - lt - ln K)
+// The adjoint runs over the parent samples with non-negligible weight only
+// (compacted list; the dropped terms are below 2^-60 of the largest weight).
+//
+// Operand layout: the canonical K-major no-swizzle layout of tcgen05
+// (8 x 8 bf16 core matrices of 128 contiguous bytes, core matrices of a row
+// group consecutive along K).  Features are written to global memory in that
+// layout, so every operand tile is one contiguous bulk copy.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <new>
+
 #include "qem_tc.cuh"
 
 namespace qem {
 
-qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc*, char*, size_t* bytes) {
-  *bytes = 0;
-  return P->precision == QEM_PREC_FP32 ? QEM_OK : QEM_ERR_UNSUPPORTED;
+struct TcBuffers {
+  int fk[QEM_MAX_LEVELS] = {};   // feature row width (bf16 elements) of child level l
+  int nb[QEM_MAX_LEVELS] = {};   // bilinear features of child level l
+  int split = 3;
+  __nv_bfloat16* bfeat[QEM_MAX_LEVELS] = {};   // child level l:   [n_l][K rows][fk] canonical
+  __nv_bfloat16* afeat[QEM_MAX_LEVELS] = {};   // parent of l:     [n_{l-1}][K rows][fk]
+  __nv_bfloat16* cfeat[QEM_MAX_LEVELS] = {};   // compacted parent rows, same layout
+  float* rowc[QEM_MAX_LEVELS] = {};            // [n_{l-1}][K] row constants (nats)
+  float* center[QEM_MAX_LEVELS] = {};          // [n_{l-1}][D_l]
+  int* cidx[QEM_MAX_LEVELS] = {};              // [n_{l-1}][K] compacted parent sample indices
+  int* ccnt[QEM_MAX_LEVELS] = {};              // [n_{l-1}] number of kept parent samples
+  float* cbase[QEM_MAX_LEVELS] = {};           // [n_{l-1}][K] rowc + ln w_p - ln K of kept samples
+};
+
+namespace tc {
+
+constexpr int kRows = 128;        // MMA M: rows of one work unit
+constexpr int kMaxN = 256;        // MMA N of one column chunk
+constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2..9 epilogue
+constexpr int kMaxFK = 128;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kNegBig = -1.0e30f;
+
+// ---------------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
-qem_status tc_plan_init(qem_plan_t, const qem_model_desc*) { return QEM_OK; }
-void tc_plan_release(qem_plan_t) {}
-cudaError_t tc_forward(qem_plan_t, int) { return cudaErrorNotSupported; }
-cudaError_t tc_adjoint(qem_plan_t, int) { return cudaErrorNotSupported; }
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on a barrier phase: false (and the CTA abort flag set) when the
+// wait exceeds `limit` cycles or another role of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit, volatile int* abort_flag) {
+  if (mbar_try_wait(b, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > limit) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 in, FP32 accumulate), one elected thread.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// Shared-memory matrix descriptor: canonical K-major layout without swizzle.
+// start address, leading-dimension byte offset (between core matrices along
+// K), stride byte offset (between 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+  const uint32_t a = smem_u32(p);
+  return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor: BF16 A and B (K-major), FP32 D, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+// TMEM -> registers (load and wait in one block, so the outputs are valid after it).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float ex2f(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Element (row, col) of a canonical tile with fk columns: bf16 index.
+__host__ __device__ __forceinline__ long long canon(long long row, int col, int fk) {
+  return ((row >> 3) * (fk >> 3) + (col >> 3)) * 64 + (row & 7) * 8 + (col & 7);
+}
+
+__device__ __forceinline__ void split2(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  if (!(x > kNegBig)) {  // -inf / very negative / NaN-safe: a large finite negative
+    a = __float2bfloat16_rn(isnan(x) ? x : kNegBig);
+    b = c = __float2bfloat16_rn(0.f);
+    return;
+  }
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
+// ---------------------------------------------------------------------------- feature builders
+// Parent side (A rows of the forward tile, B columns of the adjoint): for each
+// parent sample kp, with the children's prior written as
+//   log p(z | kp) = pc + sum_d pp_d (z_d - pm_d)^2
+// and a per-parent centre c (mean of pm over kp; z' = z - c, pm' = pm - c):
+//   mean/log-variance prior: A = log2e [pp_d, -2 pp_d pm'_d],  B = [z'^2, z']
+//   fixed-variance prior:    A = log2e [-2 pp pm'_d],          B = [z']      (pp z'^2 joins h)
+//   rowc = pc + sum_d pp_d pm'_d^2.
+// Row of fk columns: split 3: [Ah | 1 1 1 | Ah | Al | 0..], split 1: [Ah | 1 1 1 | 0..].
+__global__ void k_parent_features(LevelView par, int Dc, int mean_logvar, int K, int fk, int nb, int split,
+                                  __nv_bfloat16* afeat, float* rowc, float* center) {
+  const long long p = blockIdx.x;
+  __shared__ float cen[kMaxDim];
+  for (int d = threadIdx.x; d < Dc; d += blockDim.x) {
+    double s = 0.0;
+    for (int kp = 0; kp < K; ++kp) s += par.pm[(p * K + kp) * Dc + d];
+    cen[d] = (float)(s / K);
+    center[p * Dc + d] = cen[d];
+  }
+  __syncthreads();
+  for (int kp = threadIdx.x; kp < K; kp += blockDim.x) {
+    const float* pm = par.pm + (p * K + kp) * Dc;
+    const float* pp = par.pp + (p * K + kp) * Dc;
+    double rc = par.pc[p * K + kp];
+    for (int d = 0; d < Dc; ++d) {
+      const float dm = pm[d] - cen[d];
+      rc += (double)pp[d] * dm * dm;
+    }
+    rowc[p * K + kp] = (float)rc;
+    __nv_bfloat16* row = afeat + p * (long long)K * fk;
+    for (int c0 = 0; c0 < fk; c0 += 8) {
+      __align__(16) __nv_bfloat16 g[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = c0 + j;
+        float v = 0.f;
+        int f = -1, part = 0;  // part: 0 = hi, 1 = lo, 2 = one
+        if (c < nb) { f = c; part = 0; }
+        else if (c < nb + 3) { part = 2; }
+        else if (split == 3 && c < 2 * nb + 3) { f = c - nb - 3; part = 0; }
+        else if (split == 3 && c < 3 * nb + 3) { f = c - 2 * nb - 3; part = 1; }
+        if (part == 2) {
+          v = 1.f;
+          g[j] = __float2bfloat16_rn(v);
+          continue;
+        }
+        if (f >= 0) {
+          float a;
+          if (mean_logvar) {
+            a = f < Dc ? pp[f] : -2.f * pp[f - Dc] * (pm[f - Dc] - cen[f - Dc]);
+          } else {
+            a = -2.f * pp[f] * (pm[f] - cen[f]);
+          }
+          a *= kLog2e;
+          __nv_bfloat16 hi, lo;
+          split2(a, hi, lo);
+          g[j] = part == 0 ? hi : lo;
+        } else {
+          g[j] = __float2bfloat16_rn(0.f);
+        }
+      }
+      *reinterpret_cast<uint4*>(row + canon(kp, c0, fk)) = *reinterpret_cast<const uint4*>(g);
+    }
+  }
+}
+
+// Child side: B row of sample k of element e: split 3: [Bh | h1 h2 h3 | Bl | Bh | 0..],
+// split 1: [Bh | h1 h2 h3 | 0..], with h = log2e (htil + [fixed-variance] pp sum z'^2).
+__global__ void k_child_features(LevelView ch, int mean_logvar, float pp_fixed, int K, int fk, int nb, int split,
+                                 const float* center, __nv_bfloat16* bfeat) {
+  const long long e = blockIdx.x;
+  const int D = ch.D;
+  const long long p = ch.parent[e];
+  __shared__ float cen[kMaxDim];
+  for (int d = threadIdx.x; d < D; d += blockDim.x) cen[d] = center[p * D + d];
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const float* z = ch.z + (e * K + k) * D;
+    float zp[kMaxDim];
+    float ss = 0.f;
+    for (int d = 0; d < D; ++d) {
+      zp[d] = z[d] - cen[d];
+      ss = fmaf(zp[d], zp[d], ss);
+    }
+    float h = ch.htil[e * K + k];
+    if (!mean_logvar) h = fmaf(pp_fixed, ss, h);
+    __nv_bfloat16 h1, h2, h3;
+    split3(h * kLog2e, h1, h2, h3);
+    __nv_bfloat16* row = bfeat + e * (long long)K * fk;
+    for (int c0 = 0; c0 < fk; c0 += 8) {
+      __align__(16) __nv_bfloat16 g[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = c0 + j;
+        int f = -1, part = 0;
+        if (c < nb) { f = c; part = 0; }
+        else if (c == nb) { g[j] = h1; continue; }
+        else if (c == nb + 1) { g[j] = h2; continue; }
+        else if (c == nb + 2) { g[j] = h3; continue; }
+        else if (split == 3 && c < 2 * nb + 3) { f = c - nb - 3; part = 1; }
+        else if (split == 3 && c < 3 * nb + 3) { f = c - 2 * nb - 3; part = 0; }
+        if (f >= 0) {
+          float b;
+          if (mean_logvar) b = f < D ? zp[f] * zp[f] : zp[f - D];
+          else b = zp[f];
+          __nv_bfloat16 hi, lo;
+          split2(b, hi, lo);
+          g[j] = part == 0 ? hi : lo;
+        } else {
+          g[j] = __float2bfloat16_rn(0.f);
+        }
+      }
+      *reinterpret_cast<uint4*>(row + canon(k, c0, fk)) = *reinterpret_cast<const uint4*>(g);
+    }
+  }
+}
+
+// Compaction of the parent samples that carry weight (adjoint columns):
+// kept = w_p[kp] > 2^-60 max_kp w_p, in index order; rows gathered into cfeat;
+// the count is padded to a multiple of 16 with rows whose base is -inf.
+__global__ void k_compact(LevelView par, int K, int fk, const __nv_bfloat16* afeat, const float* rowc,
+                          __nv_bfloat16* cfeat, int* cidx, int* ccnt, float* cbase) {
+  const long long p = blockIdx.x;
+  __shared__ float red[32];
+  __shared__ int scan[1024];
+  const float* w = par.w + p * K;
+  float mx = 0.f;
+  for (int kp = threadIdx.x; kp < K; kp += blockDim.x) mx = fmaxf(mx, w[kp]);
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  float wmax = 0.f;
+  for (int j = 0; j < (int)(blockDim.x >> 5); ++j) wmax = fmaxf(wmax, red[j]);
+  const float thr = wmax * 8.673617379884035e-19f;  // 2^-60
+  // contiguous range of kp per thread; count, block scan, scatter (order preserving)
+  const int per = (K + blockDim.x - 1) / blockDim.x;
+  const int k0 = threadIdx.x * per, k1 = min(K, k0 + per);
+  int cnt = 0;
+  for (int kp = k0; kp < k1; ++kp) cnt += (w[kp] > thr && w[kp] > 0.f) ? 1 : 0;
+  scan[threadIdx.x] = cnt;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const int v = threadIdx.x >= (unsigned)o ? scan[threadIdx.x - o] : 0;
+    __syncthreads();
+    scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int pos = scan[threadIdx.x] - cnt;
+  const int total = scan[blockDim.x - 1];
+  const float lnK = logf((float)K);
+  for (int kp = k0; kp < k1; ++kp) {
+    if (w[kp] > thr && w[kp] > 0.f) {
+      cidx[p * K + pos] = kp;
+      cbase[p * K + pos] = rowc[p * K + kp] + logf(w[kp]) - lnK;
+      ++pos;
+    }
+  }
+  const int npad = max(16, (total + 15) & ~15);
+  for (int j = total + threadIdx.x; j < npad; j += blockDim.x) {
+    cidx[p * K + j] = 0;
+    cbase[p * K + j] = -INFINITY;
+  }
+  if (threadIdx.x == 0) ccnt[p] = total;
+  __syncthreads();
+  // gather the kept rows (16-byte granules) into the compacted operand
+  const int gran = fk >> 3;
+  const uint4* src = reinterpret_cast<const uint4*>(afeat + p * (long long)K * fk);
+  uint4* dst = reinterpret_cast<uint4*>(cfeat + p * (long long)K * fk);
+  for (int i = threadIdx.x; i < npad * gran; i += blockDim.x) {
+    const int j = i / gran, g = i % gran;
+    const int kp = cidx[p * K + j];
+    dst[canon(j, g * 8, fk) >> 3] = src[canon(kp, g * 8, fk) >> 3];
+  }
+}
+
+// ---------------------------------------------------------------------------- the contraction kernel
+struct ContractArgs {
+  int K, fk, ksteps, rtiles;
+  long long n_units;
+  const long long* parent;
+  const __nv_bfloat16* rows_feat;   // A operand source (forward: parent features, adjoint: child features)
+  const __nv_bfloat16* cols_feat;   // B operand source (forward: child features, adjoint: compacted parents)
+  const float* rowc;                // forward
+  float* lt;                        // forward output [n][K]
+  const int* ccnt;                  // adjoint
+  const int* cidx;
+  const float* cbase;
+  const float* lt_in;
+  float* w_out;                     // adjoint output [n][K]
+  Ctl* ctl;
+  long long timeout_cycles;
+};
+
+struct Smem {
+  uint8_t* a0;       // two A tiles, a_stride apart
+  uint8_t* b0;       // two B chunks, b_stride apart
+  uint8_t* d0;       // two d tiles (adjoint), kMaxN*16*2 apart
+  uint32_t a_stride, b_stride;
+  uint8_t* ax;
+  uint64_t* a_full;
+  uint64_t* a_empty;
+  uint64_t* b_full;
+  uint64_t* b_empty;
+  uint64_t* t_full;
+  uint64_t* t_empty;
+  uint64_t* done;
+  uint32_t* tmem_base;
+  volatile int* abort_flag;
+  volatile int* stop_flag;
+  float2* merge;
+};
+
+__host__ __device__ inline size_t contract_smem_bytes(int fk, bool adj) {
+  const size_t a = (size_t)kRows * fk * 2, b = (size_t)kMaxN * fk * 2;
+  size_t tot = 1024 + 2 * a + 2 * b;
+  if (adj) tot += 2 * (size_t)kMaxN * 16 * 2 + (size_t)kRows * 16 * 2;
+  tot += 16 * 8 + 16 + kRows * sizeof(float2);
+  return tot;
+}
+
+__device__ __forceinline__ Smem carve(uint8_t* raw, int fk, bool adj) {
+  Smem s;
+  uint8_t* p = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+  const size_t a = (size_t)kRows * fk * 2, b = (size_t)kMaxN * fk * 2;
+  s.a_stride = (uint32_t)a;
+  s.b_stride = (uint32_t)b;
+  s.a0 = p; p += 2 * a;
+  s.b0 = p; p += 2 * b;
+  if (adj) {
+    s.d0 = p; p += 2 * kMaxN * 16 * 2;
+    s.ax = p; p += kRows * 16 * 2;
+  } else {
+    s.d0 = s.ax = nullptr;
+  }
+  uint64_t* bars = reinterpret_cast<uint64_t*>(p);
+  s.a_full = bars + 0;
+  s.a_empty = bars + 2;
+  s.b_full = bars + 4;
+  s.b_empty = bars + 6;
+  s.t_full = bars + 8;
+  s.t_empty = bars + 10;
+  s.done = bars + 12;
+  p += 16 * 8;
+  s.tmem_base = reinterpret_cast<uint32_t*>(p);
+  s.abort_flag = reinterpret_cast<volatile int*>(p + 4);
+  s.stop_flag = reinterpret_cast<volatile int*>(p + 8);
+  p += 16;
+  s.merge = reinterpret_cast<float2*>(p);
+  return s;
+}
+
+template <bool ADJ>
+__global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  Smem s = carve(smem_raw, a.fk, ADJ);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int fk = a.fk, K = a.K;
+  const uint32_t sbo = (uint32_t)(fk >> 3) * 128u;
+  const long long lim = a.timeout_cycles;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&s.a_full[i], 1);
+      mbar_init(&s.a_empty[i], 1);
+      mbar_init(&s.b_full[i], ADJ ? 2 : 1);
+      mbar_init(&s.b_empty[i], 1);
+      mbar_init(&s.t_full[i], 1);
+      mbar_init(&s.t_empty[i], 8);
+    }
+    mbar_init(s.done, 1);
+    *s.abort_flag = 0;
+    *s.stop_flag = 0;
+    fence_barrier_init();
+  }
+  if (ADJ) {  // constant A operand of the extra k-step: columns 0..2 = 1 (they pick up d)
+    __nv_bfloat16* ax = reinterpret_cast<__nv_bfloat16*>(s.ax);
+    for (int i = threadIdx.x; i < kRows * 16; i += blockDim.x) {
+      const int r = i / 16, c = i % 16;
+      ax[canon(r, c, 16)] = __float2bfloat16_rn(c < 3 ? 1.f : 0.f);
+    }
+    fence_proxy_async_smem();
+  }
+  if (warp == 1) {
+    tmem_alloc(s.tmem_base, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s.tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    int as = 0, bs = 0;
+    uint32_t aph = 0, bph = 0;
+    uint32_t armed = 0, last = 0;  // bit i: a slot i, bit 2+i: b slot i
+    for (long long u = blockIdx.x; u < a.n_units; u += gridDim.x) {
+      const long long e = u / a.rtiles;
+      const int rt = (int)(u % a.rtiles);
+      const long long p = a.parent[e];
+      const long long row_elt = ADJ ? e : p;
+      bool ok = true;
+      if (lane == 0) {
+        ok = mbar_wait(&s.a_empty[as], aph ^ 1, lim, s.abort_flag);
+        if (ok) {
+          const uint32_t bytes = (uint32_t)kRows * fk * 2;
+          mbar_expect_tx(&s.a_full[as], bytes);
+          bulk_g2s((s.a0 + as * s.a_stride), a.rows_feat + (row_elt * K + (long long)rt * kRows) * fk, bytes, &s.a_full[as]);
+          armed |= 1u << as;
+          last = (last & ~(1u << as)) | (aph << as);
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
+      as ^= 1;
+      if (as == 0) aph ^= 1;
+      const int ncols = ADJ ? max(16, (a.ccnt[p] + 15) & ~15) : K;
+      const long long col_elt = ADJ ? p : e;
+      for (int c0 = 0; c0 < ncols && ok; c0 += kMaxN) {
+        const int nc = min(kMaxN, ncols - c0);
+        if (lane == 0) {
+          ok = mbar_wait(&s.b_empty[bs], bph ^ 1, lim, s.abort_flag);
+          if (ok) {
+            const uint32_t bytes = (uint32_t)nc * fk * 2;
+            mbar_expect_tx(&s.b_full[bs], bytes);
+            bulk_g2s((s.b0 + bs * s.b_stride), a.cols_feat + (col_elt * K + c0) * fk, bytes, &s.b_full[bs]);
+            armed |= 4u << bs;
+            last = (last & ~(4u << bs)) | (bph << (2 + bs));
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) break;
+        if (ADJ) {
+          // d columns of this chunk: d_j = log2e (cbase_j - lt_e[kp_j]), split in three
+          __nv_bfloat16* dt = reinterpret_cast<__nv_bfloat16*>((s.d0 + bs * (kMaxN * 16 * 2)));
+          for (int j = lane; j < nc; j += 32) {
+            const int col = c0 + j;
+            const float base = a.cbase[p * K + col];
+            float dv = kNegBig;
+            if (base > -INFINITY) dv = (base - a.lt_in[e * K + a.cidx[p * K + col]]) * kLog2e;
+            __align__(16) __nv_bfloat16 g[8];
+            split3(dv, g[0], g[1], g[2]);
+#pragma unroll
+            for (int t = 3; t < 8; ++t) g[t] = __float2bfloat16_rn(0.f);
+            *reinterpret_cast<uint4*>(dt + canon(j, 0, 16)) = *reinterpret_cast<const uint4*>(g);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) g[t] = __float2bfloat16_rn(0.f);
+            *reinterpret_cast<uint4*>(dt + canon(j, 8, 16)) = *reinterpret_cast<const uint4*>(g);
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&s.b_full[bs]);
+        }
+        bs ^= 1;
+        if (bs == 0) bph ^= 1;
+      }
+      if (!ok) break;
+    }
+    // no bulk copy of this CTA may still be landing when it exits: wait for
+    // the last phase armed on every full barrier (bounded, ignores abort)
+    if (lane == 0) {
+      volatile int never = 0;
+      for (int i = 0; i < 2; ++i) {
+        if (armed & (1u << i)) mbar_wait(&s.a_full[i], (last >> i) & 1u, lim, &never);
+        if (armed & (4u << i)) mbar_wait(&s.b_full[i], (last >> (2 + i)) & 1u, lim, &never);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer (one thread)
+    if (lane == 0) {
+      int as = 0, bs = 0, ts = 0;
+      uint32_t aph = 0, bph = 0, tph = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+        const long long e = u / a.rtiles;
+        const long long p = a.parent[e];
+        ok = mbar_wait(&s.a_full[as], aph, lim, s.abort_flag);
+        if (!ok) break;
+        const int ncols = ADJ ? max(16, (a.ccnt[p] + 15) & ~15) : K;
+        for (int c0 = 0; c0 < ncols; c0 += kMaxN) {
+          const int nc = min(kMaxN, ncols - c0);
+          ok = mbar_wait(&s.b_full[bs], bph, lim, s.abort_flag) && mbar_wait(&s.t_empty[ts], tph ^ 1, lim, s.abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t d_tmem = tmem + (uint32_t)ts * kMaxN;
+          const uint32_t idesc = idesc_bf16(nc);
+          for (int ks = 0; ks < a.ksteps; ++ks) {
+            const uint64_t ad = smem_desc((s.a0 + as * s.a_stride) + ks * 256, 128, sbo);
+            const uint64_t bd = smem_desc((s.b0 + bs * s.b_stride) + ks * 256, 128, sbo);
+            mma_bf16(d_tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+          }
+          if (ADJ) {
+            const uint64_t ad = smem_desc(s.ax, 128, 256);
+            const uint64_t bd = smem_desc((s.d0 + bs * (kMaxN * 16 * 2)), 128, 256);
+            mma_bf16(d_tmem, ad, bd, idesc, 1u);
+          }
+          mma_commit(&s.b_empty[bs]);
+          mma_commit(&s.t_full[ts]);
+          bs ^= 1;
+          if (bs == 0) bph ^= 1;
+          ts ^= 1;
+          if (ts == 0) tph ^= 1;
+        }
+        if (!ok) break;
+        mma_commit(&s.a_empty[as]);
+        as ^= 1;
+        if (as == 0) aph ^= 1;
+      }
+      // every issued MMA has completed before the teardown
+      mma_commit(s.done);
+      mbar_wait(s.done, 0, lim, s.abort_flag);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue (8 warps)
+    // Every epilogue warp executes both named barriers of every unit it
+    // enters, and the decision to stop is read from a flag written between
+    // them, so the 8 warps always agree (no unmatched bar.sync on abort).
+    const int ew = warp - 2;
+    const int half = ew >> 2;
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    int ts = 0;
+    uint32_t tph = 0;
+    for (long long u = blockIdx.x; u < a.n_units; u += gridDim.x) {
+      const long long e = u / a.rtiles;
+      const int rt = (int)(u % a.rtiles);
+      const long long p = a.parent[e];
+      const int ncols = ADJ ? max(16, (a.ccnt[p] + 15) & ~15) : K;
+      float m = -INFINITY, sacc = 0.f;
+      bool ok = true;
+      for (int c0 = 0; c0 < ncols && ok; c0 += kMaxN) {
+        const int nc = min(kMaxN, ncols - c0);
+        ok = mbar_wait(&s.t_full[ts], tph, lim, s.abort_flag);
+        if (!ok) break;
+        tc_fence_after();
+        const int hw = nc >> 1;
+        const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ts * kMaxN + half * hw);
+        int c = 0;
+        for (; c + 32 <= hw; c += 32) {
+          float v[32];
+          tmem_ld32(tbase + c, v);
+          if (ADJ) {
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              p0 += ex2f(v[j]);
+              p1 += ex2f(v[j + 1]);
+              p2 += ex2f(v[j + 2]);
+              p3 += ex2f(v[j + 3]);
+            }
+            sacc += (p0 + p1) + (p2 + p3);
+          } else {
+            if (m == -INFINITY) {
+              float mx = v[0];
+#pragma unroll
+              for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
+              m = mx;
+            }
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              p0 += ex2f(v[j] - m);
+              p1 += ex2f(v[j + 1] - m);
+              p2 += ex2f(v[j + 2] - m);
+              p3 += ex2f(v[j + 3] - m);
+            }
+            float part = (p0 + p1) + (p2 + p3);
+            if (!(part <= 3.0e38f)) {  // overflow against the running shift: rescale exactly
+              float mx = v[0];
+#pragma unroll
+              for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
+              if (mx > m) {
+                sacc *= ex2f(m - mx);
+                m = mx;
+              }
+              part = 0.f;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) part += ex2f(v[j] - m);
+            }
+            sacc += part;
+          }
+        }
+        for (; c < hw; c += 8) {  // adjoint tails (chunks narrower than 64 columns)
+          float v[8];
+          tmem_ld8(tbase + c, v);
+          if (ADJ) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sacc += ex2f(v[j]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s.t_empty[ts]);
+        ts ^= 1;
+        if (ts == 0) tph ^= 1;
+      }
+      // combine the two column halves of each row
+      if (half == 1) s.merge[row] = make_float2(m, sacc);
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (threadIdx.x == 64) *s.stop_flag = *s.abort_flag;
+      if (half == 0 && ok) {
+        const float2 o = s.merge[row];
+        const long long k = (long long)rt * kRows + row;
+        if (ADJ) {
+          a.w_out[e * K + k] = sacc + o.y;
+        } else {
+          const float M = fmaxf(m, o.x);
+          const float S = (m == -INFINITY ? 0.f : sacc * ex2f(m - M)) + (o.x == -INFINITY ? 0.f : o.y * ex2f(o.x - M));
+          a.lt[e * K + k] = a.rowc[p * K + k] + (M + log2f(S)) * kLn2 - logf((float)K);
+        }
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (*s.stop_flag) break;
+    }
+  }
+
+  if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------------------- diagnostic GEMM
+// out[128][n] = A[128][fk] * B[n][fk]^T through the same descriptors, bulk
+// copies, MMA and TMEM loads (validation of the operand layout).
+__global__ void __launch_bounds__(128, 1) k_diag_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int fk, int n,
+                                                     float* out, Ctl* ctl, long long lim) {
+  extern __shared__ uint8_t raw[];
+  uint8_t* sa = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sb = sa + (size_t)kRows * fk * 2;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sb + (size_t)kMaxN * fk * 2);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tbase + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tbase, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tbase;
+  if (threadIdx.x == 0) {
+    const uint32_t ab = (uint32_t)kRows * fk * 2, bb = (uint32_t)n * fk * 2;
+    mbar_expect_tx(&bars[0], ab + bb);
+    bulk_g2s(sa, A, ab, &bars[0]);
+    bulk_g2s(sb, B, bb, &bars[0]);
+    if (mbar_wait(&bars[0], 0, lim, abort_flag)) {
+      tc_fence_after();
+      const uint32_t sbo = (uint32_t)(fk >> 3) * 128u;
+      for (int ks = 0; ks < fk / 16; ++ks)
+        mma_bf16(tmem, smem_desc(sa + ks * 256, 128, sbo), smem_desc(sb + ks * 256, 128, sbo), idesc_bf16(n),
+                 ks > 0 ? 1u : 0u);
+    }
+    mma_commit(&bars[1]);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(&bars[1], 0, lim, abort_flag);
+  tc_fence_after();
+  if (ok) {
+    const int row = warp * 32 + lane;
+    for (int c = 0; c < n; c += 8) {
+      float v[8];
+      tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      for (int j = 0; j < 8; ++j) out[(long long)row * n + c + j] = v[j];
+    }
+  }
+  if (*abort_flag && threadIdx.x == 0) atomicOr(&ctl->err, ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------- host side
+using namespace tc;
+
+static int feature_width(int nb, int split) {
+  const int w = split == 3 ? 3 * nb + 3 : nb + 3;
+  return (w + 15) & ~15;
+}
+
+qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base, size_t* bytes) {
+  *bytes = 0;
+  if (P->precision == QEM_PREC_FP32) return QEM_OK;
+  const int K = P->K;
+  if (K % kRows != 0) return QEM_ERR_UNSUPPORTED;
+  const int split = P->precision == QEM_PREC_BF16X3 ? 3 : 1;
+  TcBuffers tb;
+  tb.split = split;
+  size_t off = 0;
+  auto take = [&](size_t b) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align256(b);
+    return p;
+  };
+  for (int l = 1; l < desc->n_levels; ++l) {
+    const qem_level_desc& c = desc->levels[l];
+    const qem_level_desc& pa = desc->levels[l - 1];
+    const int nb = c.prior == QEM_PRIOR_NORMAL_MEAN_LOGVAR ? 2 * c.dim : c.dim;
+    const int fk = feature_width(nb, split);
+    if (fk > kMaxFK) return QEM_ERR_UNSUPPORTED;
+    tb.nb[l] = nb;
+    tb.fk[l] = fk;
+    tb.bfeat[l] = (__nv_bfloat16*)take((size_t)c.n * K * fk * 2);
+    tb.afeat[l] = (__nv_bfloat16*)take((size_t)pa.n * K * fk * 2);
+    tb.cfeat[l] = (__nv_bfloat16*)take((size_t)pa.n * K * fk * 2);
+    tb.rowc[l] = (float*)take((size_t)pa.n * K * 4);
+    tb.center[l] = (float*)take((size_t)pa.n * c.dim * 4);
+    tb.cidx[l] = (int*)take((size_t)pa.n * K * 4);
+    tb.ccnt[l] = (int*)take((size_t)pa.n * 4);
+    tb.cbase[l] = (float*)take((size_t)pa.n * K * 4);
+  }
+  *bytes = off;
+  if (base) {
+    P->tc = new (std::nothrow) TcBuffers(tb);
+    if (!P->tc) return QEM_ERR_OOM;
+  }
+  return QEM_OK;
+}
+
+qem_status tc_plan_init(qem_plan_t P, const qem_model_desc*) {
+  if (P->precision == QEM_PREC_FP32) return QEM_OK;
+  int fkmax = 16;
+  for (int l = 1; l < P->L; ++l) fkmax = fkmax > P->tc->fk[l] ? fkmax : P->tc->fk[l];
+  if (cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)contract_smem_bytes(fkmax, false)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)contract_smem_bytes(fkmax, true)) != cudaSuccess)
+    return QEM_ERR_CUDA;
+  return QEM_OK;
+}
+
+void tc_plan_release(qem_plan_t P) {
+  delete P->tc;
+  P->tc = nullptr;
+}
+
+static long long timeout_cycles(qem_plan_t P) { return (long long)(P->timeout_s * (double)P->clock_khz * 1e3); }
+
+cudaError_t tc_features(qem_plan_t P, int l) {
+  TcBuffers& T = *P->tc;
+  const LevelView& ch = P->lv[l];
+  const LevelView& pa = P->lv[l - 1];
+  const int K = P->K, fk = T.fk[l], nb = T.nb[l];
+  const int mlv = ch.prior == QEM_PRIOR_NORMAL_MEAN_LOGVAR ? 1 : 0;
+  if (pa.n > 0)
+    k_parent_features<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, ch.D, mlv, K, fk, nb, T.split, T.afeat[l],
+                                                              T.rowc[l], T.center[l]);
+  if (ch.n > 0)
+    k_child_features<<<(unsigned)ch.n, 256, 0, P->stream>>>(ch, mlv, -0.5f / ch.prior_a, K, fk, nb, T.split,
+                                                            T.center[l], T.bfeat[l]);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
+  TcBuffers& T = *P->tc;
+  const LevelView& ch = P->lv[l];
+  if (ch.n == 0) return cudaSuccess;
+  ContractArgs a{};
+  a.K = P->K;
+  a.fk = T.fk[l];
+  a.ksteps = T.fk[l] / 16;
+  a.rtiles = P->K / kRows;
+  a.n_units = ch.n * a.rtiles;
+  a.parent = ch.parent;
+  a.ctl = P->ctl;
+  a.timeout_cycles = timeout_cycles(P);
+  if (!adj) {
+    a.rows_feat = T.afeat[l];
+    a.cols_feat = T.bfeat[l];
+    a.rowc = T.rowc[l];
+    a.lt = ch.lt;
+  } else {
+    a.rows_feat = T.bfeat[l];
+    a.cols_feat = T.cfeat[l];
+    a.ccnt = T.ccnt[l];
+    a.cidx = T.cidx[l];
+    a.cbase = T.cbase[l];
+    a.lt_in = ch.lt;
+    a.w_out = ch.w;
+  }
+  const long long grid = a.n_units < P->num_sms ? a.n_units : P->num_sms;
+  const size_t smem = contract_smem_bytes(a.fk, adj);
+  if (adj)
+    k_contract<true><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
+  else
+    k_contract<false><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_forward(qem_plan_t P, int l) { return launch_contract(P, l, false); }
+
+cudaError_t tc_compact(qem_plan_t P, int l) {
+  TcBuffers& T = *P->tc;
+  const LevelView& pa = P->lv[l - 1];
+  if (pa.n == 0) return cudaSuccess;
+  k_compact<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, P->K, T.fk[l], T.afeat[l], T.rowc[l], T.cfeat[l], T.cidx[l],
+                                                    T.ccnt[l], T.cbase[l]);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_adjoint(qem_plan_t P, int l) { return launch_contract(P, l, true); }
 
 }  // namespace qem
+
+extern "C" qem_status qem_diag_tc_gemm(const void* A, const void* B, int fk, int n, float* out, void* stream) {
+  using namespace qem;
+  using namespace qem::tc;
+  if (!A || !B || !out || fk < 16 || fk > kMaxFK || fk % 16 || n < 16 || n > kMaxN || n % 16) return QEM_ERR_INVALID_ARG;
+  Ctl* ctl = nullptr;
+  if (cudaMalloc(&ctl, sizeof(Ctl)) != cudaSuccess) return QEM_ERR_OOM;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+  const size_t smem = 1024 + (size_t)kRows * fk * 2 + (size_t)kMaxN * fk * 2 + 64;
+  cudaFuncSetAttribute(k_diag_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, khz = 2000000;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  k_diag_gemm<<<1, 128, smem, s>>>((const __nv_bfloat16*)A, (const __nv_bfloat16*)B, fk, n, out, ctl,
+                                   (long long)khz * 1000 * 2);
+  cudaError_t e = cudaGetLastError();
+  Ctl h{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(ctl);
+  if (e != cudaSuccess) return QEM_ERR_CUDA;
+  return (h.err & ERR_TIMEOUT) ? QEM_ERR_TIMEOUT : QEM_OK;
+}

@@ -12,8 +12,14 @@ qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base,
 // One-time set-up after the workspace exists (kernel attributes, constant operands).
 qem_status tc_plan_init(qem_plan_t P, const qem_model_desc* desc);
 void tc_plan_release(qem_plan_t P);
-// Forward contraction of level l (l >= 1) into lv[l].lt, and its adjoint into lv[l].w.
+// Operand features of level l (l >= 1) and its parent level, after the
+// level's relative local factors are final.
+cudaError_t tc_features(qem_plan_t P, int l);
+// Forward contraction of level l into lv[l].lt.
 cudaError_t tc_forward(qem_plan_t P, int l);
+// Compaction of the parent samples that carry weight, then the adjoint of
+// level l into lv[l].w.
+cudaError_t tc_compact(qem_plan_t P, int l);
 cudaError_t tc_adjoint(qem_plan_t P, int l);
 
 }  // namespace qem

@@ -1,0 +1,91 @@
+"""GPU tests of the tensor-core (tcgen05) contraction path.
+
+* the operand layout / descriptor path, through the diagnostic GEMM entry
+  point, against a plain fp32 matmul of the same BF16 operands;
+* the E-step with split-BF16 operands (BF16X3) against the FP64 oracle at the
+  mixed-precision tolerance (1e-3 relative: log P_MP, moments relative to
+  max(|m|, sd_q) or sd_q^2, weights absolute);
+* plain BF16 reports its error (it is kept for the precision study, not held
+  to the tolerance).
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2503_08264_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2503_08264_gb300 import build
+    build.build()
+    O.build()
+
+
+def canonical(x: torch.Tensor) -> torch.Tensor:
+    """[R, F] -> the K-major core-matrix layout (8 x 8 blocks, row groups major)."""
+    R, F = x.shape
+    return x.view(R // 8, 8, F // 8, 8).permute(0, 2, 1, 3).contiguous().view(-1)
+
+
+@pytest.mark.parametrize("fk,n", [(16, 16), (48, 64), (112, 256), (128, 128), (32, 240)])
+def test_diag_gemm_matches_matmul(fk, n):
+    from paper_2503_08264_gb300 import _lib as L
+    g = torch.Generator().manual_seed(fk * 1000 + n)
+    A = torch.randn(128, fk, generator=g).to(torch.bfloat16)
+    B = torch.randn(n, fk, generator=g).to(torch.bfloat16)
+    ref = A.float() @ B.float().T
+    Ad, Bd = canonical(A).cuda(), canonical(B).cuda()
+    out = torch.zeros(128, n, dtype=torch.float32, device="cuda")
+    rc = L.load().qem_diag_tc_gemm(C.c_void_p(Ad.data_ptr()), C.c_void_p(Bd.data_ptr()), fk, n,
+                                   C.c_void_p(out.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    np.testing.assert_allclose(out.cpu().numpy(), ref.numpy(), rtol=1e-5, atol=1e-4)
+
+
+from test_parity_gpu import assert_parity, moment_errors, run_pair  # noqa: E402
+
+
+@pytest.mark.parametrize("M,K", [(300, 128), (40, 256), (13, 1024)])
+def test_bf16x3_hier_logistic_parity(M, K):
+    model = S.hier_logistic(M=M, N=5, seed=11)
+    q = S.random_q(model, seed=12, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    eps = S.noise(model, K, seed=13)
+    got, ref = run_pair(model, K, q, eps, precision="bf16x3")
+    assert_parity(model, q, got, ref, 1e-3, 1e-3, 1e-3)
+
+
+def test_bf16x3_three_level_parity():
+    model = S.batched_three_level(n_inst=6, D=8, seed=21, groups=(0, 5), units=(0, 12))
+    K = 256
+    q = S.random_q(model, seed=22, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    eps = S.noise(model, K, seed=23)
+    got, ref = run_pair(model, K, q, eps, precision="bf16x3")
+    assert_parity(model, q, got, ref, 1e-3, 1e-3, 1e-3)
+
+
+def test_bf16x3_from_initial_proposal():
+    """q0 = N(0, I) (App. F): very uneven weights, the overflow-rescale path."""
+    model = S.hier_logistic(M=64, N=10, seed=31)
+    K = 512
+    q = S.initial_q(model)
+    eps = S.noise(model, K, seed=32)
+    got, ref = run_pair(model, K, q, eps, precision="bf16x3")
+    assert_parity(model, q, got, ref, 1e-3, 1e-3, 1e-3)
+
+
+def test_plain_bf16_reports_error():
+    model = S.hier_logistic(M=100, N=5, seed=41)
+    K = 256
+    q = S.random_q(model, seed=42, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    eps = S.noise(model, K, seed=43)
+    got, ref = run_pair(model, K, q, eps, precision="bf16")
+    lp = np.max(np.abs(got["log_pmp"] - ref["log_pmp"]) / np.abs(ref["log_pmp"]))
+    print("plain bf16: log_pmp rel", lp, "moments", moment_errors(model, q, got["mom"], ref["mom"]))
+    assert lp < 1e-2
