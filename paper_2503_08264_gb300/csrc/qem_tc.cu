@@ -661,7 +661,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
               p3 += ex2f(v[j + 3] - m);
             }
             float part = (p0 + p1) + (p2 + p3);
-            if (!(part <= 3.0e38f)) {  // overflow against the running shift: rescale exactly
+            // The shift is the first group's maximum; a later group far above it
+            // gives a large (or infinite) partial sum.  Rescale to that group's
+            // exact maximum whenever the partial sum exceeds 2^32, so the running
+            // sum stays below 2^32 per group and never overflows.
+            if (!(part <= 4294967296.0f)) {
               float mx = v[0];
 #pragma unroll
               for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
