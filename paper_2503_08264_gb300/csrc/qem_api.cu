@@ -156,10 +156,12 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
   }
   QEM_LAUNCH(P, QEM_K_ROOT, launch_root(P->lv[0], K, L > 1, P->log_pmp, user_lp, trace, P->ctl, s));
   for (int l = 1; l < L; ++l) {
+    QEM_LAUNCH(P, QEM_K_OPERANDS, launch_compact(P->lv[l - 1], K, s));
     if (P->precision == QEM_PREC_FP32) {
-      QEM_LAUNCH(P, QEM_K_ADJOINT, launch_adj_simt(P->lv[l], P->lv[l - 1], K, s));
+      QEM_LAUNCH(P, QEM_K_ADJOINT, launch_adj_compact(P->lv[l], P->lv[l - 1], K, 0, s));
     } else {
-      QEM_LAUNCH(P, QEM_K_OPERANDS, tc_compact(P, l));
+      QEM_LAUNCH(P, QEM_K_ADJOINT, launch_adj_small(P->lv[l], P->lv[l - 1], K, s));
+      QEM_LAUNCH(P, QEM_K_OPERANDS, tc_adjoint_prep(P, l));
       QEM_LAUNCH(P, QEM_K_ADJOINT, tc_adjoint(P, l));
     }
   }
@@ -246,6 +248,26 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
     for (size_t i = 1; i < co.size(); ++i) co[i] += co[i - 1];
   }
 
+  // plate-sum chunks: the children of each element, at most kChunkChildren per chunk
+  struct Chunks {
+    std::vector<long long> beg, end, par_off;
+  };
+  const long long kChunkChildren = 32;
+  std::vector<Chunks> chunks(L);
+  for (int l = 1; l < L; ++l) {
+    Chunks& ck = chunks[l];
+    const std::vector<long long>& co = child_off[l - 1];
+    ck.par_off.assign(co.size(), 0);
+    for (size_t p = 0; p + 1 < co.size(); ++p) {
+      ck.par_off[p] = (long long)ck.beg.size();
+      for (long long c = co[p]; c < co[p + 1]; c += kChunkChildren) {
+        ck.beg.push_back(c);
+        ck.end.push_back(std::min(co[p + 1], c + kChunkChildren));
+      }
+    }
+    ck.par_off.back() = (long long)ck.beg.size();
+  }
+
   // two passes: size, then carve
   for (int pass = 0; pass < 2; ++pass) {
     Carver cv;
@@ -290,6 +312,14 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
       lv.pm = has_children ? cv.take<float>(nK * lv.Dc) : nullptr;
       lv.pp = has_children ? cv.take<float>(nK * lv.Dc) : nullptr;
       lv.pc = has_children ? cv.take<float>(nK) : nullptr;
+      lv.cidx = has_children ? cv.take<int>(nK) : nullptr;
+      lv.ccnt = has_children ? cv.take<int>((size_t)d.n) : nullptr;
+      lv.cw = has_children ? cv.take<float>(nK) : nullptr;
+      lv.chk_off = has_children ? cv.take<long long>((size_t)d.n + 1) : nullptr;
+      lv.n_chunks = l > 0 ? (long long)chunks[l].beg.size() : 0;
+      lv.chk_beg = l > 0 ? cv.take<long long>((size_t)lv.n_chunks) : nullptr;
+      lv.chk_end = l > 0 ? cv.take<long long>((size_t)lv.n_chunks) : nullptr;
+      lv.partial = l > 0 ? cv.take<double>((size_t)lv.n_chunks * K) : nullptr;
     }
     size_t tc_bytes = 0;
     st = tc_plan_reserve(P, desc, pass == 1 ? cv.base + cv.off : nullptr, &tc_bytes);
@@ -313,6 +343,16 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
                            cudaMemcpyHostToDevice, P->stream);
     if (ce == cudaSuccess && P->lv[l].hsum)
       ce = cudaMemsetAsync(P->lv[l].hsum, 0, sizeof(double) * (size_t)d.n * K, P->stream);
+    if (ce == cudaSuccess && l + 1 < L)
+      ce = cudaMemcpyAsync(P->lv[l].chk_off, chunks[l + 1].par_off.data(), sizeof(long long) * chunks[l + 1].par_off.size(),
+                           cudaMemcpyHostToDevice, P->stream);
+    if (ce == cudaSuccess && l > 0 && P->lv[l].n_chunks > 0) {
+      ce = cudaMemcpyAsync(P->lv[l].chk_beg, chunks[l].beg.data(), sizeof(long long) * chunks[l].beg.size(),
+                           cudaMemcpyHostToDevice, P->stream);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(P->lv[l].chk_end, chunks[l].end.data(), sizeof(long long) * chunks[l].end.size(),
+                             cudaMemcpyHostToDevice, P->stream);
+    }
   }
   size_t smem = 0;
   for (int l = 0; l < L; ++l) smem = std::max(smem, sample_local_smem(P->lv[l]));

@@ -57,6 +57,18 @@ struct LevelView {
   float* pp;          // [n][K][Dc] -0.5 * child-prior precision
   float* pc;          // [n][K]     child-prior log normaliser
   int Dc;             // dimension of the children (0: none)
+  // weight compaction of this level's samples (levels with children)
+  int* cidx;          // [n][K] indices of the kept samples, in order
+  int* ccnt;          // [n]    number kept
+  float* cw;          // [n][K] ln w - ln K of the kept samples (-inf padding)
+  // plate-sum chunks: children of element p are chunks chk_off[p]..chk_off[p+1]
+  // of the next level; this level's own chunks (levels > 0) cover
+  // elements chk_beg[i]..chk_end[i] with FP64 partial sums [n_chunks][K]
+  long long* chk_off;
+  long long* chk_beg;
+  long long* chk_end;
+  long long n_chunks;
+  double* partial;
 };
 
 struct TcBuffers;  // tensor-core operand buffers (qem_tc.cu)
@@ -168,7 +180,9 @@ cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& parent, int K, 
 cudaError_t launch_plate_sum(const LevelView& parent, const LevelView& child, int K, cudaStream_t s);
 cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* log_pmp, double* user_out,
                         double* trace, Ctl* ctl, cudaStream_t s);
-cudaError_t launch_adj_simt(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
+cudaError_t launch_compact(const LevelView& parent, int K, cudaStream_t s);
+cudaError_t launch_adj_compact(const LevelView& v, const LevelView& parent, int K, int max_eff, cudaStream_t s);
+cudaError_t launch_adj_small(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
 cudaError_t launch_moments(const LevelView& v, int K, double* mom, cudaStream_t s);
 cudaError_t launch_mstep(const LevelView& v, const double* mom, double* m, float* q, double lambda,
                          double sched_p, double var_floor, long long t_host, const Ctl* ctl, cudaStream_t s);

@@ -70,29 +70,35 @@ __device__ double gamma_variate(double a, const NoiseSrc& ns, int base) {
 // ---------------------------------------------------------------------------
 // K1/K2: draw z ~ Q and evaluate the local factor of every sample
 // (Alg. 1 "z ~ Q_t"; the P(x|z)/Q(z) part of r_k in Eq. rmp):
-//   loc[e][k] = sum_n log p(y_en | z_e^k, x_en) - log q(z_e^k) (+ log p(z) at level 0).
-// One block per element; its covariates and q parameters live in shared
-// memory; the block's samples are staged in shared memory so that noise loads
-// and sample stores are coalesced.
+//   loc[e][k] = sum_n log p(y_en | z_e^k, x_en) - log q(z_e^k) (+ log p(z) at level 0),
+// split into a sample-dependent FP32 part (loc, centred on its maximum) and a
+// sample-independent FP64 part (cst).  One block per element; covariates in
+// shared memory (rows padded to a multiple of 4 for 16-byte loads); each
+// thread keeps its sample in registers; samples are staged through shared
+// memory for coalesced stores.
 constexpr int kSampleThreads = 128;
 
 __device__ __forceinline__ float softplusf(float s) { return fmaxf(s, 0.f) + log1pf(__expf(-fabsf(s))); }
 
+template <int MAXD>
 __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, int K, const float* __restrict__ q,
                                                                   const float* __restrict__ eps, const Ctl* ctl) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   __shared__ double cred[kSampleThreads / 32];
   __shared__ float fred[kSampleThreads / 32];
   __shared__ double cst_sh;
   const long long e = blockIdx.x;
-  const int D = v.D, nobs = v.n_obs, zs_stride = D + 1;
-  float* xs = sm;                       // [nobs][D]
-  float* ys = xs + nobs * D;            // [nobs]
+  const int D = v.D, nobs = v.n_obs, Dp = (D + 3) & ~3, zs_stride = D + 1;
+  float* xs = sm;                       // [nobs][Dp]
+  float* ys = xs + nobs * Dp;           // [nobs]
   float* s0s = ys + nobs;               // [nobs] reference point of the Poisson-log term
   float* ey0s = s0s + nobs;             // [nobs] exp(s0)
   float* qs = ey0s + nobs;              // [2][D]
   float* zs = qs + 2 * D;               // [blockDim][D+1]
-  for (int i = threadIdx.x; i < nobs * D; i += blockDim.x) xs[i] = v.x[e * nobs * D + i];
+  for (int i = threadIdx.x; i < nobs * Dp; i += blockDim.x) {
+    const int n = i / Dp, d = i % Dp;
+    xs[i] = d < D ? v.x[(e * nobs + n) * D + d] : 0.f;
+  }
   for (int i = threadIdx.x; i < 2 * D; i += blockDim.x) qs[i] = q[e * 2 * D + i];
   // Sample-independent part of the element's local factor, in FP64:
   // likelihood normalisers, lgamma(y+1) and the Poisson reference terms.
@@ -134,64 +140,83 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
     cst_sh = t;
   }
   const unsigned long long seed = ctl->seed, iter = ctl->iter;
+  const float4* xs4 = reinterpret_cast<const float4*>(xs);
+  float lmax = -INFINITY;
 
   for (int k0 = 0; k0 < K; k0 += blockDim.x) {
     const int nk = min((int)blockDim.x, K - k0);
     const int k = k0 + threadIdx.x;
     const bool act = threadIdx.x < nk;
-    float* zr = zs + threadIdx.x * zs_stride;
-    float lq = 0.f;  // sample-dependent part of log q
-    if (v.qfam == QEM_Q_GAUSS) {
-      // noise -> zs (coalesced when supplied)
-      if (eps) {
-        const float* src = eps + (e * K + k0) * (long long)D;
-        for (int i = threadIdx.x; i < nk * D; i += blockDim.x) zs[(i / D) * zs_stride + (i % D)] = src[i];
-        __syncthreads();
-      } else if (act) {
-        const unsigned long long sample = (unsigned long long)e * K + k;
-        for (int d0 = 0; d0 < D; d0 += 4) {
-          const float4 g = normal4(seed, iter, v.level, sample, (uint32_t)(d0 >> 2));
-          zr[d0] = g.x;
-          if (d0 + 1 < D) zr[d0 + 1] = g.y;
-          if (d0 + 2 < D) zr[d0 + 2] = g.z;
-          if (d0 + 3 < D) zr[d0 + 3] = g.w;
+    float z[MAXD];
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) z[d] = 0.f;
+    if (act) {
+      float lq = 0.f;  // sample-dependent part of log q
+      if (v.qfam == QEM_Q_GAUSS) {
+        if (eps) {
+          const float* src = eps + (e * K + k) * (long long)D;
+#pragma unroll
+          for (int d = 0; d < MAXD; ++d)
+            if (d < D) z[d] = src[d];
+        } else {
+          const unsigned long long sample = (unsigned long long)e * K + k;
+#pragma unroll
+          for (int d0 = 0; d0 < MAXD; d0 += 4) {
+            if (d0 < D) {
+              const float4 g = normal4(seed, iter, v.level, sample, (uint32_t)(d0 >> 2));
+              z[d0] = g.x;
+              if (d0 + 1 < MAXD) z[d0 + 1] = d0 + 1 < D ? g.y : 0.f;
+              if (d0 + 2 < MAXD) z[d0 + 2] = d0 + 2 < D ? g.z : 0.f;
+              if (d0 + 3 < MAXD) z[d0 + 3] = d0 + 3 < D ? g.w : 0.f;
+            }
+          }
         }
-      }
-      if (act) {
         float ss = 0.f;
-        for (int d = 0; d < D; ++d) {
-          const float ep = zr[d];
-          ss = fmaf(ep, ep, ss);
-          zr[d] = fmaf(qs[D + d], ep, qs[d]);
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) {
+          if (d < D) {
+            const float ep = z[d];
+            ss = fmaf(ep, ep, ss);
+            z[d] = fmaf(qs[D + d], ep, qs[d]);
+          }
         }
         lq = -0.5f * ss;
-      }
-    } else if (act) {
-      const unsigned long long sample = (unsigned long long)e * K + k;
-      NoiseSrc ns{eps ? eps + (e * K + k) * (long long)v.nps : nullptr, seed, iter, sample, v.level, v.qfam};
-      const int blk = 2 * QEM_GAMMA_TRIES + 1;
-      double lqd = 0.0;
-      for (int d = 0; d < D; ++d) {
-        const double a = qs[d], b = qs[D + d];
-        double zz;
-        if (v.qfam == QEM_Q_GAMMA) {
-          zz = gamma_variate(a, ns, d * blk) / b;
-          lqd += a * log(b) - lgamma(a) + (a - 1.0) * log(zz) - b * zz;
-        } else {
-          const double g1 = gamma_variate(a, ns, (2 * d) * blk), g2 = gamma_variate(b, ns, (2 * d + 1) * blk);
-          zz = g1 / (g1 + g2);
-          lqd += (a - 1.0) * log(zz) + (b - 1.0) * log1p(-zz) - (lgamma(a) + lgamma(b) - lgamma(a + b));
+      } else {
+        const unsigned long long sample = (unsigned long long)e * K + k;
+        NoiseSrc ns{eps ? eps + (e * K + k) * (long long)v.nps : nullptr, seed, iter, sample, v.level, v.qfam};
+        const int blk = 2 * QEM_GAMMA_TRIES + 1;
+        double lqd = 0.0;
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) {
+          if (d < D) {
+            const double a = qs[d], b = qs[D + d];
+            double zz;
+            if (v.qfam == QEM_Q_GAMMA) {
+              zz = gamma_variate(a, ns, d * blk) / b;
+              lqd += a * log(b) - lgamma(a) + (a - 1.0) * log(zz) - b * zz;
+            } else {
+              const double g1 = gamma_variate(a, ns, (2 * d) * blk), g2 = gamma_variate(b, ns, (2 * d + 1) * blk);
+              zz = g1 / (g1 + g2);
+              lqd += (a - 1.0) * log(zz) + (b - 1.0) * log1p(-zz) - (lgamma(a) + lgamma(b) - lgamma(a + b));
+            }
+            z[d] = (float)zz;
+          }
         }
-        zr[d] = (float)zz;
+        lq = (float)lqd;
       }
-      lq = (float)lqd;
-    }
-    if (act) {
       float ll = 0.f;
       for (int n = 0; n < nobs; ++n) {
         float s = 0.f;
-        const float* xn = xs + n * D;
-        for (int d = 0; d < D; ++d) s = fmaf(zr[d], xn[d], s);
+#pragma unroll
+        for (int d4 = 0; d4 < MAXD / 4; ++d4) {
+          if (4 * d4 < Dp) {
+            const float4 xv = xs4[n * (Dp >> 2) + d4];
+            s = fmaf(z[4 * d4], xv.x, s);
+            s = fmaf(z[4 * d4 + 1], xv.y, s);
+            s = fmaf(z[4 * d4 + 2], xv.z, s);
+            s = fmaf(z[4 * d4 + 3], xv.w, s);
+          }
+        }
         const float yv = ys[n];
         switch (v.lik) {
           case QEM_LIK_GAUSS: {
@@ -205,38 +230,38 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
             ll += yv * dl - ey0s[n] * expm1f(dl);
             break;
           }
-          case QEM_LIK_POISSON_RATE: ll += yv * logf(zr[0]) - zr[0]; break;
-          case QEM_LIK_BERNOULLI_PROB: ll += yv * logf(zr[0]) + (1.f - yv) * log1pf(-zr[0]); break;
+          case QEM_LIK_POISSON_RATE: ll += yv * logf(z[0]) - z[0]; break;
+          case QEM_LIK_BERNOULLI_PROB: ll += yv * logf(z[0]) + (1.f - yv) * log1pf(-z[0]); break;
           default: break;
         }
       }
       float lp = 0.f;
       if (v.level == 0) {
-        switch (v.prior) {
-          case QEM_PRIOR_STD_NORMAL: {
-            float ss = 0.f;
-            for (int d = 0; d < D; ++d) ss = fmaf(zr[d], zr[d], ss);
-            lp = -0.5f * ss / v.prior_a;
-            break;
-          }
-          case QEM_PRIOR_GAMMA: {
-            const double a0 = v.prior_a, b0 = v.prior_b;
-            double acc = 0.0;
-            for (int d = 0; d < D; ++d) acc += (a0 - 1.0) * log((double)zr[d]) - b0 * zr[d];
-            lp = (float)acc;
-            break;
-          }
-          case QEM_PRIOR_BETA: {
-            const double a0 = v.prior_a, b0 = v.prior_b;
-            double acc = 0.0;
-            for (int d = 0; d < D; ++d) acc += (a0 - 1.0) * log((double)zr[d]) + (b0 - 1.0) * log1p(-(double)zr[d]);
-            lp = (float)acc;
-            break;
-          }
-          default: break;
+        if (v.prior == QEM_PRIOR_STD_NORMAL) {
+          float ss = 0.f;
+#pragma unroll
+          for (int d = 0; d < MAXD; ++d) ss = fmaf(z[d], z[d], ss);
+          lp = -0.5f * ss / v.prior_a;
+        } else if (v.prior == QEM_PRIOR_GAMMA) {
+          const double a0 = v.prior_a, b0 = v.prior_b;
+          double acc = 0.0;
+          for (int d = 0; d < D && d < MAXD; ++d) acc += (a0 - 1.0) * log((double)z[d]) - b0 * z[d];
+          lp = (float)acc;
+        } else if (v.prior == QEM_PRIOR_BETA) {
+          const double a0 = v.prior_a, b0 = v.prior_b;
+          double acc = 0.0;
+          for (int d = 0; d < D && d < MAXD; ++d)
+            acc += (a0 - 1.0) * log((double)z[d]) + (b0 - 1.0) * log1p(-(double)z[d]);
+          lp = (float)acc;
         }
       }
-      v.loc[e * K + k] = ll - lq + lp;
+      const float lv = ll - lq + lp;
+      v.loc[e * K + k] = lv;
+      lmax = fmaxf(lmax, lv);
+      float* zr = zs + threadIdx.x * zs_stride;
+#pragma unroll
+      for (int d = 0; d < MAXD; ++d)
+        if (d < D) zr[d] = z[d];
     }
     __syncthreads();
     // coalesced store of the block's samples
@@ -247,8 +272,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
   // Centre the element's sample-dependent factor on its maximum (the offset
   // joins the FP64 constant), so every later FP32 step works near zero for
   // the samples that carry weight.
-  float mx = -INFINITY;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmaxf(mx, v.loc[e * K + k]);
+  float mx = lmax;
   for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) fred[threadIdx.x >> 5] = mx;
   __syncthreads();
@@ -260,19 +284,38 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
 }
 
 size_t sample_local_smem(const LevelView& v) {
-  return sizeof(float) * (size_t)(v.n_obs * v.D + 3 * v.n_obs + 2 * v.D + kSampleThreads * (v.D + 1));
+  const int Dp = (v.D + 3) & ~3;
+  return sizeof(float) * (size_t)(v.n_obs * Dp + 3 * v.n_obs + 2 * v.D + kSampleThreads * (v.D + 1)) + 16;
+}
+
+template <int MAXD>
+static cudaError_t sample_cfg(size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_sample_local<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t configure_sample_local(size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(k_sample_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = sample_cfg<4>(smem);
+  if (e == cudaSuccess) e = sample_cfg<8>(smem);
+  if (e == cudaSuccess) e = sample_cfg<12>(smem);
+  if (e == cudaSuccess) e = sample_cfg<20>(smem);
+  if (e == cudaSuccess) e = sample_cfg<40>(smem);
+  if (e == cudaSuccess) e = sample_cfg<64>(smem);
+  return e;
 }
 
 cudaError_t launch_sample_local(const LevelView& v, int K, const float* q, const float* eps, const Ctl* ctl,
                                 cudaStream_t s) {
   if (v.n == 0) return cudaSuccess;
   const size_t smem = sample_local_smem(v);
-  k_sample_local<<<(unsigned)v.n, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
+  const unsigned grid = (unsigned)v.n;
+  const int Dp = (v.D + 3) & ~3;
+  if (Dp <= 4) k_sample_local<4><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
+  else if (Dp <= 8) k_sample_local<8><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
+  else if (Dp <= 12) k_sample_local<12><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
+  else if (Dp <= 20) k_sample_local<20><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
+  else if (Dp <= 40) k_sample_local<40><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
+  else k_sample_local<64><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
   return cudaGetLastError();
 }
 
@@ -428,32 +471,34 @@ cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& par, int K, cud
 
 // ---------------------------------------------------------------------------
 // Plate sum (Sec. 7: the child's factor enters the parent's as a sum over the
-// plate): hsum_p[kp] = sum_{e in children(p)} (lt[e][kp] + off[e]) in FP64,
-// in a fixed order (deterministic).  One thread per (parent, kp); the
-// children of a parent are split into 8 interleaved slices reduced in order.
-__global__ void k_plate_sum(LevelView par, LevelView ch, int K) {
-  __shared__ double red[8][33];
-  const long long p = blockIdx.x;
-  const int kp = blockIdx.y * 32 + threadIdx.x;
-  const long long c0 = par.child_off[p], c1 = par.child_off[p + 1];
+// plate): hsum_p[kp] = sum_{e in children(p)} (lt[e][kp] + off[e] + cst[e]) in
+// FP64, in a fixed order (deterministic).  Stage 1 sums chunks of at most 32
+// consecutive children into partial[chunk][kp]; stage 2 adds a parent's
+// chunks in order.
+__global__ void k_plate_partial(LevelView ch, int K) {
+  const long long i = blockIdx.x;
+  const int kp = blockIdx.y * blockDim.x + threadIdx.x;
+  if (kp >= K) return;
   double acc = 0.0;
-  if (kp < K) {
-    for (long long c = c0 + threadIdx.y; c < c1; c += 8)
-      acc += (double)ch.lt[c * K + kp] + (ch.off ? ch.off[c] : 0.0) + ch.cst[c];
-  }
-  red[threadIdx.y][threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.y == 0 && kp < K) {
-    double t = 0.0;
-    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
-    par.hsum[p * K + kp] = t;
-  }
+  for (long long c = ch.chk_beg[i]; c < ch.chk_end[i]; ++c)
+    acc += (double)ch.lt[c * K + kp] + (ch.off ? ch.off[c] : 0.0) + ch.cst[c];
+  ch.partial[i * K + kp] = acc;
+}
+
+__global__ void k_plate_final(LevelView par, LevelView ch, int K) {
+  const long long p = blockIdx.x;
+  const int kp = blockIdx.y * blockDim.x + threadIdx.x;
+  if (kp >= K) return;
+  double acc = 0.0;
+  for (long long i = par.chk_off[p]; i < par.chk_off[p + 1]; ++i) acc += ch.partial[i * K + kp];
+  par.hsum[p * K + kp] = acc;
 }
 
 cudaError_t launch_plate_sum(const LevelView& parent, const LevelView& child, int K, cudaStream_t s) {
   if (parent.n == 0) return cudaSuccess;
-  dim3 grid((unsigned)parent.n, (unsigned)((K + 31) / 32));
-  k_plate_sum<<<grid, dim3(32, 8), 0, s>>>(parent, child, K);
+  const unsigned ky = (unsigned)((K + 255) / 256);
+  if (child.n_chunks > 0) k_plate_partial<<<dim3((unsigned)child.n_chunks, ky), 256, 0, s>>>(child, K);
+  k_plate_final<<<dim3((unsigned)parent.n, ky), 256, 0, s>>>(parent, child, K);
   return cudaGetLastError();
 }
 
@@ -511,13 +556,69 @@ cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* lo
 }
 
 // ---------------------------------------------------------------------------
+// Compaction of the parent samples that carry weight: kept = w_p[kp] >
+// 2^-60 max_kp w_p, in index order.  A dropped sample changes no marginal
+// weight by more than K 2^-60 relative.  cw = ln w_p - ln K of each kept
+// sample; the list is padded to a multiple of 16 with cw = -inf.
+__global__ void k_compact(LevelView par, int K) {
+  const long long p = blockIdx.x;
+  __shared__ float red[32];
+  __shared__ int scan[1024];
+  const float* w = par.w + p * K;
+  float mx = 0.f;
+  for (int kp = threadIdx.x; kp < K; kp += blockDim.x) mx = fmaxf(mx, w[kp]);
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  float wmax = 0.f;
+  for (int j = 0; j < (int)(blockDim.x >> 5); ++j) wmax = fmaxf(wmax, red[j]);
+  const float thr = wmax * 8.673617379884035e-19f;  // 2^-60
+  const int per = (K + blockDim.x - 1) / blockDim.x;
+  const int k0 = threadIdx.x * per, k1 = min(K, k0 + per);
+  int cnt = 0;
+  for (int kp = k0; kp < k1; ++kp) cnt += (w[kp] > thr && w[kp] > 0.f) ? 1 : 0;
+  scan[threadIdx.x] = cnt;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const int add = threadIdx.x >= (unsigned)o ? scan[threadIdx.x - o] : 0;
+    __syncthreads();
+    scan[threadIdx.x] += add;
+    __syncthreads();
+  }
+  int pos = scan[threadIdx.x] - cnt;
+  const int total = scan[blockDim.x - 1];
+  const float lnK = logf((float)K);
+  for (int kp = k0; kp < k1; ++kp) {
+    if (w[kp] > thr && w[kp] > 0.f) {
+      par.cidx[p * K + pos] = kp;
+      par.cw[p * K + pos] = logf(w[kp]) - lnK;
+      ++pos;
+    }
+  }
+  const int npad = min(K, max(16, (total + 15) & ~15));
+  for (int j = total + threadIdx.x; j < npad; j += blockDim.x) {
+    par.cidx[p * K + j] = 0;
+    par.cw[p * K + j] = -INFINITY;
+  }
+  if (threadIdx.x == 0) par.ccnt[p] = total;
+}
+
+cudaError_t launch_compact(const LevelView& parent, int K, cudaStream_t s) {
+  if (parent.n == 0) return cudaSuccess;
+  k_compact<<<(unsigned)parent.n, 256, 0, s>>>(parent, K);
+  return cudaGetLastError();
+}
+
 // K5 (FP32): adjoint of the contraction = marginal weights (Eq. mmp with the
 // indicator moment; Sec. 3.2's source-term trick in closed form):
-//   w_e[k] = sum_kp w_p[kp] exp( S_e[kp][k] - log sum_k' exp S_e[kp][k'] ).
-// One thread per child sample k; the parent's samples stream through shared
-// memory with the per-(e, kp) shift log w_p[kp] - lt[e][kp] - log K folded in.
+//   w_e[k] = sum_kp w_p[kp] exp( S_e[kp][k] - log sum_k' exp S_e[kp][k'] ),
+// over the compacted parent samples.  One thread per child sample k; the kept
+// parent samples stream through shared memory with the per-(e, kp) shift
+// pc[kp] + ln w_p[kp] - ln K - lt[e][kp] folded in.  Elements whose parent
+// keeps more than max_eff samples are left to the tensor-core adjoint
+// (max_eff = 0: no limit).
 template <int MAXD>
-__global__ void __launch_bounds__(kRowTile) k_adj_simt(LevelView v, LevelView par, int K, int n_rt) {
+__global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView par, int K, int n_rt, int max_eff) {
   __shared__ float pms[kChunk * MAXD];
   __shared__ float pps[kChunk * MAXD];
   __shared__ float pcs[kChunk];
@@ -525,27 +626,29 @@ __global__ void __launch_bounds__(kRowTile) k_adj_simt(LevelView v, LevelView pa
   const int k = (blockIdx.x % n_rt) * blockDim.x + threadIdx.x;
   const int D = v.D;
   const long long p = v.parent[e];
+  const int n_eff = par.ccnt[p];
+  if (max_eff > 0 && n_eff > max_eff) return;  // uniform over the block
   const bool act = k < K;
   float zr[MAXD];
 #pragma unroll
   for (int d = 0; d < MAXD; ++d) zr[d] = (act && d < D) ? v.z[(e * K + k) * D + d] : 0.f;
   const float hk = act ? v.htil[e * K + k] : 0.f;
-  const float logK = logf((float)K);
   float acc = 0.f;
-  for (int k0 = 0; k0 < K; k0 += kChunk) {
-    const int nk = min(kChunk, K - k0);
+  for (int j0 = 0; j0 < n_eff; j0 += kChunk) {
+    const int nj = min(kChunk, n_eff - j0);
     __syncthreads();
     for (int i = threadIdx.x; i < kChunk * MAXD; i += blockDim.x) {
       const int j = i / MAXD, d = i % MAXD;
-      const bool ok = j < nk && d < D;
-      pms[i] = ok ? par.pm[(p * K + k0 + j) * D + d] : 0.f;
-      pps[i] = ok ? par.pp[(p * K + k0 + j) * D + d] : 0.f;
+      const bool ok = j < nj && d < D;
+      const int kp = ok ? par.cidx[p * K + j0 + j] : 0;
+      pms[i] = ok ? par.pm[(p * K + kp) * D + d] : 0.f;
+      pps[i] = ok ? par.pp[(p * K + kp) * D + d] : 0.f;
     }
     for (int j = threadIdx.x; j < kChunk; j += blockDim.x) {
       float sh = -INFINITY;
-      if (j < nk) {
-        const float wp = par.w[p * K + k0 + j];
-        if (wp > 0.f) sh = par.pc[p * K + k0 + j] + logf(wp) - v.lt[e * K + k0 + j] - logK;
+      if (j < nj) {
+        const int kp = par.cidx[p * K + j0 + j];
+        sh = par.pc[p * K + kp] + par.cw[p * K + j0 + j] - v.lt[e * K + kp];
       }
       pcs[j] = sh;
     }
@@ -567,62 +670,197 @@ __global__ void __launch_bounds__(kRowTile) k_adj_simt(LevelView v, LevelView pa
   if (act) v.w[e * K + k] = acc;
 }
 
+// Small-set adjoint with its own normaliser (used when the forward ran at a
+// different precision): one block per element; for each of the <= 16 kept
+// parent samples the row normaliser log sum_k exp S[kp][k] is recomputed in
+// FP32 over all K child samples, so every row of P(k | kp) sums to one in the
+// arithmetic that evaluates it.  Elements whose parent keeps more than
+// kSmallKept samples are left to the tensor-core adjoint.
+constexpr int kSmallKept = 16;
+
 template <int MAXD>
-static cudaError_t adj_simt_dispatch(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
-  const int thr = K >= kRowTile ? kRowTile : ((K + 31) / 32) * 32;
-  const int n_rt = (K + thr - 1) / thr;
-  k_adj_simt<MAXD><<<(unsigned)(v.n * n_rt), thr, 0, s>>>(v, par, K, n_rt);
+__global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, int K) {
+  __shared__ float pms[kSmallKept * MAXD];
+  __shared__ float pps[kSmallKept * MAXD];
+  __shared__ float pcs[kSmallKept];
+  __shared__ float red_m[kSmallKept][8];
+  __shared__ float red_s[kSmallKept][8];
+  __shared__ float lse[kSmallKept];
+  const long long e = blockIdx.x;
+  const int D = v.D;
+  const long long p = v.parent[e];
+  const int n_eff = par.ccnt[p];
+  if (n_eff > kSmallKept) return;
+  for (int i = threadIdx.x; i < kSmallKept * MAXD; i += blockDim.x) {
+    const int j = i / MAXD, d = i % MAXD;
+    const bool ok = j < n_eff && d < D;
+    const int kp = ok ? par.cidx[p * K + j] : 0;
+    pms[i] = ok ? par.pm[(p * K + kp) * D + d] : 0.f;
+    pps[i] = ok ? par.pp[(p * K + kp) * D + d] : 0.f;
+  }
+  if (threadIdx.x < kSmallKept) {
+    const int j = threadIdx.x;
+    pcs[j] = j < n_eff ? par.pc[p * K + par.cidx[p * K + j]] : 0.f;
+  }
+  __syncthreads();
+  // pass 1: row normalisers of the kept parent samples
+  float m[kSmallKept], sm[kSmallKept];
+#pragma unroll
+  for (int j = 0; j < kSmallKept; ++j) {
+    m[j] = -INFINITY;
+    sm[j] = 0.f;
+  }
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    float zr[MAXD];
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) zr[d] = d < D ? v.z[(e * K + k) * D + d] : 0.f;
+    const float hk = v.htil[e * K + k];
+#pragma unroll
+    for (int j = 0; j < kSmallKept; ++j) {
+      if (j < n_eff) {
+        float a = pcs[j] + hk;
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) {
+          const float t = zr[d] - pms[j * MAXD + d];
+          a = fmaf(pps[j * MAXD + d], t * t, a);
+        }
+        if (a > m[j]) {
+          sm[j] = sm[j] * expf(m[j] - a) + 1.f;
+          m[j] = a;
+        } else {
+          sm[j] += expf(a - m[j]);
+        }
+      }
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < kSmallKept; ++j) {
+    float mj = m[j], sj = sm[j];
+    for (int o = 16; o; o >>= 1) {
+      const float mo = __shfl_xor_sync(0xffffffffu, mj, o), so = __shfl_xor_sync(0xffffffffu, sj, o);
+      const float M = fmaxf(mj, mo);
+      sj = (mj == -INFINITY ? 0.f : sj * expf(mj - M)) + (mo == -INFINITY ? 0.f : so * expf(mo - M));
+      mj = M;
+    }
+    if (lane == 0) {
+      red_m[j][warp] = mj;
+      red_s[j][warp] = sj;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kSmallKept) {
+    const int j = threadIdx.x;
+    float M = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmaxf(M, red_m[j][w]);
+    float S = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      if (red_m[j][w] > -INFINITY) S += red_s[j][w] * expf(red_m[j][w] - M);
+    // shift of the kept sample: ln w_p - ln K + ln K - log sum exp = ln w_p - lse
+    lse[j] = j < n_eff ? par.cw[p * K + j] + logf((float)K) - (M + logf(S)) : -INFINITY;
+  }
+  __syncthreads();
+  // pass 2: marginal weights
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    float zr[MAXD];
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) zr[d] = d < D ? v.z[(e * K + k) * D + d] : 0.f;
+    const float hk = v.htil[e * K + k];
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < kSmallKept; ++j) {
+      if (j < n_eff) {
+        float a = pcs[j] + hk + lse[j];
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) {
+          const float t = zr[d] - pms[j * MAXD + d];
+          a = fmaf(pps[j * MAXD + d], t * t, a);
+        }
+        acc += expf(a);
+      }
+    }
+    v.w[e * K + k] = acc;
+  }
+}
+
+cudaError_t launch_adj_small(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)v.n;
+  if (v.D <= 4) k_adj_small<4><<<grid, 256, 0, s>>>(v, par, K);
+  else if (v.D <= 8) k_adj_small<8><<<grid, 256, 0, s>>>(v, par, K);
+  else if (v.D <= 20) k_adj_small<20><<<grid, 256, 0, s>>>(v, par, K);
+  else if (v.D <= 32) k_adj_small<32><<<grid, 256, 0, s>>>(v, par, K);
+  else k_adj_small<64><<<grid, 256, 0, s>>>(v, par, K);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_simt(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
+template <int MAXD>
+static cudaError_t adj_compact_dispatch(const LevelView& v, const LevelView& par, int K, int max_eff, cudaStream_t s) {
+  const int thr = K >= kRowTile ? kRowTile : ((K + 31) / 32) * 32;
+  const int n_rt = (K + thr - 1) / thr;
+  k_adj_compact<MAXD><<<(unsigned)(v.n * n_rt), thr, 0, s>>>(v, par, K, n_rt, max_eff);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_compact(const LevelView& v, const LevelView& par, int K, int max_eff, cudaStream_t s) {
   if (v.n == 0) return cudaSuccess;
-  if (v.D <= 4) return adj_simt_dispatch<4>(v, par, K, s);
-  if (v.D <= 8) return adj_simt_dispatch<8>(v, par, K, s);
-  if (v.D <= 20) return adj_simt_dispatch<20>(v, par, K, s);
-  if (v.D <= 32) return adj_simt_dispatch<32>(v, par, K, s);
-  return adj_simt_dispatch<64>(v, par, K, s);
+  if (v.D <= 4) return adj_compact_dispatch<4>(v, par, K, max_eff, s);
+  if (v.D <= 8) return adj_compact_dispatch<8>(v, par, K, max_eff, s);
+  if (v.D <= 20) return adj_compact_dispatch<20>(v, par, K, max_eff, s);
+  if (v.D <= 32) return adj_compact_dispatch<32>(v, par, K, max_eff, s);
+  return adj_compact_dispatch<64>(v, par, K, max_eff, s);
 }
 
 // ---------------------------------------------------------------------------
-// K6: moments m_e = sum_k w_e[k] T(z_e^k) (Eq. momone(z)), FP64 accumulation
-// in a fixed order.  Thread t of a block owns dimension t % D; consecutive
-// threads read consecutive floats of z.
+// K6: moments m_e = sum_k w_e[k] T(z_e^k) (Eq. momone(z)).  Thread t of a
+// block owns dimension t % D (consecutive threads read consecutive floats of
+// z) and accumulates its share in FP32 with Kahan compensation; the shares
+// are added in FP64 in a fixed order.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 __global__ void k_moments(LevelView v, int K, double* mom) {
   extern __shared__ double smd[];
   const long long e = blockIdx.x;
   const int D = v.D;
   const int per = blockDim.x / D;
   const int t = threadIdx.x;
-  double a0 = 0.0, a1 = 0.0;
+  float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
   if (t < per * D) {
     const int d = t % D;
     for (int k = t / D; k < K; k += per) {
-      const double wk = v.w[e * K + k];
-      const double zv = v.z[(e * K + k) * D + d];
+      const float wk = v.w[e * K + k];
+      const float zv = v.z[(e * K + k) * D + d];
+      float t0, t1;
       if (v.qfam == QEM_Q_GAUSS) {
-        a0 += wk * zv;
-        a1 += wk * zv * zv;
+        t0 = zv;
+        t1 = zv * zv;
       } else if (v.qfam == QEM_Q_GAMMA) {
-        a0 += wk * zv;
-        a1 += wk * log(zv);
+        t0 = zv;
+        t1 = logf(zv);
       } else {
-        a0 += wk * log(zv);
-        a1 += wk * log1p(-zv);
+        t0 = logf(zv);
+        t1 = log1pf(-zv);
       }
+      kahan_add(s0, c0, wk * t0);
+      kahan_add(s1, c1, wk * t1);
     }
   }
-  smd[2 * t] = a0;
-  smd[2 * t + 1] = a1;
+  smd[2 * t] = (double)s0 - (double)c0;
+  smd[2 * t + 1] = (double)s1 - (double)c1;
   __syncthreads();
   if (t < D) {
-    double s0 = 0.0, s1 = 0.0;
+    double a0 = 0.0, a1 = 0.0;
     for (int j = 0; j < per; ++j) {
-      s0 += smd[2 * (j * D + t)];
-      s1 += smd[2 * (j * D + t) + 1];
+      a0 += smd[2 * (j * D + t)];
+      a1 += smd[2 * (j * D + t) + 1];
     }
-    mom[(e * 2) * D + t] = s0;
-    mom[(e * 2 + 1) * D + t] = s1;
+    mom[(e * 2) * D + t] = a0;
+    mom[(e * 2 + 1) * D + t] = a1;
   }
 }
 

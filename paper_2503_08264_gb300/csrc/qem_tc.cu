@@ -38,9 +38,7 @@ struct TcBuffers {
   __nv_bfloat16* cfeat[QEM_MAX_LEVELS] = {};   // compacted parent rows, same layout
   float* rowc[QEM_MAX_LEVELS] = {};            // [n_{l-1}][K] row constants (nats)
   float* center[QEM_MAX_LEVELS] = {};          // [n_{l-1}][D_l]
-  int* cidx[QEM_MAX_LEVELS] = {};              // [n_{l-1}][K] compacted parent sample indices
-  int* ccnt[QEM_MAX_LEVELS] = {};              // [n_{l-1}] number of kept parent samples
-  float* cbase[QEM_MAX_LEVELS] = {};           // [n_{l-1}][K] rowc + ln w_p - ln K of kept samples
+  float* dcol[QEM_MAX_LEVELS] = {};            // [n_l][K] adjoint column shifts (log2 units)
 };
 
 namespace tc {
@@ -310,61 +308,40 @@ __global__ void k_child_features(LevelView ch, int mean_logvar, float pp_fixed, 
   }
 }
 
-// Compaction of the parent samples that carry weight (adjoint columns):
-// kept = w_p[kp] > 2^-60 max_kp w_p, in index order; rows gathered into cfeat;
-// the count is padded to a multiple of 16 with rows whose base is -inf.
-__global__ void k_compact(LevelView par, int K, int fk, const __nv_bfloat16* afeat, const float* rowc,
-                          __nv_bfloat16* cfeat, int* cidx, int* ccnt, float* cbase) {
+// Adjoint operands of the parents whose compacted weight list is longer than
+// `small` (the others are handled on the CUDA cores): the kept rows of the
+// parent features, gathered in order (padding rows repeat row 0 and carry a
+// -inf shift).
+__global__ void k_gather(LevelView par, int K, int fk, int small, const __nv_bfloat16* afeat, __nv_bfloat16* cfeat) {
   const long long p = blockIdx.x;
-  __shared__ float red[32];
-  __shared__ int scan[1024];
-  const float* w = par.w + p * K;
-  float mx = 0.f;
-  for (int kp = threadIdx.x; kp < K; kp += blockDim.x) mx = fmaxf(mx, w[kp]);
-  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  float wmax = 0.f;
-  for (int j = 0; j < (int)(blockDim.x >> 5); ++j) wmax = fmaxf(wmax, red[j]);
-  const float thr = wmax * 8.673617379884035e-19f;  // 2^-60
-  // contiguous range of kp per thread; count, block scan, scatter (order preserving)
-  const int per = (K + blockDim.x - 1) / blockDim.x;
-  const int k0 = threadIdx.x * per, k1 = min(K, k0 + per);
-  int cnt = 0;
-  for (int kp = k0; kp < k1; ++kp) cnt += (w[kp] > thr && w[kp] > 0.f) ? 1 : 0;
-  scan[threadIdx.x] = cnt;
-  __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    const int v = threadIdx.x >= (unsigned)o ? scan[threadIdx.x - o] : 0;
-    __syncthreads();
-    scan[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int pos = scan[threadIdx.x] - cnt;
-  const int total = scan[blockDim.x - 1];
-  const float lnK = logf((float)K);
-  for (int kp = k0; kp < k1; ++kp) {
-    if (w[kp] > thr && w[kp] > 0.f) {
-      cidx[p * K + pos] = kp;
-      cbase[p * K + pos] = rowc[p * K + kp] + logf(w[kp]) - lnK;
-      ++pos;
-    }
-  }
-  const int npad = max(16, (total + 15) & ~15);
-  for (int j = total + threadIdx.x; j < npad; j += blockDim.x) {
-    cidx[p * K + j] = 0;
-    cbase[p * K + j] = -INFINITY;
-  }
-  if (threadIdx.x == 0) ccnt[p] = total;
-  __syncthreads();
-  // gather the kept rows (16-byte granules) into the compacted operand
+  const int n_eff = par.ccnt[p];
+  if (n_eff <= small) return;
+  const int npad = min(K, (n_eff + 15) & ~15);
   const int gran = fk >> 3;
   const uint4* src = reinterpret_cast<const uint4*>(afeat + p * (long long)K * fk);
   uint4* dst = reinterpret_cast<uint4*>(cfeat + p * (long long)K * fk);
   for (int i = threadIdx.x; i < npad * gran; i += blockDim.x) {
     const int j = i / gran, g = i % gran;
-    const int kp = cidx[p * K + j];
+    const int kp = par.cidx[p * K + j];
     dst[canon(j, g * 8, fk) >> 3] = src[canon(kp, g * 8, fk) >> 3];
+  }
+}
+
+// Column shifts of the adjoint tile of element e (log2 units):
+//   d_j = log2e (rowc[kp_j] + ln w_p[kp_j] - ln K - lt_e[kp_j]),  -inf on padding.
+__global__ void k_dcol(LevelView ch, LevelView par, int K, int small, const float* rowc, float* dcol) {
+  const long long e = blockIdx.x;
+  const long long p = ch.parent[e];
+  const int n_eff = par.ccnt[p];
+  if (n_eff <= small) return;
+  const int npad = min(K, (n_eff + 15) & ~15);
+  for (int j = threadIdx.x; j < npad; j += blockDim.x) {
+    float d = -INFINITY;
+    if (j < n_eff) {
+      const int kp = par.cidx[p * K + j];
+      d = (rowc[p * K + kp] + par.cw[p * K + j] - ch.lt[e * K + kp]) * kLog2e;
+    }
+    dcol[e * K + j] = d;
   }
 }
 
@@ -377,11 +354,10 @@ struct ContractArgs {
   const __nv_bfloat16* cols_feat;   // B operand source (forward: child features, adjoint: compacted parents)
   const float* rowc;                // forward
   float* lt;                        // forward output [n][K]
-  const int* ccnt;                  // adjoint
-  const int* cidx;
-  const float* cbase;
-  const float* lt_in;
-  float* w_out;                     // adjoint output [n][K]
+  const int* ccnt;                  // adjoint: kept parent samples per parent
+  int small;                        //          parents keeping <= small samples are skipped
+  const float* dcol;                //          column shifts [n][K] (log2 units)
+  float* w_out;                     //          output [n][K]
   Ctl* ctl;
   long long timeout_cycles;
 };
@@ -389,15 +365,16 @@ struct ContractArgs {
 struct Smem {
   uint8_t* a0;       // two A tiles, a_stride apart
   uint8_t* b0;       // two B chunks, b_stride apart
-  uint8_t* d0;       // two d tiles (adjoint), kMaxN*16*2 apart
+  float* d0;         // two column-shift rows (adjoint), kMaxN floats apart
   uint32_t a_stride, b_stride;
-  uint8_t* ax;
   uint64_t* a_full;
   uint64_t* a_empty;
   uint64_t* b_full;
   uint64_t* b_empty;
   uint64_t* t_full;
   uint64_t* t_empty;
+  uint64_t* d_full;   // adjoint column shifts landed in slot
+  uint64_t* d_empty;  // adjoint column shifts of slot consumed by the epilogue
   uint64_t* done;
   uint32_t* tmem_base;
   volatile int* abort_flag;
@@ -408,8 +385,8 @@ struct Smem {
 __host__ __device__ inline size_t contract_smem_bytes(int fk, bool adj) {
   const size_t a = (size_t)kRows * fk * 2, b = (size_t)kMaxN * fk * 2;
   size_t tot = 1024 + 2 * a + 2 * b;
-  if (adj) tot += 2 * (size_t)kMaxN * 16 * 2 + (size_t)kRows * 16 * 2;
-  tot += 16 * 8 + 16 + kRows * sizeof(float2);
+  if (adj) tot += 2 * (size_t)kMaxN * sizeof(float);
+  tot += 24 * 8 + 16 + kRows * sizeof(float2);
   return tot;
 }
 
@@ -422,10 +399,10 @@ __device__ __forceinline__ Smem carve(uint8_t* raw, int fk, bool adj) {
   s.a0 = p; p += 2 * a;
   s.b0 = p; p += 2 * b;
   if (adj) {
-    s.d0 = p; p += 2 * kMaxN * 16 * 2;
-    s.ax = p; p += kRows * 16 * 2;
+    s.d0 = reinterpret_cast<float*>(p);
+    p += 2 * kMaxN * sizeof(float);
   } else {
-    s.d0 = s.ax = nullptr;
+    s.d0 = nullptr;
   }
   uint64_t* bars = reinterpret_cast<uint64_t*>(p);
   s.a_full = bars + 0;
@@ -434,8 +411,10 @@ __device__ __forceinline__ Smem carve(uint8_t* raw, int fk, bool adj) {
   s.b_empty = bars + 6;
   s.t_full = bars + 8;
   s.t_empty = bars + 10;
-  s.done = bars + 12;
-  p += 16 * 8;
+  s.d_full = bars + 12;
+  s.d_empty = bars + 14;
+  s.done = bars + 16;
+  p += 24 * 8;
   s.tmem_base = reinterpret_cast<uint32_t*>(p);
   s.abort_flag = reinterpret_cast<volatile int*>(p + 4);
   s.stop_flag = reinterpret_cast<volatile int*>(p + 8);
@@ -457,23 +436,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&s.a_full[i], 1);
       mbar_init(&s.a_empty[i], 1);
-      mbar_init(&s.b_full[i], ADJ ? 2 : 1);
+      mbar_init(&s.b_full[i], 1);
       mbar_init(&s.b_empty[i], 1);
       mbar_init(&s.t_full[i], 1);
       mbar_init(&s.t_empty[i], 8);
+      mbar_init(&s.d_full[i], 1);
+      mbar_init(&s.d_empty[i], 8);
     }
     mbar_init(s.done, 1);
     *s.abort_flag = 0;
     *s.stop_flag = 0;
     fence_barrier_init();
-  }
-  if (ADJ) {  // constant A operand of the extra k-step: columns 0..2 = 1 (they pick up d)
-    __nv_bfloat16* ax = reinterpret_cast<__nv_bfloat16*>(s.ax);
-    for (int i = threadIdx.x; i < kRows * 16; i += blockDim.x) {
-      const int r = i / 16, c = i % 16;
-      ax[canon(r, c, 16)] = __float2bfloat16_rn(c < 3 ? 1.f : 0.f);
-    }
-    fence_proxy_async_smem();
   }
   if (warp == 1) {
     tmem_alloc(s.tmem_base, 512);
@@ -488,11 +461,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
     // ------------------------------------------------------------ producer
     int as = 0, bs = 0;
     uint32_t aph = 0, bph = 0;
-    uint32_t armed = 0, last = 0;  // bit i: a slot i, bit 2+i: b slot i
+    uint32_t armed = 0, last = 0;  // bit i: a slot i, bit 2+i: b slot i, bit 4+i: d slot i
     for (long long u = blockIdx.x; u < a.n_units; u += gridDim.x) {
       const long long e = u / a.rtiles;
       const int rt = (int)(u % a.rtiles);
       const long long p = a.parent[e];
+      if (ADJ && a.ccnt[p] <= a.small) continue;
       const long long row_elt = ADJ ? e : p;
       bool ok = true;
       if (lane == 0) {
@@ -519,33 +493,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
             const uint32_t bytes = (uint32_t)nc * fk * 2;
             mbar_expect_tx(&s.b_full[bs], bytes);
             bulk_g2s((s.b0 + bs * s.b_stride), a.cols_feat + (col_elt * K + c0) * fk, bytes, &s.b_full[bs]);
+            // the column shifts live until the epilogue has used them (own barriers)
+            if (ADJ) ok = mbar_wait(&s.d_empty[bs], bph ^ 1, lim, s.abort_flag);
+            if (ADJ && ok) {
+              mbar_expect_tx(&s.d_full[bs], (uint32_t)nc * 4u);
+              bulk_g2s(s.d0 + bs * kMaxN, a.dcol + e * K + c0, (uint32_t)nc * 4u, &s.d_full[bs]);
+              armed |= 16u << bs;
+              last = (last & ~(16u << bs)) | (bph << (4 + bs));
+            }
             armed |= 4u << bs;
             last = (last & ~(4u << bs)) | (bph << (2 + bs));
           }
         }
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         if (!ok) break;
-        if (ADJ) {
-          // d columns of this chunk: d_j = log2e (cbase_j - lt_e[kp_j]), split in three
-          __nv_bfloat16* dt = reinterpret_cast<__nv_bfloat16*>((s.d0 + bs * (kMaxN * 16 * 2)));
-          for (int j = lane; j < nc; j += 32) {
-            const int col = c0 + j;
-            const float base = a.cbase[p * K + col];
-            float dv = kNegBig;
-            if (base > -INFINITY) dv = (base - a.lt_in[e * K + a.cidx[p * K + col]]) * kLog2e;
-            __align__(16) __nv_bfloat16 g[8];
-            split3(dv, g[0], g[1], g[2]);
-#pragma unroll
-            for (int t = 3; t < 8; ++t) g[t] = __float2bfloat16_rn(0.f);
-            *reinterpret_cast<uint4*>(dt + canon(j, 0, 16)) = *reinterpret_cast<const uint4*>(g);
-#pragma unroll
-            for (int t = 0; t < 3; ++t) g[t] = __float2bfloat16_rn(0.f);
-            *reinterpret_cast<uint4*>(dt + canon(j, 8, 16)) = *reinterpret_cast<const uint4*>(g);
-          }
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&s.b_full[bs]);
-        }
         bs ^= 1;
         if (bs == 0) bph ^= 1;
       }
@@ -558,6 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       for (int i = 0; i < 2; ++i) {
         if (armed & (1u << i)) mbar_wait(&s.a_full[i], (last >> i) & 1u, lim, &never);
         if (armed & (4u << i)) mbar_wait(&s.b_full[i], (last >> (2 + i)) & 1u, lim, &never);
+        if (armed & (16u << i)) mbar_wait(&s.d_full[i], (last >> (4 + i)) & 1u, lim, &never);
       }
     }
   } else if (warp == 1) {
@@ -569,6 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       for (long long u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
         const long long e = u / a.rtiles;
         const long long p = a.parent[e];
+        if (ADJ && a.ccnt[p] <= a.small) continue;
         ok = mbar_wait(&s.a_full[as], aph, lim, s.abort_flag);
         if (!ok) break;
         const int ncols = ADJ ? max(16, (a.ccnt[p] + 15) & ~15) : K;
@@ -583,11 +546,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
             const uint64_t ad = smem_desc((s.a0 + as * s.a_stride) + ks * 256, 128, sbo);
             const uint64_t bd = smem_desc((s.b0 + bs * s.b_stride) + ks * 256, 128, sbo);
             mma_bf16(d_tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
-          }
-          if (ADJ) {
-            const uint64_t ad = smem_desc(s.ax, 128, 256);
-            const uint64_t bd = smem_desc((s.d0 + bs * (kMaxN * 16 * 2)), 128, 256);
-            mma_bf16(d_tmem, ad, bd, idesc, 1u);
           }
           mma_commit(&s.b_empty[bs]);
           mma_commit(&s.t_full[ts]);
@@ -621,28 +579,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       const long long e = u / a.rtiles;
       const int rt = (int)(u % a.rtiles);
       const long long p = a.parent[e];
+      if (ADJ && a.ccnt[p] <= a.small) continue;
       const int ncols = ADJ ? max(16, (a.ccnt[p] + 15) & ~15) : K;
       float m = -INFINITY, sacc = 0.f;
       bool ok = true;
       for (int c0 = 0; c0 < ncols && ok; c0 += kMaxN) {
         const int nc = min(kMaxN, ncols - c0);
         ok = mbar_wait(&s.t_full[ts], tph, lim, s.abort_flag);
+        if (ok && ADJ) ok = mbar_wait(&s.d_full[ts], tph, lim, s.abort_flag);
         if (!ok) break;
         tc_fence_after();
         const int hw = nc >> 1;
         const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ts * kMaxN + half * hw);
+        const float* dsm = ADJ ? s.d0 + ts * kMaxN : nullptr;  // chunk g uses B, TMEM and d slot g % 2
         int c = 0;
         for (; c + 32 <= hw; c += 32) {
           float v[32];
           tmem_ld32(tbase + c, v);
           if (ADJ) {
+            const float4* d4 = reinterpret_cast<const float4*>(dsm + half * hw + c);
             float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
-              p0 += ex2f(v[j]);
-              p1 += ex2f(v[j + 1]);
-              p2 += ex2f(v[j + 2]);
-              p3 += ex2f(v[j + 3]);
+              const float4 dv = d4[j >> 2];
+              p0 += ex2f(v[j] + dv.x);
+              p1 += ex2f(v[j + 1] + dv.y);
+              p2 += ex2f(v[j + 2] + dv.z);
+              p3 += ex2f(v[j + 3] + dv.w);
             }
             sacc += (p0 + p1) + (p2 + p3);
           } else {
@@ -685,12 +648,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
           tmem_ld8(tbase + c, v);
           if (ADJ) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) sacc += ex2f(v[j]);
+            for (int j = 0; j < 8; ++j) sacc += ex2f(v[j] + dsm[half * hw + c + j]);
           }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&s.t_empty[ts]);
+        if (lane == 0) {
+          mbar_arrive(&s.t_empty[ts]);
+          if (ADJ) mbar_arrive(&s.d_empty[ts]);
+        }
         ts ^= 1;
         if (ts == 0) tph ^= 1;
       }
@@ -822,9 +788,7 @@ qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base,
     tb.cfeat[l] = (__nv_bfloat16*)take((size_t)pa.n * K * fk * 2);
     tb.rowc[l] = (float*)take((size_t)pa.n * K * 4);
     tb.center[l] = (float*)take((size_t)pa.n * c.dim * 4);
-    tb.cidx[l] = (int*)take((size_t)pa.n * K * 4);
-    tb.ccnt[l] = (int*)take((size_t)pa.n * 4);
-    tb.cbase[l] = (float*)take((size_t)pa.n * K * 4);
+    tb.dcol[l] = (float*)take((size_t)c.n * K * 4);
   }
   *bytes = off;
   if (base) {
@@ -889,10 +853,9 @@ static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
   } else {
     a.rows_feat = T.bfeat[l];
     a.cols_feat = T.cfeat[l];
-    a.ccnt = T.ccnt[l];
-    a.cidx = T.cidx[l];
-    a.cbase = T.cbase[l];
-    a.lt_in = ch.lt;
+    a.ccnt = P->lv[l - 1].ccnt;
+    a.small = kTcAdjointMinKept;
+    a.dcol = T.dcol[l];
     a.w_out = ch.w;
   }
   const long long grid = a.n_units < P->num_sms ? a.n_units : P->num_sms;
@@ -906,12 +869,13 @@ static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
 
 cudaError_t tc_forward(qem_plan_t P, int l) { return launch_contract(P, l, false); }
 
-cudaError_t tc_compact(qem_plan_t P, int l) {
+cudaError_t tc_adjoint_prep(qem_plan_t P, int l) {
   TcBuffers& T = *P->tc;
   const LevelView& pa = P->lv[l - 1];
-  if (pa.n == 0) return cudaSuccess;
-  k_compact<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, P->K, T.fk[l], T.afeat[l], T.rowc[l], T.cfeat[l], T.cidx[l],
-                                                    T.ccnt[l], T.cbase[l]);
+  const LevelView& ch = P->lv[l];
+  if (pa.n > 0)
+    k_gather<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, P->K, T.fk[l], kTcAdjointMinKept, T.afeat[l], T.cfeat[l]);
+  if (ch.n > 0) k_dcol<<<(unsigned)ch.n, 256, 0, P->stream>>>(ch, pa, P->K, kTcAdjointMinKept, T.rowc[l], T.dcol[l]);
   return cudaGetLastError();
 }
 

@@ -89,3 +89,19 @@ def test_plain_bf16_reports_error():
     lp = np.max(np.abs(got["log_pmp"] - ref["log_pmp"]) / np.abs(ref["log_pmp"]))
     print("plain bf16: log_pmp rel", lp, "moments", moment_errors(model, q, got["mom"], ref["mom"]))
     assert lp < 1e-2
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-3), ("fp32", 1e-5)])
+def test_dense_parent_weights(precision, tol):
+    """Few children per parent: the parents' weights stay spread, so the
+    adjoint runs over hundreds of kept parent samples (the tensor-core adjoint
+    for the split-BF16 path)."""
+    model = S.batched_three_level(n_inst=4, D=8, seed=51, groups=(2, 3), units=(1, 2))
+    K = 256
+    q = S.initial_q(model)
+    eps = S.noise(model, K, seed=52)
+    got, ref = run_pair(model, K, q, eps, precision=precision)
+    kept = [(r > 1e-18 * r.max(1, keepdims=True)).sum(1).min() for r in ref["w"][:2]]
+    print("min kept parent samples per level", kept)
+    assert min(kept) > 16
+    assert_parity(model, q, got, ref, tol, tol, tol)
