@@ -39,6 +39,8 @@ UNIT = "pairs/s"
 WORKLOADS = {
     "hier_logistic_M5000_N10_K1024": (lambda seed: S.hier_logistic(M=5000, N=10, seed=seed), 1024, "bf16x3"),
     "hier_logistic_M300_N5_K128": (lambda seed: S.hier_logistic(M=300, N=5, seed=seed), 128, "fp32"),
+    # profiling case: the large workload's shapes with a fifth of its plate (fits an ncu capture)
+    "hier_logistic_M1000_N10_K1024": (lambda seed: S.hier_logistic(M=1000, N=10, seed=seed), 1024, "bf16x3"),
     "batched_three_level_256_K256": (lambda seed: S.batched_three_level(n_inst=256, seed=seed), 256, "bf16x3"),
 }
 DEFAULT_WORKLOAD = "hier_logistic_M5000_N10_K1024"

@@ -10,6 +10,9 @@
 namespace qem {
 
 constexpr int kMaxDim = 64;
+// Adjoints: a parent element keeping at most this many weighted samples is
+// handled on the CUDA cores, a denser one on the tensor cores.
+constexpr int kSmallKept = 4;
 constexpr float kLog2Pi = 1.8378770664093453f;
 constexpr double kLog2PiD = 1.8378770664093454835606594728112;
 
@@ -123,17 +126,30 @@ __device__ __forceinline__ float neg2_log_unit(uint32_t x) {
 
 __device__ __forceinline__ float unit_of(uint32_t x) { return ((float)x + 0.5f) * 2.3283064365386963e-10f; }
 
+// -2 log u for the Box-Muller radius: the fast logarithm where its relative
+// error is small (u < 1/2), the accurate log1p of -(1-u) near u = 1.
+__device__ __forceinline__ float neg2_log_unit_fast(uint32_t x) {
+  if (x < 0x80000000u) return -2.f * __logf(((float)x + 0.5f) * 2.3283064365386963e-10f);
+  const float one_minus_u = ((float)(0xFFFFFFFFu - x) + 0.5f) * 2.3283064365386963e-10f;
+  return -2.f * log1pf(-one_minus_u);
+}
+
 // Four N(0,1) numbers of block `blk` of one sample (Box-Muller on (u0,u1), (u2,u3)).
+// The angle 2 pi u is evaluated as pi + (2 pi u - pi) with the fast sine and
+// cosine on (-pi, pi) (absolute error ~2^-21), so the draws agree with an
+// exact evaluation of the same uniforms to ~1e-6.
 __device__ __forceinline__ float4 normal4(unsigned long long seed, unsigned long long iter, int level,
                                           unsigned long long sample, uint32_t blk) {
   const uint4 r = philox4x32_10(
       make_uint4((uint32_t)sample, (uint32_t)(sample >> 32), ((uint32_t)level << 24) | blk, (uint32_t)iter),
       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const float t0 = fmaf(6.283185307179586f, unit_of(r.y), -3.141592653589793f);
+  const float t1 = fmaf(6.283185307179586f, unit_of(r.w), -3.141592653589793f);
   float s0, c0, s1, c1;
-  sincospif(2.f * unit_of(r.y), &s0, &c0);
-  sincospif(2.f * unit_of(r.w), &s1, &c1);
-  const float r0 = sqrtf(neg2_log_unit(r.x)), r1 = sqrtf(neg2_log_unit(r.z));
-  return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+  __sincosf(t0, &s0, &c0);
+  __sincosf(t1, &s1, &c1);
+  const float r0 = sqrtf(neg2_log_unit_fast(r.x)), r1 = sqrtf(neg2_log_unit_fast(r.z));
+  return make_float4(-r0 * c0, -r0 * s0, -r1 * c1, -r1 * s1);
 }
 
 // One noise number of index idx (normal or uniform slot, as the family's layout says).
@@ -183,6 +199,7 @@ cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* lo
 cudaError_t launch_compact(const LevelView& parent, int K, cudaStream_t s);
 cudaError_t launch_adj_compact(const LevelView& v, const LevelView& parent, int K, int max_eff, cudaStream_t s);
 cudaError_t launch_adj_small(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
+cudaError_t configure_adj_small(int D, int K);
 cudaError_t launch_moments(const LevelView& v, int K, double* mom, cudaStream_t s);
 cudaError_t launch_mstep(const LevelView& v, const double* mom, double* m, float* q, double lambda,
                          double sched_p, double var_floor, long long t_host, const Ctl* ctl, cudaStream_t s);

@@ -556,6 +556,14 @@ cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* lo
 }
 
 // ---------------------------------------------------------------------------
+// Loads samples [k0, k0+nk) of element e into shared rows of stride D+1
+// (coalesced global reads; conflict-free row reads for odd strides).
+__device__ __forceinline__ void stage_samples(const LevelView& v, long long e, int K, int k0, int nk, float* zc) {
+  const int D = v.D;
+  const float* src = v.z + (e * K + k0) * (long long)D;
+  for (int i = threadIdx.x; i < nk * D; i += blockDim.x) zc[(i / D) * (D + 1) + (i % D)] = src[i];
+}
+
 // Compaction of the parent samples that carry weight: kept = w_p[kp] >
 // 2^-60 max_kp w_p, in index order.  A dropped sample changes no marginal
 // weight by more than K 2^-60 relative.  cw = ln w_p - ln K of each kept
@@ -629,9 +637,13 @@ __global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView
   const int n_eff = par.ccnt[p];
   if (max_eff > 0 && n_eff > max_eff) return;  // uniform over the block
   const bool act = k < K;
+  extern __shared__ float zc[];  // [blockDim][D+1]
+  const int k0 = (int)(blockIdx.x % n_rt) * blockDim.x;
+  stage_samples(v, e, K, k0, min((int)blockDim.x, K - k0), zc);
+  __syncthreads();
   float zr[MAXD];
 #pragma unroll
-  for (int d = 0; d < MAXD; ++d) zr[d] = (act && d < D) ? v.z[(e * K + k) * D + d] : 0.f;
+  for (int d = 0; d < MAXD; ++d) zr[d] = (act && d < D) ? zc[threadIdx.x * (D + 1) + d] : 0.f;
   const float hk = act ? v.htil[e * K + k] : 0.f;
   float acc = 0.f;
   for (int j0 = 0; j0 < n_eff; j0 += kChunk) {
@@ -671,21 +683,23 @@ __global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView
 }
 
 // Small-set adjoint with its own normaliser (used when the forward ran at a
-// different precision): one block per element; for each of the <= 16 kept
-// parent samples the row normaliser log sum_k exp S[kp][k] is recomputed in
-// FP32 over all K child samples, so every row of P(k | kp) sums to one in the
-// arithmetic that evaluates it.  Elements whose parent keeps more than
-// kSmallKept samples are left to the tensor-core adjoint.
-constexpr int kSmallKept = 16;
-
+// different precision): one block per element; for each of the <= kSmallKept
+// kept parent samples the log-factor of every child sample is evaluated once
+// in FP32 (kept in shared memory), its row normaliser log sum_k exp S[kp][k]
+// is reduced over the block, and the marginal weights follow, so every row of
+// P(k | kp) sums to one in the arithmetic that evaluates it.  Elements whose
+// parent keeps more samples are left to the tensor-core adjoint.
 template <int MAXD>
 __global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, int K) {
+  extern __shared__ float dyn[];
+  float* zc = dyn;                          // [256][D+1] staged samples
+  float* av = zc + 256 * (v.D + 1);         // [kSmallKept][K] log-factors (nats)
   __shared__ float pms[kSmallKept * MAXD];
   __shared__ float pps[kSmallKept * MAXD];
   __shared__ float pcs[kSmallKept];
   __shared__ float red_m[kSmallKept][8];
   __shared__ float red_s[kSmallKept][8];
-  __shared__ float lse[kSmallKept];
+  __shared__ float shift[kSmallKept];
   const long long e = blockIdx.x;
   const int D = v.D;
   const long long p = v.parent[e];
@@ -702,18 +716,22 @@ __global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, i
     const int j = threadIdx.x;
     pcs[j] = j < n_eff ? par.pc[p * K + par.cidx[p * K + j]] : 0.f;
   }
-  __syncthreads();
-  // pass 1: row normalisers of the kept parent samples
   float m[kSmallKept], sm[kSmallKept];
 #pragma unroll
   for (int j = 0; j < kSmallKept; ++j) {
     m[j] = -INFINITY;
     sm[j] = 0.f;
   }
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+  for (int k0 = 0; k0 < K; k0 += blockDim.x) {
+    const int nk = min((int)blockDim.x, K - k0);
+    __syncthreads();
+    stage_samples(v, e, K, k0, nk, zc);
+    __syncthreads();
+    if ((int)threadIdx.x >= nk) continue;
+    const int k = k0 + threadIdx.x;
     float zr[MAXD];
 #pragma unroll
-    for (int d = 0; d < MAXD; ++d) zr[d] = d < D ? v.z[(e * K + k) * D + d] : 0.f;
+    for (int d = 0; d < MAXD; ++d) zr[d] = d < D ? zc[threadIdx.x * (D + 1) + d] : 0.f;
     const float hk = v.htil[e * K + k];
 #pragma unroll
     for (int j = 0; j < kSmallKept; ++j) {
@@ -724,6 +742,7 @@ __global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, i
           const float t = zr[d] - pms[j * MAXD + d];
           a = fmaf(pps[j * MAXD + d], t * t, a);
         }
+        av[j * K + k] = a;
         if (a > m[j]) {
           sm[j] = sm[j] * expf(m[j] - a) + 1.f;
           m[j] = a;
@@ -756,29 +775,15 @@ __global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, i
     float S = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
       if (red_m[j][w] > -INFINITY) S += red_s[j][w] * expf(red_m[j][w] - M);
-    // shift of the kept sample: ln w_p - ln K + ln K - log sum exp = ln w_p - lse
-    lse[j] = j < n_eff ? par.cw[p * K + j] + logf((float)K) - (M + logf(S)) : -INFINITY;
+    // ln w_p - log sum_k exp S[kp][k]   (cw = ln w_p - ln K)
+    shift[j] = j < n_eff ? par.cw[p * K + j] + logf((float)K) - (M + logf(S)) : -INFINITY;
   }
   __syncthreads();
-  // pass 2: marginal weights
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    float zr[MAXD];
-#pragma unroll
-    for (int d = 0; d < MAXD; ++d) zr[d] = d < D ? v.z[(e * K + k) * D + d] : 0.f;
-    const float hk = v.htil[e * K + k];
     float acc = 0.f;
 #pragma unroll
-    for (int j = 0; j < kSmallKept; ++j) {
-      if (j < n_eff) {
-        float a = pcs[j] + hk + lse[j];
-#pragma unroll
-        for (int d = 0; d < MAXD; ++d) {
-          const float t = zr[d] - pms[j * MAXD + d];
-          a = fmaf(pps[j * MAXD + d], t * t, a);
-        }
-        acc += expf(a);
-      }
-    }
+    for (int j = 0; j < kSmallKept; ++j)
+      if (j < n_eff) acc += expf(av[j * K + k] + shift[j]);
     v.w[e * K + k] = acc;
   }
 }
@@ -786,19 +791,36 @@ __global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, i
 cudaError_t launch_adj_small(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
   if (v.n == 0) return cudaSuccess;
   const unsigned grid = (unsigned)v.n;
-  if (v.D <= 4) k_adj_small<4><<<grid, 256, 0, s>>>(v, par, K);
-  else if (v.D <= 8) k_adj_small<8><<<grid, 256, 0, s>>>(v, par, K);
-  else if (v.D <= 20) k_adj_small<20><<<grid, 256, 0, s>>>(v, par, K);
-  else if (v.D <= 32) k_adj_small<32><<<grid, 256, 0, s>>>(v, par, K);
-  else k_adj_small<64><<<grid, 256, 0, s>>>(v, par, K);
+  const size_t sm = sizeof(float) * (256 * (size_t)(v.D + 1) + (size_t)kSmallKept * K);
+  if (v.D <= 4) k_adj_small<4><<<grid, 256, sm, s>>>(v, par, K);
+  else if (v.D <= 8) k_adj_small<8><<<grid, 256, sm, s>>>(v, par, K);
+  else if (v.D <= 20) k_adj_small<20><<<grid, 256, sm, s>>>(v, par, K);
+  else if (v.D <= 32) k_adj_small<32><<<grid, 256, sm, s>>>(v, par, K);
+  else k_adj_small<64><<<grid, 256, sm, s>>>(v, par, K);
   return cudaGetLastError();
+}
+
+template <int MAXD>
+static cudaError_t adj_small_cfg(size_t sm) {
+  return cudaFuncSetAttribute(k_adj_small<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+cudaError_t configure_adj_small(int D, int K) {
+  const size_t sm = sizeof(float) * (256 * (size_t)(D + 1) + (size_t)kSmallKept * K);
+  if (sm <= 48 * 1024) return cudaSuccess;
+  if (D <= 4) return adj_small_cfg<4>(sm);
+  if (D <= 8) return adj_small_cfg<8>(sm);
+  if (D <= 20) return adj_small_cfg<20>(sm);
+  if (D <= 32) return adj_small_cfg<32>(sm);
+  return adj_small_cfg<64>(sm);
 }
 
 template <int MAXD>
 static cudaError_t adj_compact_dispatch(const LevelView& v, const LevelView& par, int K, int max_eff, cudaStream_t s) {
   const int thr = K >= kRowTile ? kRowTile : ((K + 31) / 32) * 32;
   const int n_rt = (K + thr - 1) / thr;
-  k_adj_compact<MAXD><<<(unsigned)(v.n * n_rt), thr, 0, s>>>(v, par, K, n_rt, max_eff);
+  k_adj_compact<MAXD><<<(unsigned)(v.n * n_rt), thr, sizeof(float) * thr * (size_t)(v.D + 1), s>>>(v, par, K, n_rt,
+                                                                                                  max_eff);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <new>
 
 #include "qem_tc.cuh"
@@ -45,7 +46,12 @@ namespace tc {
 
 constexpr int kRows = 128;        // MMA M: rows of one work unit
 constexpr int kMaxN = 256;        // MMA N of one column chunk
-constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2..9 epilogue
+constexpr int kEpiWarps = 16;    // 4 per TMEM lane quarter, each owning a quarter of a chunk's columns
+constexpr int kBStagesC = 3;     // column-operand ring depth (one producer warp per stage)
+constexpr int kProdWarps = 1 + kBStagesC;        // warp 0: row operand, warps 1..3: one column stage each
+constexpr int kMmaWarp = kProdWarps;             // warp 4: MMA issuer, TMEM owner
+constexpr int kEpiWarp0 = kProdWarps + 1;        // warps 5..20: epilogue
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
 constexpr int kMaxFK = 128;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -86,11 +92,35 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long lon
     }
   }
 }
+// Non-suspending variant for the single MMA-issuing thread: polls with
+// test_wait so it reacts to a completed phase at once.
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_spin(uint64_t* b, uint32_t parity, long long limit, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  for (int i = 0;; ++i) {
+    if (mbar_test(b, parity)) return true;
+    if ((i & 63) == 63) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > limit) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
 __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
@@ -162,6 +192,41 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
       : "memory");
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Split TMEM load: issue (outputs valid only after tmem_wait on the same
+// registers; the in-out operands of the wait order every use after it).
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) : : "memory");
 }
 
 __device__ __forceinline__ float ex2f(float x) {
@@ -259,52 +324,151 @@ __global__ void k_parent_features(LevelView par, int Dc, int mean_logvar, int K,
 
 // Child side: B row of sample k of element e: split 3: [Bh | h1 h2 h3 | Bl | Bh | 0..],
 // split 1: [Bh | h1 h2 h3 | 0..], with h = log2e (htil + [fixed-variance] pp sum z'^2).
-__global__ void k_child_features(LevelView ch, int mean_logvar, float pp_fixed, int K, int fk, int nb, int split,
-                                 const float* center, __nv_bfloat16* bfeat) {
+// Samples are staged through shared memory (coalesced loads); each thread
+// builds the B features of one sample into its own shared row, then writes
+// the row as 16-byte granules of the canonical layout.
+__global__ void __launch_bounds__(128) k_child_features(LevelView ch, int mean_logvar, float pp_fixed, int K, int fk,
+                                                        int nb, int split, const float* center,
+                                                        __nv_bfloat16* bfeat) {
+  extern __shared__ float csm[];
   const long long e = blockIdx.x;
-  const int D = ch.D;
+  const int D = ch.D, zst = D + 1, bst = nb + 1;
   const long long p = ch.parent[e];
-  __shared__ float cen[kMaxDim];
+  float* cen = csm;                      // [D]
+  float* zc = cen + D;                   // [128][D+1]
+  float* bf = zc + 128 * zst;            // [128][nb+1] B feature values
+  float* hs = bf + 128 * bst;            // [128] h (log2 units)
   for (int d = threadIdx.x; d < D; d += blockDim.x) cen[d] = center[p * D + d];
-  __syncthreads();
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const float* z = ch.z + (e * K + k) * D;
-    float zp[kMaxDim];
-    float ss = 0.f;
-    for (int d = 0; d < D; ++d) {
-      zp[d] = z[d] - cen[d];
-      ss = fmaf(zp[d], zp[d], ss);
-    }
-    float h = ch.htil[e * K + k];
-    if (!mean_logvar) h = fmaf(pp_fixed, ss, h);
-    __nv_bfloat16 h1, h2, h3;
-    split3(h * kLog2e, h1, h2, h3);
-    __nv_bfloat16* row = bfeat + e * (long long)K * fk;
-    for (int c0 = 0; c0 < fk; c0 += 8) {
-      __align__(16) __nv_bfloat16 g[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int c = c0 + j;
-        int f = -1, part = 0;
-        if (c < nb) { f = c; part = 0; }
-        else if (c == nb) { g[j] = h1; continue; }
-        else if (c == nb + 1) { g[j] = h2; continue; }
-        else if (c == nb + 2) { g[j] = h3; continue; }
-        else if (split == 3 && c < 2 * nb + 3) { f = c - nb - 3; part = 1; }
-        else if (split == 3 && c < 3 * nb + 3) { f = c - 2 * nb - 3; part = 0; }
-        if (f >= 0) {
-          float b;
-          if (mean_logvar) b = f < D ? zp[f] * zp[f] : zp[f - D];
-          else b = zp[f];
-          __nv_bfloat16 hi, lo;
-          split2(b, hi, lo);
-          g[j] = part == 0 ? hi : lo;
+  __nv_bfloat16* out = bfeat + e * (long long)K * fk;
+  for (int k0 = 0; k0 < K; k0 += blockDim.x) {
+    const int nk = min((int)blockDim.x, K - k0);
+    __syncthreads();
+    const float* src = ch.z + (e * K + k0) * (long long)D;
+    for (int i = threadIdx.x; i < nk * D; i += blockDim.x) zc[(i / D) * zst + (i % D)] = src[i];
+    __syncthreads();
+    if ((int)threadIdx.x < nk) {
+      const int r = threadIdx.x;
+      float ss = 0.f;
+      for (int d = 0; d < D; ++d) {
+        const float zp = zc[r * zst + d] - cen[d];
+        ss = fmaf(zp, zp, ss);
+        if (mean_logvar) {
+          bf[r * bst + d] = zp * zp;
+          bf[r * bst + D + d] = zp;
         } else {
-          g[j] = __float2bfloat16_rn(0.f);
+          bf[r * bst + d] = zp;
         }
       }
-      *reinterpret_cast<uint4*>(row + canon(k, c0, fk)) = *reinterpret_cast<const uint4*>(g);
+      float h = ch.htil[e * K + k0 + r];
+      if (!mean_logvar) h = fmaf(pp_fixed, ss, h);
+      hs[r] = h * kLog2e;
     }
+    __syncthreads();
+    // one 16-byte granule (8 features of one sample) per thread and step;
+    // consecutive threads take consecutive samples of the same granule column
+    const int gran = fk >> 3;
+    for (int i = threadIdx.x; i < nk * gran; i += blockDim.x) {
+      const int r = i % nk, g = i / nk;
+      __align__(16) __nv_bfloat16 q[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = g * 8 + j;
+        if (c < nb) {
+          q[j] = __float2bfloat16_rn(bf[r * bst + c]);
+        } else if (c < nb + 3) {
+          __nv_bfloat16 h1, h2, h3;
+          split3(hs[r], h1, h2, h3);
+          q[j] = c == nb ? h1 : (c == nb + 1 ? h2 : h3);
+        } else if (split == 3 && c < 2 * nb + 3) {
+          const float x = bf[r * bst + c - nb - 3];
+          q[j] = __float2bfloat16_rn(x - __bfloat162float(__float2bfloat16_rn(x)));
+        } else if (split == 3 && c < 3 * nb + 3) {
+          q[j] = __float2bfloat16_rn(bf[r * bst + c - 2 * nb - 3]);
+        } else {
+          q[j] = __float2bfloat16_rn(0.f);
+        }
+      }
+      *reinterpret_cast<uint4*>(out + canon(k0 + r, g * 8, fk)) = *reinterpret_cast<const uint4*>(q);
+    }
+  }
+}
+
+// Compile-time specialisation of the child features for the common widths:
+// the sample's features live in registers and every column of the row is
+// resolved at compile time (no per-value branches); rows are written as
+// 16-byte granules of the canonical layout.
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+template <int NB, int SPLIT, bool MLV>
+__global__ void __launch_bounds__(128) k_child_features_t(LevelView ch, float pp_fixed, int K, const float* center,
+                                                          __nv_bfloat16* bfeat) {
+  constexpr int D = MLV ? NB / 2 : NB;
+  constexpr int W = SPLIT == 3 ? 3 * NB + 3 : NB + 3;
+  constexpr int FK = (W + 15) & ~15;
+  constexpr int ZS = D + 1;
+  __shared__ float cen[D];
+  __shared__ float zc[128 * ZS];
+  const long long e = blockIdx.x;
+  const long long p = ch.parent[e];
+  for (int d = threadIdx.x; d < D; d += blockDim.x) cen[d] = center[p * D + d];
+  __nv_bfloat16* out = bfeat + e * (long long)K * FK;
+  for (int k0 = 0; k0 < K; k0 += 128) {
+    const int nk = min(128, K - k0);
+    __syncthreads();
+    const float* src = ch.z + (e * K + k0) * (long long)D;
+    for (int i = threadIdx.x; i < nk * D; i += blockDim.x) zc[(i / D) * ZS + (i % D)] = src[i];
+    __syncthreads();
+    if ((int)threadIdx.x >= nk) continue;
+    const int r = threadIdx.x;
+    float b[NB];
+    float ss = 0.f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const float zp = zc[r * ZS + d] - cen[d];
+      ss = fmaf(zp, zp, ss);
+      if (MLV) {
+        b[d] = zp * zp;
+        b[D + d] = zp;
+      } else {
+        b[d] = zp;
+      }
+    }
+    float h = ch.htil[e * K + k0 + r];
+    if (!MLV) h = fmaf(pp_fixed, ss, h);
+    __nv_bfloat16 h1, h2, h3;
+    split3(h * kLog2e, h1, h2, h3);
+    __nv_bfloat16 bh[NB], bl[NB];
+#pragma unroll
+    for (int f = 0; f < NB; ++f) {
+      bh[f] = __float2bfloat16_rn(b[f]);
+      bl[f] = __float2bfloat16_rn(b[f] - __bfloat162float(bh[f]));
+    }
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    uint32_t wv[FK / 2];
+#pragma unroll
+    for (int c = 0; c < FK; c += 2) {
+      __nv_bfloat16 v[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int cc = c + t;
+        __nv_bfloat16 x = zero;
+        if (cc < NB) x = bh[cc];
+        else if (cc == NB) x = h1;
+        else if (cc == NB + 1) x = h2;
+        else if (cc == NB + 2) x = h3;
+        else if (SPLIT == 3 && cc < 2 * NB + 3) x = bl[cc - NB - 3];
+        else if (SPLIT == 3 && cc < 3 * NB + 3) x = bh[cc - 2 * NB - 3];
+        v[t] = x;
+      }
+      wv[c / 2] = pack_bf16x2(v[0], v[1]);
+    }
+    const long long k = k0 + r;
+#pragma unroll
+    for (int g = 0; g < FK / 8; ++g)
+      *reinterpret_cast<uint4*>(out + canon(k, g * 8, FK)) =
+          make_uint4(wv[4 * g], wv[4 * g + 1], wv[4 * g + 2], wv[4 * g + 3]);
   }
 }
 
@@ -345,10 +509,67 @@ __global__ void k_dcol(LevelView ch, LevelView par, int K, int small, const floa
   }
 }
 
+
+// Online log-sum-exp of one row over the group of 32 values at TMEM address
+// taddr (log2 units): shift by the running maximum m (set from the first
+// group), all 32 subtractions, then all 32 exponentials, then a pairwise sum,
+// in place; a partial sum above 2^32 (a group far above the shift) is redone
+// from TMEM at the group's exact maximum, so the running sum never overflows.
+// Called by all 32 lanes of a warp together (it issues warp-collective loads).
+__device__ __forceinline__ void lse_group32(uint32_t taddr, float& m, float& sacc) {
+  float v[32];
+  tmem_ld32(taddr, v);
+  if (m == -INFINITY) {
+    float mx = v[0];
+#pragma unroll
+    for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
+    m = mx;
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] -= m;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = ex2f(v[j]);
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1)
+#pragma unroll
+    for (int j = 0; j < w; ++j) v[j] += v[j + w];
+  float pt = v[0];
+  const bool redo = !(pt <= 4294967296.0f);
+  // tcgen05.ld is warp-collective: the reload runs on the whole warp whenever
+  // any lane needs it, and only those lanes use it.
+  if (__any_sync(0xffffffffu, redo)) {
+    tmem_ld32(taddr, v);
+    if (redo) {
+      float mx = v[0];
+#pragma unroll
+      for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
+      if (mx > m) {
+        sacc *= ex2f(m - mx);
+        m = mx;
+      }
+      pt = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) pt += ex2f(v[j] - m);
+    }
+  }
+  sacc += pt;
+}
+
 // ---------------------------------------------------------------------------- the contraction kernel
+// One work unit = 128 rows of one plate element.  Columns stream in chunks
+// of up to 256 (the MMA reaches its full rate only at N = 256: an M = 128,
+// K = 16 instruction takes ~128 cycles at N = 128 and at N = 256) through a
+// 3-deep ring of bulk copies, one issuing warp per stage; the MMA accumulates
+// each chunk in FP32 in TMEM (2 slots of 256 columns, so the MMA of chunk
+// g+1 overlaps the epilogue of chunk g); 16 epilogue warps turn TMEM into
+// row sums.  The A tile is reloaded only when the unit's row block changes
+// (double-buffered when shared memory allows, otherwise single).
+constexpr int kNB = 256;          // columns per chunk
+constexpr int kBStages = kBStagesC;
+
 struct ContractArgs {
-  int K, fk, ksteps, rtiles;
-  long long n_units;
+  int K, fk, ksteps, rt_per_unit, units_per_elt, a_slots;
+  long long n_units, n_elts;
   const long long* parent;
   const __nv_bfloat16* rows_feat;   // A operand source (forward: parent features, adjoint: child features)
   const __nv_bfloat16* cols_feat;   // B operand source (forward: child features, adjoint: compacted parents)
@@ -363,9 +584,9 @@ struct ContractArgs {
 };
 
 struct Smem {
-  uint8_t* a0;       // two A tiles, a_stride apart
-  uint8_t* b0;       // two B chunks, b_stride apart
-  float* d0;         // two column-shift rows (adjoint), kMaxN floats apart
+  uint8_t* a0;       // two A blocks (RT row tiles each), a_stride apart
+  uint8_t* b0;       // kBStages B chunks, b_stride apart
+  float* d0;         // kBStages column-shift rows (adjoint), kNB floats apart
   uint32_t a_stride, b_stride;
   uint64_t* a_full;
   uint64_t* a_empty;
@@ -373,34 +594,40 @@ struct Smem {
   uint64_t* b_empty;
   uint64_t* t_full;
   uint64_t* t_empty;
-  uint64_t* d_full;   // adjoint column shifts landed in slot
-  uint64_t* d_empty;  // adjoint column shifts of slot consumed by the epilogue
+  uint64_t* d_full;   // adjoint column shifts landed in stage
+  uint64_t* d_empty;  // adjoint column shifts of stage consumed by the epilogue
   uint64_t* done;
   uint32_t* tmem_base;
   volatile int* abort_flag;
   volatile int* stop_flag;
-  float2* merge;
+  float2* merge;      // [kRows][4] partial (max, sum) of every row
 };
 
-__host__ __device__ inline size_t contract_smem_bytes(int fk, bool adj) {
-  const size_t a = (size_t)kRows * fk * 2, b = (size_t)kMaxN * fk * 2;
-  size_t tot = 1024 + 2 * a + 2 * b;
-  if (adj) tot += 2 * (size_t)kMaxN * sizeof(float);
-  tot += 24 * 8 + 16 + kRows * sizeof(float2);
+__host__ __device__ inline size_t contract_smem_bytes(int fk, bool adj, int a_slots) {
+  const size_t a = (size_t)kRows * fk * 2, b = (size_t)kNB * fk * 2;
+  size_t tot = 1024 + a_slots * a + kBStages * b;
+  if (adj) tot += kBStages * (size_t)kNB * sizeof(float);
+  tot += 32 * 8 + 16 + kRows * 4 * sizeof(float2);
   return tot;
 }
+constexpr size_t kSmemLimit = 227 * 1024;
+__host__ inline int contract_a_slots(int fk, bool adj) {
+  return contract_smem_bytes(fk, adj, 2) <= kSmemLimit ? 2 : 1;
+}
 
-__device__ __forceinline__ Smem carve(uint8_t* raw, int fk, bool adj) {
+__device__ __forceinline__ Smem carve(uint8_t* raw, int fk, bool adj, int a_slots) {
   Smem s;
   uint8_t* p = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
-  const size_t a = (size_t)kRows * fk * 2, b = (size_t)kMaxN * fk * 2;
+  const size_t a = (size_t)kRows * fk * 2, b = (size_t)kNB * fk * 2;
   s.a_stride = (uint32_t)a;
   s.b_stride = (uint32_t)b;
-  s.a0 = p; p += 2 * a;
-  s.b0 = p; p += 2 * b;
+  s.a0 = p;
+  p += a_slots * a;
+  s.b0 = p;
+  p += kBStages * b;
   if (adj) {
     s.d0 = reinterpret_cast<float*>(p);
-    p += 2 * kMaxN * sizeof(float);
+    p += kBStages * kNB * sizeof(float);
   } else {
     s.d0 = nullptr;
   }
@@ -408,13 +635,13 @@ __device__ __forceinline__ Smem carve(uint8_t* raw, int fk, bool adj) {
   s.a_full = bars + 0;
   s.a_empty = bars + 2;
   s.b_full = bars + 4;
-  s.b_empty = bars + 6;
-  s.t_full = bars + 8;
-  s.t_empty = bars + 10;
-  s.d_full = bars + 12;
-  s.d_empty = bars + 14;
-  s.done = bars + 16;
-  p += 24 * 8;
+  s.b_empty = bars + 8;
+  s.t_full = bars + 12;
+  s.t_empty = bars + 14;
+  s.d_full = bars + 16;
+  s.d_empty = bars + 20;
+  s.done = bars + 24;
+  p += 32 * 8;
   s.tmem_base = reinterpret_cast<uint32_t*>(p);
   s.abort_flag = reinterpret_cast<volatile int*>(p + 4);
   s.stop_flag = reinterpret_cast<volatile int*>(p + 8);
@@ -423,32 +650,96 @@ __device__ __forceinline__ Smem carve(uint8_t* raw, int fk, bool adj) {
   return s;
 }
 
+// The sequence of work units of a CTA, identical in every role.
+// Forward: units u = blockIdx.x + i * gridDim.x, u -> (element u / upe, row
+// block u % upe); the parent of the next unit is loaded one unit ahead.
+// Adjoint: elements e = blockIdx.x + i * gridDim.x whose parent keeps more
+// than `small` weighted samples, each contributing its upe row blocks in
+// order; the next element's parent and count are loaded while the current
+// element is processed.
+struct Unit {
+  long long e, p;
+  int rb;       // row block
+  int ncols;    // columns of the unit
+};
+template <bool ADJ>
+struct Walker {
+  const ContractArgs& a;
+  long long cur;          // forward: next unit; adjoint: current element
+  long long p_next;       // forward: parent of unit `cur`
+  long long ep, pp;       // adjoint: element whose units are being yielded and its parent
+  int cnt, rb;            //          its kept count and next row block (rb == upe: need a new element)
+  long long nxt, p_nx;    //          prefetched element and its parent
+  __device__ explicit Walker(const ContractArgs& args) : a(args) {
+    if (!ADJ) {
+      cur = blockIdx.x;
+      p_next = cur < a.n_units ? a.parent[cur / a.units_per_elt] : 0;
+    } else {
+      rb = a.units_per_elt;
+      ep = pp = -1;
+      cnt = 0;
+      nxt = blockIdx.x;
+      p_nx = nxt < a.n_elts ? a.parent[nxt] : 0;
+    }
+  }
+  __device__ bool next(Unit& x) {
+    if (!ADJ) {
+      if (cur >= a.n_units) return false;
+      x.e = cur / a.units_per_elt;
+      x.rb = (int)(cur % a.units_per_elt);
+      x.p = p_next;
+      x.ncols = a.K;
+      cur += gridDim.x;
+      if (cur < a.n_units) p_next = a.parent[cur / a.units_per_elt];
+      return true;
+    }
+    while (rb >= a.units_per_elt) {  // advance to the next element that has work
+      if (nxt >= a.n_elts) return false;
+      ep = nxt;
+      pp = p_nx;
+      cnt = a.ccnt[pp];
+      nxt += gridDim.x;
+      if (nxt < a.n_elts) p_nx = a.parent[nxt];
+      rb = cnt > a.small ? 0 : a.units_per_elt;
+    }
+    x.e = ep;
+    x.p = pp;
+    x.rb = rb++;
+    x.ncols = min(a.K, max(16, (cnt + 15) & ~15));
+    return true;
+  }
+};
+
 template <bool ADJ>
 __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  Smem s = carve(smem_raw, a.fk, ADJ);
+  Smem s = carve(smem_raw, a.fk, ADJ, a.a_slots);
+  const int NA = a.a_slots;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int fk = a.fk, K = a.K;
+  const int fk = a.fk, K = a.K, RT = a.rt_per_unit;
   const uint32_t sbo = (uint32_t)(fk >> 3) * 128u;
+  const uint32_t tile_bytes = (uint32_t)kRows * fk * 2;
   const long long lim = a.timeout_cycles;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&s.a_full[i], 1);
       mbar_init(&s.a_empty[i], 1);
+      mbar_init(&s.t_full[i], 1);
+      mbar_init(&s.t_empty[i], kEpiWarps);
+    }
+    for (int i = 0; i < kBStages; ++i) {
       mbar_init(&s.b_full[i], 1);
       mbar_init(&s.b_empty[i], 1);
-      mbar_init(&s.t_full[i], 1);
-      mbar_init(&s.t_empty[i], 8);
       mbar_init(&s.d_full[i], 1);
-      mbar_init(&s.d_empty[i], 8);
+      mbar_init(&s.d_empty[i], kEpiWarps);
     }
     mbar_init(s.done, 1);
     *s.abort_flag = 0;
     *s.stop_flag = 0;
     fence_barrier_init();
   }
-  if (warp == 1) {
+  if (warp == kMmaWarp) {
     tmem_alloc(s.tmem_base, 512);
     tmem_relinquish();
   }
@@ -457,107 +748,125 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
   tc_fence_after();
   const uint32_t tmem = *s.tmem_base;
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
-    int as = 0, bs = 0;
+  if (warp < kProdWarps) {
+    // ------------------------------------------------------------ producers
+    // Warp 0 loads the row operand (once per row block); warp 1 + i loads the
+    // column chunks of ring stage i.  Several issuing warps keep several bulk
+    // copies in flight per SM (one thread waiting on every stage in turn
+    // serialises them).
+    const bool is_a = warp == 0;
+    const int my_stage = warp - 1;
+    int as = 0;
     uint32_t aph = 0, bph = 0;
-    uint32_t armed = 0, last = 0;  // bit i: a slot i, bit 2+i: b slot i, bit 4+i: d slot i
-    for (long long u = blockIdx.x; u < a.n_units; u += gridDim.x) {
-      const long long e = u / a.rtiles;
-      const int rt = (int)(u % a.rtiles);
-      const long long p = a.parent[e];
-      if (ADJ && a.ccnt[p] <= a.small) continue;
-      const long long row_elt = ADJ ? e : p;
-      bool ok = true;
-      if (lane == 0) {
-        ok = mbar_wait(&s.a_empty[as], aph ^ 1, lim, s.abort_flag);
+    long long g = 0;                // chunk counter of this CTA (all roles count the same chunks)
+    uint32_t armed = 0, last = 0;  // bit i: a slot i, bit 2: my b stage, bit 3: my d stage
+    long long prev_row = -1;
+    bool ok = true;
+    Walker<ADJ> wk(a);
+    Unit x;
+    while (ok && wk.next(x)) {
+      const long long row_elt = ADJ ? x.e : x.p;
+      const long long row_key = row_elt * a.units_per_elt + x.rb;
+      if (row_key != prev_row) {
+        if (is_a && lane == 0) {  // new row block: load it into the next A slot
+          ok = mbar_wait(&s.a_empty[as], aph ^ 1, lim, s.abort_flag);
+          if (ok) {
+            const uint32_t bytes = (uint32_t)RT * tile_bytes;
+            mbar_expect_tx(&s.a_full[as], bytes);
+            bulk_g2s(s.a0 + as * s.a_stride, a.rows_feat + (row_elt * K + (long long)x.rb * RT * kRows) * fk, bytes,
+                     &s.a_full[as]);
+            armed |= 1u << as;
+            last = (last & ~(1u << as)) | (aph << as);
+          }
+        }
+        if (++as == NA) {
+          as = 0;
+          aph ^= 1;
+        }
+        prev_row = row_key;
+      }
+      const long long col_elt = ADJ ? x.p : x.e;
+      for (int c0 = 0; c0 < x.ncols && ok; c0 += kNB, ++g) {
+        const int bs = (int)(g % kBStages);
+        if (bs == 0 && g > 0) bph ^= 1;
+        if (is_a || bs != my_stage || lane != 0) continue;
+        const int nc = min(kNB, x.ncols - c0);
+        ok = mbar_wait(&s.b_empty[bs], bph ^ 1, lim, s.abort_flag);
         if (ok) {
-          const uint32_t bytes = (uint32_t)kRows * fk * 2;
-          mbar_expect_tx(&s.a_full[as], bytes);
-          bulk_g2s((s.a0 + as * s.a_stride), a.rows_feat + (row_elt * K + (long long)rt * kRows) * fk, bytes, &s.a_full[as]);
-          armed |= 1u << as;
-          last = (last & ~(1u << as)) | (aph << as);
+          const uint32_t bytes = (uint32_t)nc * fk * 2;
+          mbar_expect_tx(&s.b_full[bs], bytes);
+          bulk_g2s(s.b0 + bs * s.b_stride, a.cols_feat + (col_elt * K + c0) * fk, bytes, &s.b_full[bs]);
+          armed |= 4u;
+          last = (last & ~4u) | (bph << 2);
+        }
+        // the column shifts live until the epilogue has used them (own barriers)
+        if (ADJ && ok) ok = mbar_wait(&s.d_empty[bs], bph ^ 1, lim, s.abort_flag);
+        if (ADJ && ok) {
+          mbar_expect_tx(&s.d_full[bs], (uint32_t)nc * 4u);
+          bulk_g2s(s.d0 + bs * kNB, a.dcol + x.e * K + c0, (uint32_t)nc * 4u, &s.d_full[bs]);
+          armed |= 8u;
+          last = (last & ~8u) | (bph << 3);
         }
       }
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (!ok) break;
-      as ^= 1;
-      if (as == 0) aph ^= 1;
-      const int ncols = ADJ ? max(16, (a.ccnt[p] + 15) & ~15) : K;
-      const long long col_elt = ADJ ? p : e;
-      for (int c0 = 0; c0 < ncols && ok; c0 += kMaxN) {
-        const int nc = min(kMaxN, ncols - c0);
-        if (lane == 0) {
-          ok = mbar_wait(&s.b_empty[bs], bph ^ 1, lim, s.abort_flag);
-          if (ok) {
-            const uint32_t bytes = (uint32_t)nc * fk * 2;
-            mbar_expect_tx(&s.b_full[bs], bytes);
-            bulk_g2s((s.b0 + bs * s.b_stride), a.cols_feat + (col_elt * K + c0) * fk, bytes, &s.b_full[bs]);
-            // the column shifts live until the epilogue has used them (own barriers)
-            if (ADJ) ok = mbar_wait(&s.d_empty[bs], bph ^ 1, lim, s.abort_flag);
-            if (ADJ && ok) {
-              mbar_expect_tx(&s.d_full[bs], (uint32_t)nc * 4u);
-              bulk_g2s(s.d0 + bs * kMaxN, a.dcol + e * K + c0, (uint32_t)nc * 4u, &s.d_full[bs]);
-              armed |= 16u << bs;
-              last = (last & ~(16u << bs)) | (bph << (4 + bs));
-            }
-            armed |= 4u << bs;
-            last = (last & ~(4u << bs)) | (bph << (2 + bs));
-          }
-        }
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-        if (!ok) break;
-        bs ^= 1;
-        if (bs == 0) bph ^= 1;
-      }
-      if (!ok) break;
     }
     // no bulk copy of this CTA may still be landing when it exits: wait for
-    // the last phase armed on every full barrier (bounded, ignores abort)
+    // the last phase armed on every full barrier this warp armed (bounded,
+    // ignores abort)
     if (lane == 0) {
       volatile int never = 0;
-      for (int i = 0; i < 2; ++i) {
-        if (armed & (1u << i)) mbar_wait(&s.a_full[i], (last >> i) & 1u, lim, &never);
-        if (armed & (4u << i)) mbar_wait(&s.b_full[i], (last >> (2 + i)) & 1u, lim, &never);
-        if (armed & (16u << i)) mbar_wait(&s.d_full[i], (last >> (4 + i)) & 1u, lim, &never);
+      if (is_a) {
+        for (int i = 0; i < NA; ++i)
+          if (armed & (1u << i)) mbar_wait(&s.a_full[i], (last >> i) & 1u, lim, &never);
+      } else {
+        if (armed & 4u) mbar_wait(&s.b_full[my_stage], (last >> 2) & 1u, lim, &never);
+        if (armed & 8u) mbar_wait(&s.d_full[my_stage], (last >> 3) & 1u, lim, &never);
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer (one thread)
     if (lane == 0) {
-      int as = 0, bs = 0, ts = 0;
-      uint32_t aph = 0, bph = 0, tph = 0;
+      int as = NA - 1, bs = 0, ts = 0;   // as: slot of the current row block (advanced on each new block)
+      uint32_t aph = 1, bph = 0, tph = 0;
+      long long prev_row = -1;
       bool ok = true;
-      for (long long u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
-        const long long e = u / a.rtiles;
-        const long long p = a.parent[e];
-        if (ADJ && a.ccnt[p] <= a.small) continue;
-        ok = mbar_wait(&s.a_full[as], aph, lim, s.abort_flag);
-        if (!ok) break;
-        const int ncols = ADJ ? max(16, (a.ccnt[p] + 15) & ~15) : K;
-        for (int c0 = 0; c0 < ncols; c0 += kMaxN) {
-          const int nc = min(kMaxN, ncols - c0);
-          ok = mbar_wait(&s.b_full[bs], bph, lim, s.abort_flag) && mbar_wait(&s.t_empty[ts], tph ^ 1, lim, s.abort_flag);
+      Walker<ADJ> wk(a);
+      Unit x;
+      while (ok && wk.next(x)) {
+        const long long row_key = (ADJ ? x.e : x.p) * a.units_per_elt + x.rb;
+        if (row_key != prev_row) {
+          if (prev_row >= 0) mma_commit(&s.a_empty[as]);  // the previous block's last MMA has been issued
+          if (++as == NA) {
+            as = 0;
+            aph ^= 1;
+          }
+          ok = mbar_spin(&s.a_full[as], aph, lim, s.abort_flag);
+          if (!ok) break;
+          prev_row = row_key;
+        }
+        for (int c0 = 0; c0 < x.ncols; c0 += kNB) {
+          const int nc = min(kNB, x.ncols - c0);
+          ok = mbar_spin(&s.b_full[bs], bph, lim, s.abort_flag) && mbar_spin(&s.t_empty[ts], tph ^ 1, lim, s.abort_flag);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t d_tmem = tmem + (uint32_t)ts * kMaxN;
           const uint32_t idesc = idesc_bf16(nc);
-          for (int ks = 0; ks < a.ksteps; ++ks) {
-            const uint64_t ad = smem_desc((s.a0 + as * s.a_stride) + ks * 256, 128, sbo);
-            const uint64_t bd = smem_desc((s.b0 + bs * s.b_stride) + ks * 256, 128, sbo);
-            mma_bf16(d_tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+          for (int r = 0; r < RT; ++r) {
+            const uint32_t d_tmem = tmem + (uint32_t)(ts * 256 + r * kNB);
+            const uint8_t* ab = s.a0 + as * s.a_stride + r * tile_bytes;
+            const uint8_t* bb = s.b0 + bs * s.b_stride;
+            for (int ks = 0; ks < a.ksteps; ++ks)
+              mma_bf16(d_tmem, smem_desc(ab + ks * 256, 128, sbo), smem_desc(bb + ks * 256, 128, sbo), idesc,
+                       ks > 0 ? 1u : 0u);
           }
           mma_commit(&s.b_empty[bs]);
           mma_commit(&s.t_full[ts]);
-          bs ^= 1;
-          if (bs == 0) bph ^= 1;
+          if (++bs == kBStages) {
+            bs = 0;
+            bph ^= 1;
+          }
           ts ^= 1;
           if (ts == 0) tph ^= 1;
         }
-        if (!ok) break;
-        mma_commit(&s.a_empty[as]);
-        as ^= 1;
-        if (as == 0) aph ^= 1;
       }
       // every issued MMA has completed before the teardown
       mma_commit(s.done);
@@ -565,39 +874,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------------------ epilogue (8 warps)
-    // Every epilogue warp executes both named barriers of every unit it
-    // enters, and the decision to stop is read from a flag written between
-    // them, so the 8 warps always agree (no unmatched bar.sync on abort).
-    const int ew = warp - 2;
-    const int half = ew >> 2;
+    // ------------------------------------------------------------ epilogue (16 warps)
+    // Warp w reads TMEM lanes 32 (w % 4) .. +31 (the restriction of
+    // tcgen05.ld).  With RT = 2 the four warps of a lane quarter take (row
+    // tile, column half); with RT = 1 they take column quarters.  Four warps
+    // share each SM sub-partition, so one warp's TMEM-load latency is hidden
+    // by the others' exponentials.  Every epilogue warp executes both named
+    // barriers of every unit it enters, and the decision to stop is read from
+    // a flag written between them, so the warps always agree.
+    const int part = (warp - kEpiWarp0) >> 2;
     const int quarter = warp & 3;
+    const int r = RT == 2 ? (part >> 1) : 0;
+    const int ncp = RT == 2 ? 2 : 4;             // column parts per row tile
+    const int cpart = RT == 2 ? (part & 1) : part;
     const int row = quarter * 32 + lane;
-    int ts = 0;
-    uint32_t tph = 0;
-    for (long long u = blockIdx.x; u < a.n_units; u += gridDim.x) {
-      const long long e = u / a.rtiles;
-      const int rt = (int)(u % a.rtiles);
-      const long long p = a.parent[e];
-      if (ADJ && a.ccnt[p] <= a.small) continue;
-      const int ncols = ADJ ? max(16, (a.ccnt[p] + 15) & ~15) : K;
+    int ts = 0, ds = 0;
+    uint32_t tph = 0, dph = 0;
+    Walker<ADJ> wk(a);
+    Unit x;
+    while (wk.next(x)) {
       float m = -INFINITY, sacc = 0.f;
       bool ok = true;
-      for (int c0 = 0; c0 < ncols && ok; c0 += kMaxN) {
-        const int nc = min(kMaxN, ncols - c0);
+      for (int c0 = 0; c0 < x.ncols && ok; c0 += kNB) {
+        const int nc = min(kNB, x.ncols - c0);
         ok = mbar_wait(&s.t_full[ts], tph, lim, s.abort_flag);
-        if (ok && ADJ) ok = mbar_wait(&s.d_full[ts], tph, lim, s.abort_flag);
+        if (ok && ADJ) ok = mbar_wait(&s.d_full[ds], dph, lim, s.abort_flag);
+        ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
         if (!ok) break;
         tc_fence_after();
-        const int hw = nc >> 1;
-        const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ts * kMaxN + half * hw);
-        const float* dsm = ADJ ? s.d0 + ts * kMaxN : nullptr;  // chunk g uses B, TMEM and d slot g % 2
+        const int qw = nc / ncp;  // columns of this warp (multiple of 4)
+        const int col0 = cpart * qw;
+        const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ts * 256 + r * kNB + col0);
+        const float* dsm = ADJ ? s.d0 + ds * kNB + col0 : nullptr;
         int c = 0;
-        for (; c + 32 <= hw; c += 32) {
-          float v[32];
-          tmem_ld32(tbase + c, v);
-          if (ADJ) {
-            const float4* d4 = reinterpret_cast<const float4*>(dsm + half * hw + c);
+        if (!ADJ) {
+          for (; c < qw; c += 32) lse_group32(tbase + c, m, sacc);
+        } else {
+          for (; c + 32 <= qw; c += 32) {
+            float v[32];
+            tmem_ld32(tbase + c, v);
+            const float4* d4 = reinterpret_cast<const float4*>(dsm + c);
             float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
@@ -608,74 +924,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
               p3 += ex2f(v[j + 3] + dv.w);
             }
             sacc += (p0 + p1) + (p2 + p3);
-          } else {
-            if (m == -INFINITY) {
-              float mx = v[0];
-#pragma unroll
-              for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
-              m = mx;
-            }
-            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              p0 += ex2f(v[j] - m);
-              p1 += ex2f(v[j + 1] - m);
-              p2 += ex2f(v[j + 2] - m);
-              p3 += ex2f(v[j + 3] - m);
-            }
-            float part = (p0 + p1) + (p2 + p3);
-            // The shift is the first group's maximum; a later group far above it
-            // gives a large (or infinite) partial sum.  Rescale to that group's
-            // exact maximum whenever the partial sum exceeds 2^32, so the running
-            // sum stays below 2^32 per group and never overflows.
-            if (!(part <= 4294967296.0f)) {
-              float mx = v[0];
-#pragma unroll
-              for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
-              if (mx > m) {
-                sacc *= ex2f(m - mx);
-                m = mx;
-              }
-              part = 0.f;
-#pragma unroll
-              for (int j = 0; j < 32; ++j) part += ex2f(v[j] - m);
-            }
-            sacc += part;
           }
-        }
-        for (; c < hw; c += 8) {  // adjoint tails (chunks narrower than 64 columns)
-          float v[8];
-          tmem_ld8(tbase + c, v);
-          if (ADJ) {
+          for (; c < qw; c += 4) {
+            float v[4];
+            tmem_ld4(tbase + c, v);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) sacc += ex2f(v[j] + dsm[half * hw + c + j]);
+            for (int j = 0; j < 4; ++j) sacc += ex2f(v[j] + dsm[c + j]);
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&s.t_empty[ts]);
-          if (ADJ) mbar_arrive(&s.d_empty[ts]);
+          if (ADJ) mbar_arrive(&s.d_empty[ds]);
         }
         ts ^= 1;
         if (ts == 0) tph ^= 1;
-      }
-      // combine the two column halves of each row
-      if (half == 1) s.merge[row] = make_float2(m, sacc);
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (threadIdx.x == 64) *s.stop_flag = *s.abort_flag;
-      if (half == 0 && ok) {
-        const float2 o = s.merge[row];
-        const long long k = (long long)rt * kRows + row;
-        if (ADJ) {
-          a.w_out[e * K + k] = sacc + o.y;
-        } else {
-          const float M = fmaxf(m, o.x);
-          const float S = (m == -INFINITY ? 0.f : sacc * ex2f(m - M)) + (o.x == -INFINITY ? 0.f : o.y * ex2f(o.x - M));
-          a.lt[e * K + k] = a.rowc[p * K + k] + (M + log2f(S)) * kLn2 - logf((float)K);
+        if (++ds == kBStages) {
+          ds = 0;
+          dph ^= 1;
         }
       }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
+      // combine the column parts of each row
+      const int mrow = r * kRows + row;
+      s.merge[mrow * 4 + cpart] = make_float2(m, sacc);
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+      if (threadIdx.x == 32 * kEpiWarp0) *s.stop_flag = *s.abort_flag;
+      if (cpart == 0 && ok) {
+        const long long k = (long long)x.rb * RT * kRows + mrow;
+        if (ADJ) {
+          float S = 0.f;
+          for (int i = 0; i < ncp; ++i) S += s.merge[mrow * 4 + i].y;
+          a.w_out[x.e * K + k] = S;
+        } else {
+          float M = -INFINITY;
+          for (int i = 0; i < ncp; ++i) M = fmaxf(M, s.merge[mrow * 4 + i].x);
+          float S = 0.f;
+          for (int i = 0; i < ncp; ++i) {
+            const float2 o = s.merge[mrow * 4 + i];
+            if (o.x != -INFINITY) S += o.y * ex2f(o.x - M);
+          }
+          a.lt[x.e * K + k] = a.rowc[x.p * K + k] + (M + log2f(S)) * kLn2 - logf((float)K);
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
       if (*s.stop_flag) break;
     }
   }
@@ -683,7 +975,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
   if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
@@ -730,7 +1022,7 @@ __global__ void __launch_bounds__(128, 1) k_diag_gemm(const __nv_bfloat16* A, co
     mma_commit(&bars[1]);
   }
   __syncwarp();
-  const bool ok = mbar_wait(&bars[1], 0, lim, abort_flag);
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[1], 0, lim, abort_flag));  // warp-collective loads follow
   tc_fence_after();
   if (ok) {
     const int row = warp * 32 + lane;
@@ -802,10 +1094,16 @@ qem_status tc_plan_init(qem_plan_t P, const qem_model_desc*) {
   if (P->precision == QEM_PREC_FP32) return QEM_OK;
   int fkmax = 16;
   for (int l = 1; l < P->L; ++l) fkmax = fkmax > P->tc->fk[l] ? fkmax : P->tc->fk[l];
-  if (cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)contract_smem_bytes(fkmax, false)) != cudaSuccess ||
-      cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)contract_smem_bytes(fkmax, true)) != cudaSuccess)
+  size_t sf = 0, sa = 0;
+  for (int l = 1; l < P->L; ++l) {
+    const int fk = P->tc->fk[l];
+    sf = std::max(sf, contract_smem_bytes(fk, false, contract_a_slots(fk, false)));
+    sa = std::max(sa, contract_smem_bytes(fk, true, contract_a_slots(fk, true)));
+  }
+  (void)fkmax;
+  if (sf > kSmemLimit || sa > kSmemLimit) return QEM_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf) != cudaSuccess ||
+      cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess)
     return QEM_ERR_CUDA;
   return QEM_OK;
 }
@@ -826,9 +1124,18 @@ cudaError_t tc_features(qem_plan_t P, int l) {
   if (pa.n > 0)
     k_parent_features<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, ch.D, mlv, K, fk, nb, T.split, T.afeat[l],
                                                               T.rowc[l], T.center[l]);
-  if (ch.n > 0)
-    k_child_features<<<(unsigned)ch.n, 256, 0, P->stream>>>(ch, mlv, -0.5f / ch.prior_a, K, fk, nb, T.split,
-                                                            T.center[l], T.bfeat[l]);
+  if (ch.n > 0) {
+    const unsigned g = (unsigned)ch.n;
+    const float ppf = -0.5f / ch.prior_a;
+    if (mlv && nb == 36 && T.split == 3) k_child_features_t<36, 3, true><<<g, 128, 0, P->stream>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
+    else if (mlv && nb == 36 && T.split == 1) k_child_features_t<36, 1, true><<<g, 128, 0, P->stream>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
+    else if (!mlv && nb == 8 && T.split == 3) k_child_features_t<8, 3, false><<<g, 128, 0, P->stream>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
+    else if (!mlv && nb == 8 && T.split == 1) k_child_features_t<8, 1, false><<<g, 128, 0, P->stream>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
+    else {
+      const size_t sm = sizeof(float) * (size_t)(ch.D + 128 * (ch.D + 1) + 128 * (nb + 1) + 128);
+      k_child_features<<<g, 128, sm, P->stream>>>(ch, mlv, ppf, K, fk, nb, T.split, T.center[l], T.bfeat[l]);
+    }
+  }
   return cudaGetLastError();
 }
 
@@ -840,8 +1147,11 @@ static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
   a.K = P->K;
   a.fk = T.fk[l];
   a.ksteps = T.fk[l] / 16;
-  a.rtiles = P->K / kRows;
-  a.n_units = ch.n * a.rtiles;
+  a.rt_per_unit = 1;
+  a.units_per_elt = P->K / kRows;
+  a.a_slots = contract_a_slots(a.fk, adj);
+  a.n_units = ch.n * a.units_per_elt;
+  a.n_elts = ch.n;
   a.parent = ch.parent;
   a.ctl = P->ctl;
   a.timeout_cycles = timeout_cycles(P);
@@ -854,12 +1164,13 @@ static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
     a.rows_feat = T.bfeat[l];
     a.cols_feat = T.cfeat[l];
     a.ccnt = P->lv[l - 1].ccnt;
-    a.small = kTcAdjointMinKept;
+    a.small = kSmallKept;
     a.dcol = T.dcol[l];
     a.w_out = ch.w;
   }
-  const long long grid = a.n_units < P->num_sms ? a.n_units : P->num_sms;
-  const size_t smem = contract_smem_bytes(a.fk, adj);
+  const long long work = adj ? a.n_elts : a.n_units;
+  const long long grid = work < P->num_sms ? work : P->num_sms;
+  const size_t smem = contract_smem_bytes(a.fk, adj, a.a_slots);
   if (adj)
     k_contract<true><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
   else
@@ -874,8 +1185,8 @@ cudaError_t tc_adjoint_prep(qem_plan_t P, int l) {
   const LevelView& pa = P->lv[l - 1];
   const LevelView& ch = P->lv[l];
   if (pa.n > 0)
-    k_gather<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, P->K, T.fk[l], kTcAdjointMinKept, T.afeat[l], T.cfeat[l]);
-  if (ch.n > 0) k_dcol<<<(unsigned)ch.n, 256, 0, P->stream>>>(ch, pa, P->K, kTcAdjointMinKept, T.rowc[l], T.dcol[l]);
+    k_gather<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, P->K, T.fk[l], kSmallKept, T.afeat[l], T.cfeat[l]);
+  if (ch.n > 0) k_dcol<<<(unsigned)ch.n, 256, 0, P->stream>>>(ch, pa, P->K, kSmallKept, T.rowc[l], T.dcol[l]);
   return cudaGetLastError();
 }
 

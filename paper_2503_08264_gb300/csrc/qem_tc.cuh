@@ -18,9 +18,8 @@ cudaError_t tc_features(qem_plan_t P, int l);
 // Forward contraction of level l into lv[l].lt.
 cudaError_t tc_forward(qem_plan_t P, int l);
 // Adjoint of level l into lv[l].w for the elements whose parent keeps more
-// than kTcAdjointMinKept weighted samples (the rest run on the CUDA cores):
+// than kSmallKept weighted samples (the rest run on the CUDA cores):
 // operand gathering and column shifts, then the contraction.
-constexpr int kTcAdjointMinKept = 16;
 cudaError_t tc_adjoint_prep(qem_plan_t P, int l);
 cudaError_t tc_adjoint(qem_plan_t P, int l);
 
