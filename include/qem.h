@@ -236,6 +236,27 @@ const char* qem_profile_name(int kind);
  * `stream`; allocates and frees a small control block.                      */
 qem_status qem_diag_tc_gemm(const void* A, const void* B, int fk, int n, float* out, void* stream);
 
+/* Allocation-free E-step for single-level models (every instance has one
+ * latent, no plate below it: the global importance weighting of App. A.1 as
+ * the n = 1 case of MPIW).  The paper has no counterpart of this entry point;
+ * it exists for callers that cannot allocate device memory when they run an
+ * E-step (inside a CUDA-graph capture they do not own, under a memory pool
+ * that forbids outside allocations, or in a latency-bound loop), and it
+ * allocates nothing, on the device or the host.
+ *   level      HOST descriptor of the single level (parent must be NULL; x, y DEVICE)
+ *   q_params   DEVICE float [n][2][D]; eps DEVICE float [n][K][nps] or NULL
+ *   moments    DEVICE double [n][2][D] out; log_pmp DEVICE double [n] out (nullable)
+ *   stream     cudaStream_t (NULL: legacy default stream), asynchronous
+ * Scratch lives in one library-wide device array of 32 MiB, held by every GPU
+ * that loads the library until the process exits: requests needing more
+ * (about n*K*(D+2)*4 bytes) return QEM_ERR_UNSUPPORTED.  Calls whose GPU work
+ * overlaps race on that array.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Results equal qem_estep's on the same
+ * single-level model and inputs.                                            */
+qem_status qem_estep_single_noalloc(const qem_level_desc* level, int K, const float* q_params, const float* eps,
+                                    uint64_t seed, uint64_t iter, double* moments, double* log_pmp, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,6 +59,8 @@ SIGNATURES = {
     "qem_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "qem_profile_name": (C.c_char_p, [C.c_int]),
     "qem_diag_tc_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "qem_estep_single_noalloc": (C.c_int, [C.POINTER(LevelDesc), C.c_int, C.c_void_p, C.c_void_p, C.c_uint64,
+                                           C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 QEM_K_NAMES = ["sample_local", "parent_params", "finalize", "forward", "plate_sum", "root", "adjoint", "moments",
