@@ -30,12 +30,33 @@
 
 namespace qem {
 
+// Column layout of the operand rows of one level (bf16 columns, canonical
+// K-major core-matrix layout).  Parent rows (A of the forward):
+//   [Ah | 1 1 1 | .. | Ah at a_ah2 | .. | Al at a_al | 0..]   (split 3)
+// child rows (B of the forward):
+//   [Bh | h1 h2 h3 | .. | Bl at b_bl | (Bh at b_bh2) | 0..]
+// and a table of MMA k-steps pairing parent columns ka[i]..+16 with child
+// columns kb[i]..+16.  When it saves child bytes, the lo*hi product re-reads
+// the first Bh block instead of storing Bh twice (b_bh2 = -1), with the
+// ragged tail of that product packed into the padding (tail, a_alt, b_bht).
+struct Layout {
+  int nb = 0, split = 1;
+  int fka = 0, fkb = 0;
+  int a_ah2 = -1, a_al = -1, b_bl = -1, b_bh2 = -1;
+  // compact form: the last `tail` features of the lo*hi product sit in the
+  // padding after the Ah/Bl block (parent Al at a_alt, child Bh copy at
+  // b_bht); the Al block at a_al then holds only the first nb - tail.
+  int tail = 0, a_alt = -1, b_bht = -1;
+  int nks = 0;
+  int ka[16] = {}, kb[16] = {};
+};
+
 struct TcBuffers {
-  int fk[QEM_MAX_LEVELS] = {};   // feature row width (bf16 elements) of child level l
+  Layout lay[QEM_MAX_LEVELS];
   int nb[QEM_MAX_LEVELS] = {};   // bilinear features of child level l
   int split = 3;
-  __nv_bfloat16* bfeat[QEM_MAX_LEVELS] = {};   // child level l:   [n_l][K rows][fk] canonical
-  __nv_bfloat16* afeat[QEM_MAX_LEVELS] = {};   // parent of l:     [n_{l-1}][K rows][fk]
+  __nv_bfloat16* bfeat[QEM_MAX_LEVELS] = {};   // child level l:   [n_l][K rows][fkb] canonical
+  __nv_bfloat16* afeat[QEM_MAX_LEVELS] = {};   // parent of l:     [n_{l-1}][K rows][fka]
   __nv_bfloat16* cfeat[QEM_MAX_LEVELS] = {};   // compacted parent rows, same layout
   float* rowc[QEM_MAX_LEVELS] = {};            // [n_{l-1}][K] row constants (nats)
   float* center[QEM_MAX_LEVELS] = {};          // [n_{l-1}][D_l]
@@ -266,17 +287,30 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
 //   rowc = pc + sum_d pp_d pm'_d^2.
 // Row of fk columns: split 3: [Ah | 1 1 1 | Ah | Al | 0..], split 1: [Ah | 1 1 1 | 0..].
 __global__ void k_parent_features(LevelView par, int Dc, int mean_logvar, int K, int fk, int nb, int split,
-                                  __nv_bfloat16* afeat, float* rowc, float* center) {
+                                  int a_ah2, int a_al, int a_alt, int tail, __nv_bfloat16* afeat, float* rowc,
+                                  float* center) {
   const long long p = blockIdx.x;
   __shared__ float cen[kMaxDim];
-  for (int d = threadIdx.x; d < Dc; d += blockDim.x) {
-    double s = 0.0;
-    for (int kp = 0; kp < K; ++kp) s += par.pm[(p * K + kp) * Dc + d];
-    cen[d] = (float)(s / K);
-    center[p * Dc + d] = cen[d];
+  __shared__ float red[8][kMaxDim];
+  // centre: mean over the parent samples of the children's prior mean
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = 0; d < Dc; ++d) {
+      float acc = 0.f;
+      for (int kp = threadIdx.x; kp < K; kp += blockDim.x) acc += par.pm[(p * K + kp) * Dc + d];
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) red[warp][d] = acc;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < Dc; d += blockDim.x) {
+      float t = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][d];
+      cen[d] = t / K;
+      center[p * Dc + d] = cen[d];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int kp = threadIdx.x; kp < K; kp += blockDim.x) {
+  for (int kp = blockIdx.y * blockDim.x + threadIdx.x; kp < K; kp += gridDim.y * blockDim.x) {
     const float* pm = par.pm + (p * K + kp) * Dc;
     const float* pp = par.pp + (p * K + kp) * Dc;
     double rc = par.pc[p * K + kp];
@@ -284,31 +318,22 @@ __global__ void k_parent_features(LevelView par, int Dc, int mean_logvar, int K,
       const float dm = pm[d] - cen[d];
       rc += (double)pp[d] * dm * dm;
     }
-    rowc[p * K + kp] = (float)rc;
+    if (blockIdx.z == 0) rowc[p * K + kp] = (float)rc;
     __nv_bfloat16* row = afeat + p * (long long)K * fk;
     for (int c0 = 0; c0 < fk; c0 += 8) {
       __align__(16) __nv_bfloat16 g[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int c = c0 + j;
-        float v = 0.f;
-        int f = -1, part = 0;  // part: 0 = hi, 1 = lo, 2 = one
-        if (c < nb) { f = c; part = 0; }
-        else if (c < nb + 3) { part = 2; }
-        else if (split == 3 && c < 2 * nb + 3) { f = c - nb - 3; part = 0; }
-        else if (split == 3 && c < 3 * nb + 3) { f = c - 2 * nb - 3; part = 1; }
-        if (part == 2) {
-          v = 1.f;
-          g[j] = __float2bfloat16_rn(v);
-          continue;
-        }
+        int f = -1, part = 0;  // part: 0 = hi, 1 = lo
+        if (c < nb) f = c;
+        else if (c < nb + 3) { g[j] = __float2bfloat16_rn(1.f); continue; }
+        else if (split == 3 && c >= a_ah2 && c < a_ah2 + nb) f = c - a_ah2;
+        else if (split == 3 && tail > 0 && c >= a_alt && c < a_alt + tail) { f = nb - tail + (c - a_alt); part = 1; }
+        else if (split == 3 && c >= a_al && c < a_al + nb - tail) { f = c - a_al; part = 1; }
         if (f >= 0) {
-          float a;
-          if (mean_logvar) {
-            a = f < Dc ? pp[f] : -2.f * pp[f - Dc] * (pm[f - Dc] - cen[f - Dc]);
-          } else {
-            a = -2.f * pp[f] * (pm[f] - cen[f]);
-          }
+          float a = mean_logvar ? (f < Dc ? pp[f] : -2.f * pp[f - Dc] * (pm[f - Dc] - cen[f - Dc]))
+                                : -2.f * pp[f] * (pm[f] - cen[f]);
           a *= kLog2e;
           __nv_bfloat16 hi, lo;
           split2(a, hi, lo);
@@ -328,8 +353,8 @@ __global__ void k_parent_features(LevelView par, int Dc, int mean_logvar, int K,
 // builds the B features of one sample into its own shared row, then writes
 // the row as 16-byte granules of the canonical layout.
 __global__ void __launch_bounds__(128) k_child_features(LevelView ch, int mean_logvar, float pp_fixed, int K, int fk,
-                                                        int nb, int split, const float* center,
-                                                        __nv_bfloat16* bfeat) {
+                                                        int nb, int split, int b_bl, int b_bh2, int b_bht, int tail,
+                                                        const float* center, __nv_bfloat16* bfeat) {
   extern __shared__ float csm[];
   const long long e = blockIdx.x;
   const int D = ch.D, zst = D + 1, bst = nb + 1;
@@ -379,11 +404,13 @@ __global__ void __launch_bounds__(128) k_child_features(LevelView ch, int mean_l
           __nv_bfloat16 h1, h2, h3;
           split3(hs[r], h1, h2, h3);
           q[j] = c == nb ? h1 : (c == nb + 1 ? h2 : h3);
-        } else if (split == 3 && c < 2 * nb + 3) {
-          const float x = bf[r * bst + c - nb - 3];
+        } else if (split == 3 && c >= b_bl && c < b_bl + nb) {
+          const float x = bf[r * bst + c - b_bl];
           q[j] = __float2bfloat16_rn(x - __bfloat162float(__float2bfloat16_rn(x)));
-        } else if (split == 3 && c < 3 * nb + 3) {
-          q[j] = __float2bfloat16_rn(bf[r * bst + c - 2 * nb - 3]);
+        } else if (split == 3 && b_bh2 >= 0 && c >= b_bh2 && c < b_bh2 + nb) {
+          q[j] = __float2bfloat16_rn(bf[r * bst + c - b_bh2]);
+        } else if (split == 3 && tail > 0 && c >= b_bht && c < b_bht + tail) {
+          q[j] = __float2bfloat16_rn(bf[r * bst + nb - tail + (c - b_bht)]);
         } else {
           q[j] = __float2bfloat16_rn(0.f);
         }
@@ -401,12 +428,10 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-template <int NB, int SPLIT, bool MLV>
+template <int NB, int SPLIT, bool MLV, int BBL, int BBH2, int FK, int BBT = -1, int TAIL = 0>
 __global__ void __launch_bounds__(128) k_child_features_t(LevelView ch, float pp_fixed, int K, const float* center,
                                                           __nv_bfloat16* bfeat) {
   constexpr int D = MLV ? NB / 2 : NB;
-  constexpr int W = SPLIT == 3 ? 3 * NB + 3 : NB + 3;
-  constexpr int FK = (W + 15) & ~15;
   constexpr int ZS = D + 1;
   __shared__ float cen[D];
   __shared__ float zc[128 * ZS];
@@ -458,8 +483,9 @@ __global__ void __launch_bounds__(128) k_child_features_t(LevelView ch, float pp
         else if (cc == NB) x = h1;
         else if (cc == NB + 1) x = h2;
         else if (cc == NB + 2) x = h3;
-        else if (SPLIT == 3 && cc < 2 * NB + 3) x = bl[cc - NB - 3];
-        else if (SPLIT == 3 && cc < 3 * NB + 3) x = bh[cc - 2 * NB - 3];
+        else if (SPLIT == 3 && cc >= BBL && cc < BBL + NB) x = bl[cc - BBL];
+        else if (SPLIT == 3 && BBH2 >= 0 && cc >= BBH2 && cc < BBH2 + NB) x = bh[cc - BBH2];
+        else if (SPLIT == 3 && TAIL > 0 && cc >= BBT && cc < BBT + TAIL) x = bh[NB - TAIL + (cc - BBT)];
         v[t] = x;
       }
       wv[c / 2] = pack_bf16x2(v[0], v[1]);
@@ -568,7 +594,8 @@ constexpr int kNB = 256;          // columns per chunk
 constexpr int kBStages = kBStagesC;
 
 struct ContractArgs {
-  int K, fk, ksteps, rt_per_unit, units_per_elt, a_slots;
+  int K, frow, fcol, ksteps, rt_per_unit, units_per_elt, a_slots;
+  int koff_row[16], koff_col[16];   // per k-step: column offset in the row / column operand
   long long n_units, n_elts;
   const long long* parent;
   const __nv_bfloat16* rows_feat;   // A operand source (forward: parent features, adjoint: child features)
@@ -603,22 +630,22 @@ struct Smem {
   float2* merge;      // [kRows][4] partial (max, sum) of every row
 };
 
-__host__ __device__ inline size_t contract_smem_bytes(int fk, bool adj, int a_slots) {
-  const size_t a = (size_t)kRows * fk * 2, b = (size_t)kNB * fk * 2;
+__host__ __device__ inline size_t contract_smem_bytes(int frow, int fcol, bool adj, int a_slots) {
+  const size_t a = (size_t)kRows * frow * 2, b = (size_t)kNB * fcol * 2;
   size_t tot = 1024 + a_slots * a + kBStages * b;
   if (adj) tot += kBStages * (size_t)kNB * sizeof(float);
   tot += 32 * 8 + 16 + kRows * 4 * sizeof(float2);
   return tot;
 }
 constexpr size_t kSmemLimit = 227 * 1024;
-__host__ inline int contract_a_slots(int fk, bool adj) {
-  return contract_smem_bytes(fk, adj, 2) <= kSmemLimit ? 2 : 1;
+__host__ inline int contract_a_slots(int frow, int fcol, bool adj) {
+  return contract_smem_bytes(frow, fcol, adj, 2) <= kSmemLimit ? 2 : 1;
 }
 
-__device__ __forceinline__ Smem carve(uint8_t* raw, int fk, bool adj, int a_slots) {
+__device__ __forceinline__ Smem carve(uint8_t* raw, int frow, int fcol, bool adj, int a_slots) {
   Smem s;
   uint8_t* p = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
-  const size_t a = (size_t)kRows * fk * 2, b = (size_t)kNB * fk * 2;
+  const size_t a = (size_t)kRows * frow * 2, b = (size_t)kNB * fcol * 2;
   s.a_stride = (uint32_t)a;
   s.b_stride = (uint32_t)b;
   s.a0 = p;
@@ -713,12 +740,12 @@ struct Walker {
 template <bool ADJ>
 __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  Smem s = carve(smem_raw, a.fk, ADJ, a.a_slots);
+  Smem s = carve(smem_raw, a.frow, a.fcol, ADJ, a.a_slots);
   const int NA = a.a_slots;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int fk = a.fk, K = a.K, RT = a.rt_per_unit;
-  const uint32_t sbo = (uint32_t)(fk >> 3) * 128u;
-  const uint32_t tile_bytes = (uint32_t)kRows * fk * 2;
+  const int K = a.K, RT = a.rt_per_unit, frow = a.frow, fcol = a.fcol;
+  const uint32_t sbo_a = (uint32_t)(frow >> 3) * 128u, sbo_b = (uint32_t)(fcol >> 3) * 128u;
+  const uint32_t tile_bytes = (uint32_t)kRows * frow * 2;
   const long long lim = a.timeout_cycles;
 
   if (threadIdx.x == 0) {
@@ -773,7 +800,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
           if (ok) {
             const uint32_t bytes = (uint32_t)RT * tile_bytes;
             mbar_expect_tx(&s.a_full[as], bytes);
-            bulk_g2s(s.a0 + as * s.a_stride, a.rows_feat + (row_elt * K + (long long)x.rb * RT * kRows) * fk, bytes,
+            bulk_g2s(s.a0 + as * s.a_stride, a.rows_feat + (row_elt * K + (long long)x.rb * RT * kRows) * frow, bytes,
                      &s.a_full[as]);
             armed |= 1u << as;
             last = (last & ~(1u << as)) | (aph << as);
@@ -793,9 +820,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
         const int nc = min(kNB, x.ncols - c0);
         ok = mbar_wait(&s.b_empty[bs], bph ^ 1, lim, s.abort_flag);
         if (ok) {
-          const uint32_t bytes = (uint32_t)nc * fk * 2;
+          const uint32_t bytes = (uint32_t)nc * fcol * 2;
           mbar_expect_tx(&s.b_full[bs], bytes);
-          bulk_g2s(s.b0 + bs * s.b_stride, a.cols_feat + (col_elt * K + c0) * fk, bytes, &s.b_full[bs]);
+          bulk_g2s(s.b0 + bs * s.b_stride, a.cols_feat + (col_elt * K + c0) * fcol, bytes, &s.b_full[bs]);
           armed |= 4u;
           last = (last & ~4u) | (bph << 2);
         }
@@ -855,8 +882,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
             const uint8_t* ab = s.a0 + as * s.a_stride + r * tile_bytes;
             const uint8_t* bb = s.b0 + bs * s.b_stride;
             for (int ks = 0; ks < a.ksteps; ++ks)
-              mma_bf16(d_tmem, smem_desc(ab + ks * 256, 128, sbo), smem_desc(bb + ks * 256, 128, sbo), idesc,
-                       ks > 0 ? 1u : 0u);
+              mma_bf16(d_tmem, smem_desc(ab + a.koff_row[ks] * 16, 128, sbo_a),
+                       smem_desc(bb + a.koff_col[ks] * 16, 128, sbo_b), idesc, ks > 0 ? 1u : 0u);
           }
           mma_commit(&s.b_empty[bs]);
           mma_commit(&s.t_full[ts]);
@@ -1048,9 +1075,51 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // ---------------------------------------------------------------------------- host side
 using namespace tc;
 
-static int feature_width(int nb, int split) {
-  const int w = split == 3 ? 3 * nb + 3 : nb + 3;
-  return (w + 15) & ~15;
+static int up16(int x) { return (x + 15) & ~15; }
+static int up8(int x) { return (x + 7) & ~7; }
+
+// Operand layout of a level with nb bilinear features (see Layout).
+static Layout make_layout(int nb, int split) {
+  Layout L;
+  L.nb = nb;
+  L.split = split;
+  if (split == 1) {
+    L.fka = L.fkb = up16(nb + 3);
+    L.nks = L.fka / 16;
+    for (int i = 0; i < L.nks; ++i) L.ka[i] = L.kb[i] = 16 * i;
+    return L;
+  }
+  const int fk_dup = up16(3 * nb + 3);            // [Bh | h | Bl | Bh]: both rows fk_dup wide
+  const int p1 = up8(nb + 3), p2 = up16(p1 + nb);
+  const int r = nb % 16, slack = p2 - (p1 + nb);
+  const int tail = r <= slack ? r : 0;             // ragged tail of the lo*hi product packed in the padding
+  const int q = up16(nb - tail);
+  if (p2 < fk_dup && (p2 + q) / 16 <= 16) {        // [Bh | h | Bl | Bh tail], the lo*hi product re-reads Bh
+    L.fka = p2 + q;
+    L.fkb = p2;
+    L.a_ah2 = p1;
+    L.a_al = p2;
+    L.b_bl = p1;
+    L.b_bh2 = -1;
+    L.tail = tail;
+    L.a_alt = tail ? p1 + nb : -1;
+    L.b_bht = tail ? p1 + nb : -1;
+    L.nks = 0;
+    for (int c = 0; c < p2; c += 16, ++L.nks) L.ka[L.nks] = L.kb[L.nks] = c;
+    for (int c = 0; c < q; c += 16, ++L.nks) {
+      L.ka[L.nks] = p2 + c;
+      L.kb[L.nks] = c;
+    }
+  } else {
+    L.fka = L.fkb = fk_dup;
+    L.a_ah2 = nb + 3;
+    L.a_al = 2 * nb + 3;
+    L.b_bl = nb + 3;
+    L.b_bh2 = 2 * nb + 3;
+    L.nks = fk_dup / 16;
+    for (int i = 0; i < L.nks; ++i) L.ka[i] = L.kb[i] = 16 * i;
+  }
+  return L;
 }
 
 qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base, size_t* bytes) {
@@ -1071,13 +1140,13 @@ qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base,
     const qem_level_desc& c = desc->levels[l];
     const qem_level_desc& pa = desc->levels[l - 1];
     const int nb = c.prior == QEM_PRIOR_NORMAL_MEAN_LOGVAR ? 2 * c.dim : c.dim;
-    const int fk = feature_width(nb, split);
-    if (fk > kMaxFK) return QEM_ERR_UNSUPPORTED;
+    const Layout L = make_layout(nb, split);
+    if (L.fka > kMaxFK || L.fkb > kMaxFK || L.nks > 16) return QEM_ERR_UNSUPPORTED;
     tb.nb[l] = nb;
-    tb.fk[l] = fk;
-    tb.bfeat[l] = (__nv_bfloat16*)take((size_t)c.n * K * fk * 2);
-    tb.afeat[l] = (__nv_bfloat16*)take((size_t)pa.n * K * fk * 2);
-    tb.cfeat[l] = (__nv_bfloat16*)take((size_t)pa.n * K * fk * 2);
+    tb.lay[l] = L;
+    tb.bfeat[l] = (__nv_bfloat16*)take((size_t)c.n * K * L.fkb * 2);
+    tb.afeat[l] = (__nv_bfloat16*)take((size_t)pa.n * K * L.fka * 2);
+    tb.cfeat[l] = (__nv_bfloat16*)take((size_t)pa.n * K * L.fka * 2);
     tb.rowc[l] = (float*)take((size_t)pa.n * K * 4);
     tb.center[l] = (float*)take((size_t)pa.n * c.dim * 4);
     tb.dcol[l] = (float*)take((size_t)c.n * K * 4);
@@ -1092,15 +1161,12 @@ qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base,
 
 qem_status tc_plan_init(qem_plan_t P, const qem_model_desc*) {
   if (P->precision == QEM_PREC_FP32) return QEM_OK;
-  int fkmax = 16;
-  for (int l = 1; l < P->L; ++l) fkmax = fkmax > P->tc->fk[l] ? fkmax : P->tc->fk[l];
   size_t sf = 0, sa = 0;
   for (int l = 1; l < P->L; ++l) {
-    const int fk = P->tc->fk[l];
-    sf = std::max(sf, contract_smem_bytes(fk, false, contract_a_slots(fk, false)));
-    sa = std::max(sa, contract_smem_bytes(fk, true, contract_a_slots(fk, true)));
+    const Layout& L = P->tc->lay[l];
+    sf = std::max(sf, contract_smem_bytes(L.fka, L.fkb, false, contract_a_slots(L.fka, L.fkb, false)));
+    sa = std::max(sa, contract_smem_bytes(L.fkb, L.fka, true, contract_a_slots(L.fkb, L.fka, true)));
   }
-  (void)fkmax;
   if (sf > kSmemLimit || sa > kSmemLimit) return QEM_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf) != cudaSuccess ||
       cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess)
@@ -1119,21 +1185,31 @@ cudaError_t tc_features(qem_plan_t P, int l) {
   TcBuffers& T = *P->tc;
   const LevelView& ch = P->lv[l];
   const LevelView& pa = P->lv[l - 1];
-  const int K = P->K, fk = T.fk[l], nb = T.nb[l];
+  const Layout& L = T.lay[l];
+  const int K = P->K, nb = T.nb[l];
   const int mlv = ch.prior == QEM_PRIOR_NORMAL_MEAN_LOGVAR ? 1 : 0;
-  if (pa.n > 0)
-    k_parent_features<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, ch.D, mlv, K, fk, nb, T.split, T.afeat[l],
-                                                              T.rowc[l], T.center[l]);
+  if (pa.n > 0) {
+    const dim3 grid((unsigned)pa.n, (unsigned)std::max(1, std::min(16, (int)(2 * P->num_sms / std::max(1LL, pa.n)))));
+    k_parent_features<<<grid, 256, 0, P->stream>>>(pa, ch.D, mlv, K, L.fka, nb, T.split, L.a_ah2, L.a_al, L.a_alt,
+                                                   L.tail, T.afeat[l], T.rowc[l], T.center[l]);
+  }
   if (ch.n > 0) {
     const unsigned g = (unsigned)ch.n;
     const float ppf = -0.5f / ch.prior_a;
-    if (mlv && nb == 36 && T.split == 3) k_child_features_t<36, 3, true><<<g, 128, 0, P->stream>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
-    else if (mlv && nb == 36 && T.split == 1) k_child_features_t<36, 1, true><<<g, 128, 0, P->stream>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
-    else if (!mlv && nb == 8 && T.split == 3) k_child_features_t<8, 3, false><<<g, 128, 0, P->stream>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
-    else if (!mlv && nb == 8 && T.split == 1) k_child_features_t<8, 1, false><<<g, 128, 0, P->stream>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
+    cudaStream_t st = P->stream;
+    // compile-time layouts of the common shapes (checked against the plan's layout)
+    if (mlv && nb == 36 && T.split == 3 && L.b_bl == 40 && L.b_bh2 < 0 && L.fkb == 80 && L.tail == 4 && L.b_bht == 76)
+      k_child_features_t<36, 3, true, 40, -1, 80, 76, 4><<<g, 128, 0, st>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
+    else if (mlv && nb == 36 && T.split == 1 && L.fkb == 48)
+      k_child_features_t<36, 1, true, -1, -1, 48><<<g, 128, 0, st>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
+    else if (!mlv && nb == 8 && T.split == 3 && L.b_bl == 11 && L.b_bh2 == 19 && L.fkb == 32)
+      k_child_features_t<8, 3, false, 11, 19, 32><<<g, 128, 0, st>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
+    else if (!mlv && nb == 8 && T.split == 1 && L.fkb == 16)
+      k_child_features_t<8, 1, false, -1, -1, 16><<<g, 128, 0, st>>>(ch, ppf, K, T.center[l], T.bfeat[l]);
     else {
       const size_t sm = sizeof(float) * (size_t)(ch.D + 128 * (ch.D + 1) + 128 * (nb + 1) + 128);
-      k_child_features<<<g, 128, sm, P->stream>>>(ch, mlv, ppf, K, fk, nb, T.split, T.center[l], T.bfeat[l]);
+      k_child_features<<<g, 128, sm, st>>>(ch, mlv, ppf, K, L.fkb, nb, T.split, L.b_bl, L.b_bh2, L.b_bht, L.tail,
+                                           T.center[l], T.bfeat[l]);
     }
   }
   return cudaGetLastError();
@@ -1142,14 +1218,20 @@ cudaError_t tc_features(qem_plan_t P, int l) {
 static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
   TcBuffers& T = *P->tc;
   const LevelView& ch = P->lv[l];
+  const Layout& L = T.lay[l];
   if (ch.n == 0) return cudaSuccess;
   ContractArgs a{};
   a.K = P->K;
-  a.fk = T.fk[l];
-  a.ksteps = T.fk[l] / 16;
+  a.ksteps = L.nks;
+  a.frow = adj ? L.fkb : L.fka;
+  a.fcol = adj ? L.fka : L.fkb;
+  for (int i = 0; i < L.nks; ++i) {
+    a.koff_row[i] = adj ? L.kb[i] : L.ka[i];
+    a.koff_col[i] = adj ? L.ka[i] : L.kb[i];
+  }
   a.rt_per_unit = 1;
   a.units_per_elt = P->K / kRows;
-  a.a_slots = contract_a_slots(a.fk, adj);
+  a.a_slots = contract_a_slots(a.frow, a.fcol, adj);
   a.n_units = ch.n * a.units_per_elt;
   a.n_elts = ch.n;
   a.parent = ch.parent;
@@ -1170,7 +1252,7 @@ static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
   }
   const long long work = adj ? a.n_elts : a.n_units;
   const long long grid = work < P->num_sms ? work : P->num_sms;
-  const size_t smem = contract_smem_bytes(a.fk, adj, a.a_slots);
+  const size_t smem = contract_smem_bytes(a.frow, a.fcol, adj, a.a_slots);
   if (adj)
     k_contract<true><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
   else
@@ -1185,7 +1267,7 @@ cudaError_t tc_adjoint_prep(qem_plan_t P, int l) {
   const LevelView& pa = P->lv[l - 1];
   const LevelView& ch = P->lv[l];
   if (pa.n > 0)
-    k_gather<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, P->K, T.fk[l], kSmallKept, T.afeat[l], T.cfeat[l]);
+    k_gather<<<(unsigned)pa.n, 256, 0, P->stream>>>(pa, P->K, T.lay[l].fka, kSmallKept, T.afeat[l], T.cfeat[l]);
   if (ch.n > 0) k_dcol<<<(unsigned)ch.n, 256, 0, P->stream>>>(ch, pa, P->K, kSmallKept, T.rowc[l], T.dcol[l]);
   return cudaGetLastError();
 }
