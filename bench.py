@@ -97,7 +97,7 @@ def aggregate(local_ms: float, local_units: float, ws: int, device=None):
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -114,7 +114,7 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -203,15 +203,17 @@ def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7):
             return S.Model([full.levels[0], users]), f"{count} of {total} plate elements"
         return S.batched_three_level(n_inst=count, seed=seed), f"{count} of {total} instances"
 
-    calib = 4 if two_level else 1
-    model, _ = sub(calib)
-    t0 = time.perf_counter()
-    O.estep(model, S.initial_q(model), K, seed=1, it=1)
-    t = max(time.perf_counter() - t0, 1e-3)
-    model, desc = sub(calib * target_s / t)
-    t0 = time.perf_counter()
-    O.estep(model, S.initial_q(model), K, seed=1, it=1)
-    t = time.perf_counter() - t0
+    # grow the sample until one run takes at least 60% of the target (the
+    # per-element cost only shows once the fixed per-call cost is amortised)
+    count = 4 if two_level else 1
+    for _ in range(5):
+        model, desc = sub(count)
+        t0 = time.perf_counter()
+        O.estep(model, S.initial_q(model), K, seed=1, it=1)
+        t = time.perf_counter() - t0
+        if t >= 0.6 * target_s or count >= total:
+            break
+        count = min(total, count * min(50.0, target_s / max(t, 1e-3)))
     pairs = model.pairs(K)
     return {"value": pairs / t, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
             "sample": f"one FP64 E-step on {desc} of {workload} (counter-based noise), {t:.1f} s"}, model

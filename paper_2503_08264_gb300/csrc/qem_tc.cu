@@ -68,10 +68,10 @@ namespace tc {
 constexpr int kRows = 128;        // MMA M: rows of one work unit
 constexpr int kMaxN = 256;        // MMA N of one column chunk
 constexpr int kEpiWarps = 16;    // 4 per TMEM lane quarter, each owning a quarter of a chunk's columns
-constexpr int kBStagesC = 3;     // column-operand ring depth (one producer warp per stage)
-constexpr int kProdWarps = 1 + kBStagesC;        // warp 0: row operand, warps 1..3: one column stage each
-constexpr int kMmaWarp = kProdWarps;             // warp 4: MMA issuer, TMEM owner
-constexpr int kEpiWarp0 = kProdWarps + 1;        // warps 5..20: epilogue
+constexpr int kBStagesMax = 4;   // column-operand ring depth limit (one producer warp per stage)
+constexpr int kProdWarps = 1 + kBStagesMax;      // warp 0: row operand, warps 1..4: one column stage each
+constexpr int kMmaWarp = kProdWarps;             // warp 5: MMA issuer, TMEM owner
+constexpr int kEpiWarp0 = kProdWarps + 1;        // warps 6..21: epilogue
 constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
 constexpr int kMaxFK = 128;
 constexpr float kLog2e = 1.4426950408889634f;
@@ -585,16 +585,15 @@ __device__ __forceinline__ void lse_group32(uint32_t taddr, float& m, float& sac
 // One work unit = 128 rows of one plate element.  Columns stream in chunks
 // of up to 256 (the MMA reaches its full rate only at N = 256: an M = 128,
 // K = 16 instruction takes ~128 cycles at N = 128 and at N = 256) through a
-// 3-deep ring of bulk copies, one issuing warp per stage; the MMA accumulates
+// ring of up to 4 bulk copies, one issuing warp per stage; the MMA accumulates
 // each chunk in FP32 in TMEM (2 slots of 256 columns, so the MMA of chunk
 // g+1 overlaps the epilogue of chunk g); 16 epilogue warps turn TMEM into
 // row sums.  The A tile is reloaded only when the unit's row block changes
 // (double-buffered when shared memory allows, otherwise single).
 constexpr int kNB = 256;          // columns per chunk
-constexpr int kBStages = kBStagesC;
 
 struct ContractArgs {
-  int K, frow, fcol, ksteps, rt_per_unit, units_per_elt, a_slots;
+  int K, frow, fcol, ksteps, rt_per_unit, units_per_elt, a_slots, nst;  // nst: column ring depth
   int koff_row[16], koff_col[16];   // per k-step: column offset in the row / column operand
   long long n_units, n_elts;
   const long long* parent;
@@ -612,8 +611,8 @@ struct ContractArgs {
 
 struct Smem {
   uint8_t* a0;       // two A blocks (RT row tiles each), a_stride apart
-  uint8_t* b0;       // kBStages B chunks, b_stride apart
-  float* d0;         // kBStages column-shift rows (adjoint), kNB floats apart
+  uint8_t* b0;       // nst B chunks, b_stride apart
+  float* d0;         // nst column-shift rows (adjoint), kNB floats apart
   uint32_t a_stride, b_stride;
   uint64_t* a_full;
   uint64_t* a_empty;
@@ -630,19 +629,31 @@ struct Smem {
   float2* merge;      // [kRows][4] partial (max, sum) of every row
 };
 
-__host__ __device__ inline size_t contract_smem_bytes(int frow, int fcol, bool adj, int a_slots) {
+__host__ __device__ inline size_t contract_smem_bytes(int frow, int fcol, bool adj, int a_slots, int nst) {
   const size_t a = (size_t)kRows * frow * 2, b = (size_t)kNB * fcol * 2;
-  size_t tot = 1024 + a_slots * a + kBStages * b;
-  if (adj) tot += kBStages * (size_t)kNB * sizeof(float);
+  size_t tot = 1024 + a_slots * a + nst * b;
+  if (adj) tot += nst * (size_t)kNB * sizeof(float);
   tot += 32 * 8 + 16 + kRows * 4 * sizeof(float2);
   return tot;
 }
 constexpr size_t kSmemLimit = 227 * 1024;
-__host__ inline int contract_a_slots(int frow, int fcol, bool adj) {
-  return contract_smem_bytes(frow, fcol, adj, 2) <= kSmemLimit ? 2 : 1;
+// Shared-memory budget: a double-buffered row operand first (a new row block
+// per unit when parents change from unit to unit), then the deepest column
+// ring that fits (a chunk's MMAs are known complete only well after they
+// finish, so the ring needs about three chunks of lead).  False when not even
+// one row slot and two column stages fit.
+__host__ inline bool contract_config(int frow, int fcol, bool adj, int& a_slots, int& nst) {
+  static const int opts[][2] = {{2, 4}, {2, 3}, {1, 4}, {1, 3}, {2, 2}, {1, 2}};
+  for (const auto& o : opts)
+    if (contract_smem_bytes(frow, fcol, adj, o[0], o[1]) <= kSmemLimit) {
+      a_slots = o[0];
+      nst = o[1];
+      return true;
+    }
+  return false;
 }
 
-__device__ __forceinline__ Smem carve(uint8_t* raw, int frow, int fcol, bool adj, int a_slots) {
+__device__ __forceinline__ Smem carve(uint8_t* raw, int frow, int fcol, bool adj, int a_slots, int nst) {
   Smem s;
   uint8_t* p = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
   const size_t a = (size_t)kRows * frow * 2, b = (size_t)kNB * fcol * 2;
@@ -651,10 +662,10 @@ __device__ __forceinline__ Smem carve(uint8_t* raw, int frow, int fcol, bool adj
   s.a0 = p;
   p += a_slots * a;
   s.b0 = p;
-  p += kBStages * b;
+  p += nst * b;
   if (adj) {
     s.d0 = reinterpret_cast<float*>(p);
-    p += kBStages * kNB * sizeof(float);
+    p += nst * kNB * sizeof(float);
   } else {
     s.d0 = nullptr;
   }
@@ -740,8 +751,8 @@ struct Walker {
 template <bool ADJ>
 __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  Smem s = carve(smem_raw, a.frow, a.fcol, ADJ, a.a_slots);
-  const int NA = a.a_slots;
+  Smem s = carve(smem_raw, a.frow, a.fcol, ADJ, a.a_slots, a.nst);
+  const int NA = a.a_slots, NS = a.nst;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int K = a.K, RT = a.rt_per_unit, frow = a.frow, fcol = a.fcol;
   const uint32_t sbo_a = (uint32_t)(frow >> 3) * 128u, sbo_b = (uint32_t)(fcol >> 3) * 128u;
@@ -755,7 +766,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       mbar_init(&s.t_full[i], 1);
       mbar_init(&s.t_empty[i], kEpiWarps);
     }
-    for (int i = 0; i < kBStages; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(&s.b_full[i], 1);
       mbar_init(&s.b_empty[i], 1);
       mbar_init(&s.d_full[i], 1);
@@ -814,7 +825,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       }
       const long long col_elt = ADJ ? x.p : x.e;
       for (int c0 = 0; c0 < x.ncols && ok; c0 += kNB, ++g) {
-        const int bs = (int)(g % kBStages);
+        const int bs = (int)(g % NS);
         if (bs == 0 && g > 0) bph ^= 1;
         if (is_a || bs != my_stage || lane != 0) continue;
         const int nc = min(kNB, x.ncols - c0);
@@ -855,6 +866,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
     if (lane == 0) {
       int as = NA - 1, bs = 0, ts = 0;   // as: slot of the current row block (advanced on each new block)
       uint32_t aph = 1, bph = 0, tph = 0;
+      // Descriptors are built once: a k-step at column c of a slot adds c to
+      // the start-address field (16-byte units; shared addresses stay below
+      // 2^18, so the 14-bit field never carries), so the issue loop is a few
+      // integer adds per MMA and keeps the tensor pipe fed.
+      uint32_t kro[16], kco[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        kro[i] = (uint32_t)a.koff_row[i];
+        kco[i] = (uint32_t)a.koff_col[i];
+      }
+      const int nks = a.ksteps;
+      const uint64_t adesc0 = smem_desc(s.a0, 128, sbo_a), bdesc0 = smem_desc(s.b0, 128, sbo_b);
+      const uint32_t a_step = s.a_stride >> 4, b_step = s.b_stride >> 4, t_step = tile_bytes >> 4;
       long long prev_row = -1;
       bool ok = true;
       Walker<ADJ> wk(a);
@@ -877,17 +901,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
           if (!ok) break;
           tc_fence_after();
           const uint32_t idesc = idesc_bf16(nc);
+          const uint64_t bd = bdesc0 + (uint64_t)(bs * b_step);
           for (int r = 0; r < RT; ++r) {
             const uint32_t d_tmem = tmem + (uint32_t)(ts * 256 + r * kNB);
-            const uint8_t* ab = s.a0 + as * s.a_stride + r * tile_bytes;
-            const uint8_t* bb = s.b0 + bs * s.b_stride;
-            for (int ks = 0; ks < a.ksteps; ++ks)
-              mma_bf16(d_tmem, smem_desc(ab + a.koff_row[ks] * 16, 128, sbo_a),
-                       smem_desc(bb + a.koff_col[ks] * 16, 128, sbo_b), idesc, ks > 0 ? 1u : 0u);
+            const uint64_t ad = adesc0 + (uint64_t)(as * a_step + r * t_step);
+#pragma unroll
+            for (int ks = 0; ks < 16; ++ks)
+              if (ks < nks) mma_bf16(d_tmem, ad + kro[ks], bd + kco[ks], idesc, ks > 0 ? 1u : 0u);
           }
           mma_commit(&s.b_empty[bs]);
           mma_commit(&s.t_full[ts]);
-          if (++bs == kBStages) {
+          if (++bs == NS) {
             bs = 0;
             bph ^= 1;
           }
@@ -967,7 +991,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
         }
         ts ^= 1;
         if (ts == 0) tph ^= 1;
-        if (++ds == kBStages) {
+        if (++ds == NS) {
           ds = 0;
           dph ^= 1;
         }
@@ -1164,10 +1188,12 @@ qem_status tc_plan_init(qem_plan_t P, const qem_model_desc*) {
   size_t sf = 0, sa = 0;
   for (int l = 1; l < P->L; ++l) {
     const Layout& L = P->tc->lay[l];
-    sf = std::max(sf, contract_smem_bytes(L.fka, L.fkb, false, contract_a_slots(L.fka, L.fkb, false)));
-    sa = std::max(sa, contract_smem_bytes(L.fkb, L.fka, true, contract_a_slots(L.fkb, L.fka, true)));
+    int na, ns;
+    if (!contract_config(L.fka, L.fkb, false, na, ns)) return QEM_ERR_UNSUPPORTED;
+    sf = std::max(sf, contract_smem_bytes(L.fka, L.fkb, false, na, ns));
+    if (!contract_config(L.fkb, L.fka, true, na, ns)) return QEM_ERR_UNSUPPORTED;
+    sa = std::max(sa, contract_smem_bytes(L.fkb, L.fka, true, na, ns));
   }
-  if (sf > kSmemLimit || sa > kSmemLimit) return QEM_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf) != cudaSuccess ||
       cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess)
     return QEM_ERR_CUDA;
@@ -1231,7 +1257,7 @@ static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
   }
   a.rt_per_unit = 1;
   a.units_per_elt = P->K / kRows;
-  a.a_slots = contract_a_slots(a.frow, a.fcol, adj);
+  if (!contract_config(a.frow, a.fcol, adj, a.a_slots, a.nst)) return cudaErrorInvalidValue;
   a.n_units = ch.n * a.units_per_elt;
   a.n_elts = ch.n;
   a.parent = ch.parent;
@@ -1252,7 +1278,7 @@ static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
   }
   const long long work = adj ? a.n_elts : a.n_units;
   const long long grid = work < P->num_sms ? work : P->num_sms;
-  const size_t smem = contract_smem_bytes(a.frow, a.fcol, adj, a.a_slots);
+  const size_t smem = contract_smem_bytes(a.frow, a.fcol, adj, a.a_slots, a.nst);
   if (adj)
     k_contract<true><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
   else
