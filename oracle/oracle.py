@@ -54,6 +54,8 @@ def lib():
         _lib.orc_trigamma.restype = C.c_double
         _lib.orc_trigamma.argtypes = [C.c_double]
         _lib.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_draw_noise_at.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_void_p, C.c_int64, C.c_int,
+                                           C.c_int, C.c_int, C.c_void_p]
         _lib.orc_draw_noise.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_int64, C.c_int, C.c_int,
                                         C.c_int, C.c_void_p]
         for nm in ("orc_mstep_gamma", "orc_mstep_beta"):
@@ -153,6 +155,14 @@ def philox4x32_10(ctr, key):
 def draw_noise(seed: int, it: int, level: int, n: int, K: int, nps: int, qfam: int = Q_GAUSS) -> np.ndarray:
     out = np.zeros((n, K, nps))
     lib().orc_draw_noise(seed, it, level, n, K, nps, qfam, _p(out))
+    return out
+
+
+def draw_noise_at(seed: int, it: int, level: int, idx, K: int, nps: int, qfam: int = Q_GAUSS) -> np.ndarray:
+    """draw_noise for the elements idx of a level (their indices in the full model)."""
+    idx = np.ascontiguousarray(idx, np.int64)
+    out = np.zeros((len(idx), K, nps))
+    lib().orc_draw_noise_at(seed, it, level, _p(idx), len(idx), K, nps, qfam, _p(out))
     return out
 
 

@@ -122,6 +122,17 @@ void orc_draw_noise(uint64_t seed, uint64_t iter, int level, int64_t n, int K, i
         out[(e * K + k) * nps + d] = draw_noise(seed, iter, level, (uint64_t)e * K + k, d, qfam);
 }
 
+/* The same stream for selected elements only: idx[i] is the element's index
+ * within its level (the counter uses it, so a sub-model drawn this way gets
+ * the noise its elements have in the full model). */
+void orc_draw_noise_at(uint64_t seed, uint64_t iter, int level, const int64_t* idx, int64_t n, int K, int nps,
+                       int qfam, double* out) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < K; ++k)
+      for (int d = 0; d < nps; ++d)
+        out[(i * K + k) * nps + d] = draw_noise(seed, iter, level, (uint64_t)idx[i] * K + k, d, qfam);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Special functions, from their series (no vendor code).                    */
 /* digamma: psi(x+1) = psi(x) + 1/x to shift x >= 10, then the asymptotic

@@ -139,9 +139,11 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
                       double* trace) {
   cudaStream_t s = P->stream;
   const int L = P->L, K = P->K;
-  for (int l = 0; l < L; ++l)
+  for (int l = 0; l < L; ++l) {
     QEM_LAUNCH(P, QEM_K_SAMPLE,
                launch_sample_local(P->lv[l], K, q + P->q_off[l], eps ? eps + P->eps_off[l] : nullptr, P->ctl, s));
+    QEM_LAUNCH(P, QEM_K_SAMPLE, launch_elem_const(P->lv[l], q + P->q_off[l], s));
+  }
   for (int l = 0; l + 1 < L; ++l) QEM_LAUNCH(P, QEM_K_PARENT, launch_parent_params(P->lv[l], P->lv[l + 1], K, s));
   for (int l = L - 1; l >= 1; --l) {
     const bool has_children = l + 1 < L;
@@ -280,6 +282,9 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
     }
     P->ctl = cv.take<Ctl>(1);
     P->log_pmp = cv.take<double>((size_t)desc->levels[0].n);
+    bool counts = false;
+    for (int l = 0; l < L; ++l) counts = counts || desc->levels[l].lik == QEM_LIK_POISSON_LOG;
+    P->count_tab = counts ? cv.take<double>((size_t)kCountTable) : nullptr;
     for (int l = 0; l < L; ++l) {
       const qem_level_desc& d = desc->levels[l];
       LevelView& lv = P->lv[l];
@@ -304,6 +309,8 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
       lv.z = cv.take<float>(nK * d.dim);
       lv.loc = cv.take<float>(nK);
       lv.cst = cv.take<double>((size_t)d.n);
+      lv.cshift = cv.take<float>((size_t)d.n);
+      lv.ltab = d.lik == QEM_LIK_POISSON_LOG ? P->count_tab : nullptr;
       lv.htil = has_children ? cv.take<float>(nK) : lv.loc;
       lv.hsum = has_children ? cv.take<double>(nK) : nullptr;
       lv.off = has_children ? cv.take<double>((size_t)d.n) : nullptr;
@@ -354,6 +361,7 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
                              cudaMemcpyHostToDevice, P->stream);
     }
   }
+  if (ce == cudaSuccess && P->count_tab) ce = launch_count_table(P->count_tab, P->stream);
   size_t smem = 0;
   for (int l = 0; l < L; ++l) smem = std::max(smem, sample_local_smem(P->lv[l]));
   if (ce == cudaSuccess) ce = configure_sample_local(smem);

@@ -50,6 +50,8 @@ struct LevelView {
   float* z;           // [n][K][D]
   float* loc;         // [n][K]  sample-dependent part of log lik - log q (+ log prior at level 0)
   double* cst;        // [n]     sample-independent part of the same (normalisers, lgamma(y+1), ...)
+  float* cshift;      // [n]     maximum taken out of loc by the sampler (joins cst)
+  const double* ltab; // [kCountTable] per-count Poisson-log constants (levels with that likelihood)
   float* htil;        // [n][K]  loc + children's sum - off  (relative local factor)
   double* hsum;       // [n][K]  sum over children of their log mean-exp (FP64)
   double* off;        // [n]     constant removed from htil
@@ -93,6 +95,7 @@ struct qem_plan_s {
   long long q_off[QEM_MAX_LEVELS], eps_off[QEM_MAX_LEVELS], w_off[QEM_MAX_LEVELS], z_off[QEM_MAX_LEVELS];
   long long q_len = 0, eps_len = 0, w_len = 0, z_len = 0;
   double* log_pmp = nullptr;   // [n_inst] of the last E-step
+  double* count_tab = nullptr; // [kCountTable] Poisson-log count constants (nullptr: no such level)
   qem::Ctl* ctl = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -188,6 +191,11 @@ __device__ __forceinline__ bool spin_until_ge(const volatile int* flag, int targ
 cudaError_t launch_set_ctl(Ctl* ctl, unsigned long long seed, unsigned long long iter, long long t,
                            long long trace_row, cudaStream_t s);
 cudaError_t launch_advance_ctl(Ctl* ctl, long long n_inst, cudaStream_t s);
+// Counts y < kCountTable of a Poisson-log likelihood take their constant
+// y s0 - e^s0 - lgamma(y + 1) from a table built once per plan.
+constexpr int kCountTable = 4096;
+cudaError_t launch_count_table(double* tab, cudaStream_t s);
+cudaError_t launch_elem_const(const LevelView& v, const float* q, cudaStream_t s);
 cudaError_t launch_sample_local(const LevelView& v, int K, const float* q, const float* eps, const Ctl* ctl,
                                 cudaStream_t s);
 cudaError_t launch_parent_params(const LevelView& parent, const LevelView& child, int K, cudaStream_t s);

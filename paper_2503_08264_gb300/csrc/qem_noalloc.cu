@@ -56,10 +56,13 @@ extern "C" qem_status qem_estep_single_noalloc(const qem_level_desc* level, int 
     return QEM_ERR_INVALID_ARG;
   if (d.n == 0) return QEM_OK;
 
-  // scratch layout: control block, log P_MP, per-instance constants, local
-  // factors, weights, samples
+  // scratch layout: control block, log P_MP, per-instance constants and
+  // shifts, the count table (Poisson-log only), local factors, weights,
+  // samples
   const size_t nK = (size_t)d.n * K;
-  const size_t need = up256(sizeof(Ctl)) + up256(sizeof(double) * (size_t)d.n) * 2 + up256(sizeof(float) * nK) * 2 +
+  const bool counts = d.lik == QEM_LIK_POISSON_LOG;
+  const size_t need = up256(sizeof(Ctl)) + up256(sizeof(double) * (size_t)d.n) * 2 + up256(sizeof(float) * (size_t)d.n) +
+                      (counts ? up256(sizeof(double) * kCountTable) : 0) + up256(sizeof(float) * nK) * 2 +
                       up256(sizeof(float) * nK * d.dim);
   if (need > kNoAllocScratchBytes) return QEM_ERR_UNSUPPORTED;
 
@@ -94,6 +97,9 @@ extern "C" qem_status qem_estep_single_noalloc(const qem_level_desc* level, int 
   v.x = d.x;
   v.y = d.y;
   v.cst = reinterpret_cast<double*>(take(sizeof(double) * (size_t)d.n));
+  v.cshift = reinterpret_cast<float*>(take(sizeof(float) * (size_t)d.n));
+  double* tab = counts ? reinterpret_cast<double*>(take(sizeof(double) * kCountTable)) : nullptr;
+  v.ltab = tab;
   v.loc = reinterpret_cast<float*>(take(sizeof(float) * nK));
   v.htil = v.loc;
   v.w = reinterpret_cast<float*>(take(sizeof(float) * nK));
@@ -103,7 +109,9 @@ extern "C" qem_status qem_estep_single_noalloc(const qem_level_desc* level, int 
   if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) return QEM_ERR_CUDA;
   if (launch_set_ctl(ctl, seed, iter, 1, -1, s) != cudaSuccess) return QEM_ERR_CUDA;
   if (configure_sample_local(sample_local_smem(v)) != cudaSuccess) return QEM_ERR_CUDA;
+  if (tab && launch_count_table(tab, s) != cudaSuccess) return QEM_ERR_CUDA;
   if (launch_sample_local(v, K, q_params, eps, ctl, s) != cudaSuccess) return QEM_ERR_CUDA;
+  if (launch_elem_const(v, q_params, s) != cudaSuccess) return QEM_ERR_CUDA;
   if (launch_root(v, K, false, lp_internal, log_pmp, nullptr, ctl, s) != cudaSuccess) return QEM_ERR_CUDA;
   if (launch_moments(v, K, moments, s) != cudaSuccess) return QEM_ERR_CUDA;
   return QEM_OK;

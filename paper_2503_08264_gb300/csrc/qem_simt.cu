@@ -72,11 +72,83 @@ __device__ double gamma_variate(double a, const NoiseSrc& ns, int base) {
 // (Alg. 1 "z ~ Q_t"; the P(x|z)/Q(z) part of r_k in Eq. rmp):
 //   loc[e][k] = sum_n log p(y_en | z_e^k, x_en) - log q(z_e^k) (+ log p(z) at level 0),
 // split into a sample-dependent FP32 part (loc, centred on its maximum) and a
-// sample-independent FP64 part (cst).  One block per element; covariates in
-// shared memory (rows padded to a multiple of 4 for 16-byte loads); each
-// thread keeps its sample in registers; samples are staged through shared
-// memory for coalesced stores.
+// sample-independent FP64 part (cst, written by k_elem_const).  One block per
+// element; covariates in shared memory (rows padded to a multiple of 4 for
+// 16-byte loads); each thread keeps its sample in registers; samples are
+// staged through shared memory for coalesced stores.  No FP64 arithmetic
+// runs per element here: a block has one element, and single-lane FP64 work
+// (GB300's FP64 rate is a small fraction of FP32) dominated it.
 constexpr int kSampleThreads = 128;
+
+// Poisson-log reference point of a count: s0 = log max(y, 1) and e^s0, both
+// in FP32 and identical wherever they are evaluated (the sampler, the count
+// table and the per-element constants use this one function).
+__device__ __forceinline__ void pois_ref(float y, float& s0, float& ey0) {
+  s0 = logf(fmaxf(y, 1.f));
+  ey0 = expf(s0);
+}
+
+// y s0 - e^s0 - lgamma(y + 1) of every count y < kCountTable (FP64).
+__global__ void k_count_table(double* tab) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= kCountTable) return;
+  float s0, ey0;
+  pois_ref((float)y, s0, ey0);
+  tab[y] = (double)y * s0 - (double)ey0 - lgamma((double)y + 1.0);
+}
+
+cudaError_t launch_count_table(double* tab, cudaStream_t s) {
+  k_count_table<<<(kCountTable + 255) / 256, 256, 0, s>>>(tab);
+  return cudaGetLastError();
+}
+
+// Sample-independent part of each element's local factor, one thread per
+// element, in FP64 (all lanes busy): likelihood normalisers and count terms,
+// the -log q normaliser sum_d log sigma_d + D/2 log 2 pi, the root prior's
+// normaliser, and the maximum the sampler took out of loc.
+__global__ void k_elem_const(LevelView v, const float* __restrict__ q) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= v.n) return;
+  const int D = v.D, nobs = v.n_obs;
+  double c = 0.0;
+  for (int n = 0; n < nobs; ++n) {
+    const float yv = v.y[e * nobs + n];
+    switch (v.lik) {
+      case QEM_LIK_GAUSS: c += -0.5 * log(2.0 * 3.141592653589793 * (double)v.lik_var); break;
+      case QEM_LIK_POISSON_LOG: {
+        const int yi = (int)yv;
+        if (yv >= 0.f && yv < (float)kCountTable && (float)yi == yv && v.ltab) {
+          c += v.ltab[yi];
+        } else {
+          float s0, ey0;
+          pois_ref(yv, s0, ey0);
+          c += (double)yv * s0 - (double)ey0 - lgamma((double)yv + 1.0);
+        }
+        break;
+      }
+      case QEM_LIK_POISSON_RATE: c += -lgamma((double)yv + 1.0); break;
+      default: break;
+    }
+  }
+  if (v.qfam == QEM_Q_GAUSS) {
+    const float* sd = q + e * 2 * D + D;
+    for (int d = 0; d < D; ++d) c += (double)logf(sd[d]);
+    c += 0.5 * D * kLog2PiD;
+  }
+  if (v.level == 0) {
+    const double a0 = v.prior_a, b0 = v.prior_b;
+    if (v.prior == QEM_PRIOR_STD_NORMAL) c += -0.5 * D * log(2.0 * 3.141592653589793 * a0);
+    if (v.prior == QEM_PRIOR_GAMMA) c += D * (a0 * log(b0) - lgamma(a0));
+    if (v.prior == QEM_PRIOR_BETA) c += -D * (lgamma(a0) + lgamma(b0) - lgamma(a0 + b0));
+  }
+  v.cst[e] = c + (double)v.cshift[e];
+}
+
+cudaError_t launch_elem_const(const LevelView& v, const float* q, cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  k_elem_const<<<(unsigned)((v.n + 255) / 256), 256, 0, s>>>(v, q);
+  return cudaGetLastError();
+}
 
 __device__ __forceinline__ float softplusf(float s) { return fmaxf(s, 0.f) + log1pf(__expf(-fabsf(s))); }
 
@@ -84,9 +156,7 @@ template <int MAXD>
 __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, int K, const float* __restrict__ q,
                                                                   const float* __restrict__ eps, const Ctl* ctl) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ double cred[kSampleThreads / 32];
   __shared__ float fred[kSampleThreads / 32];
-  __shared__ double cst_sh;
   const long long e = blockIdx.x;
   const int D = v.D, nobs = v.n_obs, Dp = (D + 3) & ~3, zs_stride = D + 1;
   float* xs = sm;                       // [nobs][Dp]
@@ -100,45 +170,14 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
     xs[i] = d < D ? v.x[(e * nobs + n) * D + d] : 0.f;
   }
   for (int i = threadIdx.x; i < 2 * D; i += blockDim.x) qs[i] = q[e * 2 * D + i];
-  // Sample-independent part of the element's local factor, in FP64:
-  // likelihood normalisers, lgamma(y+1) and the Poisson reference terms.
-  double c = 0.0;
   for (int n = threadIdx.x; n < nobs; n += blockDim.x) {
     const float yv = v.y[e * nobs + n];
     ys[n] = yv;
-    switch (v.lik) {
-      case QEM_LIK_GAUSS: c += -0.5 * log(2.0 * 3.141592653589793 * (double)v.lik_var); break;
-      case QEM_LIK_POISSON_LOG: {
-        // y s - e^s = [y s0 - e^s0] + y (s - s0) - e^s0 expm1(s - s0), s0 = log max(y, 1)
-        const float s0 = logf(fmaxf(yv, 1.f));
-        const double ey0 = exp((double)s0);
-        s0s[n] = s0;
-        ey0s[n] = (float)ey0;
-        c += (double)yv * s0 - ey0 - lgamma((double)yv + 1.0);
-        break;
-      }
-      case QEM_LIK_POISSON_RATE: c += -lgamma((double)yv + 1.0); break;
-      default: break;
-    }
+    // y s - e^s = [y s0 - e^s0] + y (s - s0) - e^s0 expm1(s - s0): the
+    // bracket is in the element constant, the rest is evaluated per sample
+    if (v.lik == QEM_LIK_POISSON_LOG) pois_ref(yv, s0s[n], ey0s[n]);
   }
-  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) cred[threadIdx.x >> 5] = c;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += cred[j];
-    if (v.qfam == QEM_Q_GAUSS) {  // -log q normaliser: sum log sigma + D/2 log 2 pi
-      for (int d = 0; d < D; ++d) t += log((double)qs[D + d]);
-      t += 0.5 * D * kLog2PiD;
-    }
-    if (v.level == 0) {
-      const double a0 = v.prior_a, b0 = v.prior_b;
-      if (v.prior == QEM_PRIOR_STD_NORMAL) t += -0.5 * D * log(2.0 * 3.141592653589793 * a0);
-      if (v.prior == QEM_PRIOR_GAMMA) t += D * (a0 * log(b0) - lgamma(a0));
-      if (v.prior == QEM_PRIOR_BETA) t += -D * (lgamma(a0) + lgamma(b0) - lgamma(a0 + b0));
-    }
-    cst_sh = t;
-  }
   const unsigned long long seed = ctl->seed, iter = ctl->iter;
   const float4* xs4 = reinterpret_cast<const float4*>(xs);
   float lmax = -INFINITY;
@@ -280,7 +319,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
   for (int j = 0; j < (int)(blockDim.x >> 5); ++j) cmax = fmaxf(cmax, fred[j]);
   if (!isfinite(cmax)) cmax = 0.f;
   for (int k = threadIdx.x; k < K; k += blockDim.x) v.loc[e * K + k] -= cmax;
-  if (threadIdx.x == 0) v.cst[e] = cst_sh + (double)cmax;
+  if (threadIdx.x == 0) v.cshift[e] = cmax;
 }
 
 size_t sample_local_smem(const LevelView& v) {
@@ -836,17 +875,28 @@ cudaError_t launch_adj_compact(const LevelView& v, const LevelView& par, int K, 
 // ---------------------------------------------------------------------------
 // K6: moments m_e = sum_k w_e[k] T(z_e^k) (Eq. momone(z)).  Thread t of a
 // block owns dimension t % D (consecutive threads read consecutive floats of
-// z) and accumulates its share in FP32 with Kahan compensation; the shares
-// are added in FP64 in a fixed order.
+// z) and accumulates its share in FP32 with Kahan compensation; the shares of
+// a dimension are then combined pairwise in a fixed tree with an error-free
+// FP32 sum (TwoSum), so the result carries close to FP64 accuracy without
+// per-element FP64 arithmetic (single-lane FP64 loops dominated this kernel).
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   const float y = x - c;
   const float t = s + y;
   c = (t - s) - y;
   s = t;
 }
+// (s1 - c1) + (s2 - c2) -> (s1 - c1): TwoSum of the leading parts, the
+// rounding error joins the compensation.
+__device__ __forceinline__ void comp_merge(float& s1, float& c1, float s2, float c2) {
+  const float t = s1 + s2;
+  const float bp = t - s1;
+  const float err = (s1 - (t - bp)) + (s2 - bp);
+  s1 = t;
+  c1 = (c1 + c2) - err;
+}
 
 __global__ void k_moments(LevelView v, int K, double* mom) {
-  extern __shared__ double smd[];
+  extern __shared__ float4 smf[];   // per thread: (s0, c0, s1, c1)
   const long long e = blockIdx.x;
   const int D = v.D;
   const int per = blockDim.x / D;
@@ -872,17 +922,24 @@ __global__ void k_moments(LevelView v, int K, double* mom) {
       kahan_add(s1, c1, wk * t1);
     }
   }
-  smd[2 * t] = (double)s0 - (double)c0;
-  smd[2 * t + 1] = (double)s1 - (double)c1;
+  smf[t] = make_float4(s0, c0, s1, c1);
   __syncthreads();
-  if (t < D) {
-    double a0 = 0.0, a1 = 0.0;
-    for (int j = 0; j < per; ++j) {
-      a0 += smd[2 * (j * D + t)];
-      a1 += smd[2 * (j * D + t) + 1];
+  // share j of dimension d sits at j * D + d; merge j and j + h for h = 1, 2, 4, ...
+  const int j = t / D;
+  for (int h = 1; h < per; h <<= 1) {
+    if (t < per * D && (j & (2 * h - 1)) == 0 && j + h < per) {
+      float4 a = smf[t];
+      const float4 b = smf[t + h * D];
+      comp_merge(a.x, a.y, b.x, b.y);
+      comp_merge(a.z, a.w, b.z, b.w);
+      smf[t] = a;
     }
-    mom[(e * 2) * D + t] = a0;
-    mom[(e * 2 + 1) * D + t] = a1;
+    __syncthreads();
+  }
+  if (t < D) {
+    const float4 a = smf[t];
+    mom[(e * 2) * D + t] = (double)a.x - (double)a.y;
+    mom[(e * 2 + 1) * D + t] = (double)a.z - (double)a.w;
   }
 }
 
@@ -890,7 +947,7 @@ cudaError_t launch_moments(const LevelView& v, int K, double* mom, cudaStream_t 
   if (v.n == 0) return cudaSuccess;
   const int per = 256 / v.D > 0 ? 256 / v.D : 1;
   const int thr = per * v.D;
-  k_moments<<<(unsigned)v.n, thr, sizeof(double) * 2 * thr, s>>>(v, K, mom);
+  k_moments<<<(unsigned)v.n, thr, sizeof(float4) * thr, s>>>(v, K, mom);
   return cudaGetLastError();
 }
 

@@ -180,6 +180,28 @@ def beta_bernoulli(n_inst: int = 4, N: int = 20, a0: float = 2.0, b0: float = 3.
     return Model([root], name="beta_bernoulli", truth={"theta": th})
 
 
+def subset(model: Model, inst_ids) -> tuple:
+    """The sub-model of the instances inst_ids (roots), with every descendant.
+
+    Returns (sub_model, keep) where keep[l] holds, in order, the indices in the
+    full model of the elements of level l that the sub-model keeps (so per-
+    element arrays of the full model are sliced with keep[l]).
+    """
+    keep = [np.unique(np.asarray(inst_ids, np.int64))]
+    levels = [Level(**{**model.levels[0].__dict__, "n": len(keep[0]),
+                       "x": None if model.levels[0].x is None else model.levels[0].x[keep[0]],
+                       "y": None if model.levels[0].y is None else model.levels[0].y[keep[0]]})]
+    for lv in model.levels[1:]:
+        prev = keep[-1]
+        sel = np.nonzero(np.isin(lv.parent, prev))[0].astype(np.int64)
+        pos = np.searchsorted(prev, lv.parent[sel]).astype(np.int64)
+        keep.append(sel)
+        levels.append(Level(**{**lv.__dict__, "n": len(sel), "parent": pos,
+                               "x": None if lv.x is None else lv.x[sel],
+                               "y": None if lv.y is None else lv.y[sel]}))
+    return Model(levels, name=f"{model.name}_subset{len(keep[0])}"), keep
+
+
 def initial_q(model: Model) -> list:
     """Initial proposal of App. F: N(0, I) for Gaussian latents; the prior otherwise.
 

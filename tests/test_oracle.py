@@ -293,3 +293,22 @@ def test_gamma_and_beta_samplers_ks():
     o = O.estep(bb, q, K, eps=S.noise(bb, K, seed=2))
     for i, (a, b) in enumerate([(0.5, 0.8), (3.0, 7.0)]):
         assert stats.kstest(o["z"][0][i, :, 0], stats.beta(a, b).cdf).pvalue > 1e-3
+
+
+def test_instances_are_independent_and_subset_noise_matches():
+    """Instances share nothing: the oracle on a sub-model of a few instances,
+    with the counter-based noise those elements have in the full model, gives
+    the full model's numbers for them (the basis of sampled parity at full
+    size)."""
+    K = 8
+    full = S.batched_three_level(n_inst=7, D=3, seed=41, groups=(1, 3), units=(0, 4), n_obs=2)
+    q = S.random_q(full, seed=42, loc_scale=0.3, sd_lo=0.4, sd_hi=0.9)
+    ref = O.estep(full, q, K, seed=17, it=3)
+    sub, keep = S.subset(full, [5, 2])
+    assert [lv.n for lv in sub.levels] == [len(k) for k in keep]
+    eps = [O.draw_noise_at(17, 3, l, keep[l], K, lv.noise_per_sample(), lv.qfam) for l, lv in enumerate(sub.levels)]
+    got = O.estep(sub, [q[l][keep[l]] for l in range(3)], K, eps=eps)
+    np.testing.assert_allclose(got["log_pmp"], ref["log_pmp"][keep[0]], rtol=1e-13)
+    for l in range(3):
+        np.testing.assert_allclose(got["mom"][l], ref["mom"][l][keep[l]], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(got["w"][l], ref["w"][l][keep[l]], rtol=1e-12, atol=1e-15)
