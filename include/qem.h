@@ -110,13 +110,16 @@ typedef struct {
 typedef struct {
   int K;                /* samples per latent, 1..4096                                       */
   int precision;        /* QEM_PREC_*                                                        */
-  int tile;             /* 0: tuned default; otherwise a contraction tile preset             */
+  int tile;             /* 0: default launch shapes; QEM_TILE_AUTO: autotuned (see qem_tune)  */
   void* stream;         /* cudaStream_t the plan's work is enqueued on (NULL: default stream) */
   double var_floor;     /* Gaussian M-step variance floor factor (0: 1e-10)                   */
   double timeout_s;     /* bound of every device-side wait (0: 2 s)                           */
 } qem_plan_opts;
 
 typedef struct qem_plan_s* qem_plan_t;
+
+#define QEM_TILE_AUTO (-1)
+#define QEM_TUNE_FORCE 1
 
 /* Human-readable name of a status code (static storage). */
 const char* qem_status_string(qem_status s);
@@ -185,9 +188,13 @@ qem_status qem_weights(qem_plan_t plan, float* weights);
  * (level-major, [n_l][K][D_l] per level), asynchronously.                   */
 qem_status qem_samples(qem_plan_t plan, float* z);
 
-/* Run T iterations of QEM (Alg. 1) on the device, the E-step and M-step of
- * every iteration enqueued back to back (captured once as a CUDA graph and
- * replayed):
+/* Run T iterations of QEM (Alg. 1) on the device in ONE graph launch: a CUDA
+ * graph whose conditional (while) node repeats one iteration (E-step, EMA +
+ * M-step) until T are done or an error bit is set, with no host round trip
+ * between iterations.  The graph is built on the first call and kept by the
+ * plan while the buffers, lambda and sched_p stay the same (a call with
+ * others rebuilds it).  Asynchronous on the plan's stream (on the legacy
+ * stream: a private stream, synchronised before returning):
  *   mean_params   DEVICE double [q_len]  in: m_0; out: m_T
  *   q_params      DEVICE float  [q_len]  out: parameters matched to m_T
  *   moments       DEVICE double [q_len]  scratch for each iteration's estimate
@@ -195,6 +202,25 @@ qem_status qem_samples(qem_plan_t plan, float* z);
  * Iteration t draws its noise from the stream keyed by (seed, t).           */
 qem_status qem_run(qem_plan_t plan, int64_t T, double lambda, double sched_p, uint64_t seed,
                    double* mean_params, float* q_params, double* moments, double* log_pmp_trace);
+
+/* Autotuning of the launch shapes (sampler and moments block sizes; FP32
+ * contraction rows per block and staged child samples): a coordinate search
+ * timing whole E-steps on q_params (DEVICE float [q_len]) on the plan's
+ * stream, keeping a candidate only when it is at least 3% faster; results do
+ * not depend on the choice beyond rounding order of the FP32 contraction.
+ * The choice is cached per shape signature for the process, and in the file
+ * named by the environment variable QEM_TUNE_CACHE when set; a cached
+ * choice is applied without timing unless flags has QEM_TUNE_FORCE.  Runs
+ * E-steps and allocates q_len doubles of scratch; synchronises the stream;
+ * QEM_ERR_INVALID_ARG while the stream is being captured.  Plans made with
+ * tile = QEM_TILE_AUTO call it on their first qem_estep / qem_run outside a
+ * capture.  No counterpart in the paper (launch configuration only).        */
+qem_status qem_tune(qem_plan_t plan, const float* q_params, int flags);
+
+/* The plan's launch shapes: HOST int [4] = sampler threads per block, moments
+ * threads per block, FP32 contraction rows per block, FP32 staged child
+ * samples.                                                                    */
+qem_status qem_tune_get(qem_plan_t plan, int* params);
 
 /* Kernel classes of the per-kernel profiler. */
 enum {

@@ -17,6 +17,7 @@ QEM_GAMMA_TRIES = 8
 
 QEM_OK, QEM_ERR_INVALID_ARG, QEM_ERR_UNSUPPORTED, QEM_ERR_OOM, QEM_ERR_CUDA, QEM_ERR_NUMERIC, QEM_ERR_TIMEOUT = range(7)
 QEM_PREC_FP32, QEM_PREC_BF16, QEM_PREC_BF16X3 = 0, 1, 2
+QEM_TILE_AUTO, QEM_TUNE_FORCE = -1, 1
 
 
 class LevelDesc(C.Structure):
@@ -59,6 +60,8 @@ SIGNATURES = {
     "qem_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "qem_profile_name": (C.c_char_p, [C.c_int]),
     "qem_diag_tc_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "qem_tune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "qem_tune_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "qem_estep_single_noalloc": (C.c_int, [C.POINTER(LevelDesc), C.c_int, C.c_void_p, C.c_void_p, C.c_uint64,
                                            C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
 }

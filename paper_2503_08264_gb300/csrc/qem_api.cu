@@ -4,8 +4,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "qem_internal.cuh"
@@ -40,6 +45,7 @@ qem_status validate(const qem_model_desc* desc, const qem_plan_opts* o) {
   if (o->K < 1 || o->K > 4096) return QEM_ERR_INVALID_ARG;
   if (o->precision < QEM_PREC_FP32 || o->precision > QEM_PREC_BF16X3) return QEM_ERR_INVALID_ARG;
   if (o->var_floor < 0 || o->timeout_s < 0) return QEM_ERR_INVALID_ARG;
+  if (o->tile != 0 && o->tile != QEM_TILE_AUTO) return QEM_ERR_INVALID_ARG;
   const int L = desc->n_levels;
   for (int l = 0; l < L; ++l) {
     const qem_level_desc& d = desc->levels[l];
@@ -117,6 +123,20 @@ struct Prof {
 
 inline Prof* prof_of(qem_plan_t P) { return static_cast<Prof*>(P->prof); }
 
+// qem_run's graph: one conditional (while) node whose body is one iteration
+// (E-step, EMA + M-step, loop control), instantiated once per argument set.
+struct RunGraph {
+  const void* key[4] = {};
+  double lambda = -1.0, sched_p = -1.0;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  ~RunGraph() {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+  }
+};
+inline RunGraph* run_of(qem_plan_t P) { return static_cast<RunGraph*>(P->run); }
+
 // Launch `expr` (a cudaError_t expression), bracketed by events when profiling.
 #define QEM_LAUNCH(P, kind, expr)                                          \
   do {                                                                     \
@@ -141,7 +161,8 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
   const int L = P->L, K = P->K;
   for (int l = 0; l < L; ++l) {
     QEM_LAUNCH(P, QEM_K_SAMPLE,
-               launch_sample_local(P->lv[l], K, q + P->q_off[l], eps ? eps + P->eps_off[l] : nullptr, P->ctl, s));
+               launch_sample_local(P->lv[l], K, P->tune.sample_threads, q + P->q_off[l],
+                                   eps ? eps + P->eps_off[l] : nullptr, P->ctl, s));
     QEM_LAUNCH(P, QEM_K_SAMPLE, launch_elem_const(P->lv[l], q + P->q_off[l], s));
   }
   for (int l = 0; l + 1 < L; ++l) QEM_LAUNCH(P, QEM_K_PARENT, launch_parent_params(P->lv[l], P->lv[l + 1], K, s));
@@ -149,7 +170,7 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
     const bool has_children = l + 1 < L;
     if (has_children) QEM_LAUNCH(P, QEM_K_FINALIZE, launch_finalize(P->lv[l], K, has_children, s));
     if (P->precision == QEM_PREC_FP32) {
-      QEM_LAUNCH(P, QEM_K_FORWARD, launch_fwd_simt(P->lv[l], P->lv[l - 1], K, s));
+      QEM_LAUNCH(P, QEM_K_FORWARD, launch_fwd_simt(P->lv[l], P->lv[l - 1], K, P->tune.fwd_rows, P->tune.fwd_chunk, s));
     } else {
       QEM_LAUNCH(P, QEM_K_OPERANDS, tc_features(P, l));
       QEM_LAUNCH(P, QEM_K_FORWARD, tc_forward(P, l));
@@ -167,7 +188,7 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
       QEM_LAUNCH(P, QEM_K_ADJOINT, tc_adjoint(P, l));
     }
   }
-  for (int l = 0; l < L; ++l) QEM_LAUNCH(P, QEM_K_MOMENTS, launch_moments(P->lv[l], K, moments + P->q_off[l], s));
+  for (int l = 0; l < L; ++l) QEM_LAUNCH(P, QEM_K_MOMENTS, launch_moments(P->lv[l], K, P->tune.mom_threads, moments + P->q_off[l], s));
   return QEM_OK;
 }
 
@@ -178,6 +199,183 @@ qem_status mstep_body(qem_plan_t P, const double* moments, double* m, float* q, 
                launch_mstep(P->lv[l], moments ? moments + P->q_off[l] : nullptr, m + P->q_off[l], q + P->q_off[l],
                             lambda, sched_p, P->var_floor, t_host, P->ctl, P->stream));
   return QEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the launch shapes (Tune): a coordinate search over each knob's
+// candidates, timing whole E-steps with CUDA events on the plan's stream and
+// keeping a candidate only when it is at least 3% faster.  The choice is
+// cached per shape signature (precision, K, SM count; per level: element
+// count to a power of two, dimension, observations, likelihood, proposal
+// family) for the process and, when the environment variable QEM_TUNE_CACHE
+// names a file, across processes (one "signature|values" line per entry).
+std::mutex g_tune_mu;
+std::map<std::string, Tune> g_tune_cache;
+bool g_tune_file_read = false;
+
+const int kSampleCand[] = {64, 128, 256};
+const int kMomCand[] = {128, 256, 512};
+const int kRowsCand[] = {64, 128, 256};
+const int kChunkCand[] = {16, 32, 64};
+
+template <size_t N>
+bool one_of(int v, const int (&c)[N]) {
+  for (int x : c)
+    if (x == v) return true;
+  return false;
+}
+bool tune_valid(const Tune& t) {
+  return one_of(t.sample_threads, kSampleCand) && one_of(t.mom_threads, kMomCand) && one_of(t.fwd_rows, kRowsCand) &&
+         one_of(t.fwd_chunk, kChunkCand);
+}
+
+std::string tune_signature(const qem_plan_s* P) {
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "p%d K%d sm%d", P->precision, P->K, P->num_sms);
+  std::string sig = buf;
+  for (int l = 0; l < P->L; ++l) {
+    const LevelView& v = P->lv[l];
+    int b = 0;
+    while (b < 62 && (1LL << b) < v.n) ++b;
+    std::snprintf(buf, sizeof buf, " L%d:n2^%d,D%d,o%d,lik%d,q%d", l, b, v.D, v.n_obs, v.lik, v.qfam);
+    sig += buf;
+  }
+  return sig;
+}
+
+const char* tune_file() {
+  const char* f = std::getenv("QEM_TUNE_CACHE");
+  return f && *f ? f : nullptr;
+}
+
+void tune_read_file_locked() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = tune_file();
+  FILE* f = path ? std::fopen(path, "r") : nullptr;
+  if (!f) return;
+  char line[1024];
+  while (std::fgets(line, sizeof line, f)) {
+    char* bar = std::strchr(line, '|');
+    if (!bar) continue;
+    *bar = 0;
+    Tune t;
+    if (std::sscanf(bar + 1, "%d %d %d %d", &t.sample_threads, &t.mom_threads, &t.fwd_rows, &t.fwd_chunk) == 4 &&
+        tune_valid(t))
+      g_tune_cache[line] = t;
+  }
+  std::fclose(f);
+}
+
+void tune_store_locked(const std::string& sig, const Tune& t) {
+  g_tune_cache[sig] = t;
+  const char* path = tune_file();
+  FILE* f = path ? std::fopen(path, "a") : nullptr;
+  if (!f) return;
+  std::fprintf(f, "%s|%d %d %d %d\n", sig.c_str(), t.sample_threads, t.mom_threads, t.fwd_rows, t.fwd_chunk);
+  std::fclose(f);
+}
+
+// Mean time of `reps` E-steps after one warm-up (profiling is off meanwhile).
+qem_status time_esteps(qem_plan_t P, const float* q, double* mom, int reps, float* ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  qem_status st = QEM_OK;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) st = QEM_ERR_CUDA;
+  if (st == QEM_OK) st = estep_body(P, q, nullptr, mom, nullptr, nullptr);
+  if (st == QEM_OK && cudaEventRecord(a, P->stream) != cudaSuccess) st = QEM_ERR_CUDA;
+  for (int r = 0; r < reps && st == QEM_OK; ++r) st = estep_body(P, q, nullptr, mom, nullptr, nullptr);
+  if (st == QEM_OK && (cudaEventRecord(b, P->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+                       cudaEventElapsedTime(ms, a, b) != cudaSuccess))
+    st = QEM_ERR_CUDA;
+  if (st == QEM_OK) *ms /= (float)reps;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return st;
+}
+
+}  // namespace
+
+extern "C" qem_status qem_tune(qem_plan_t P, const float* q_params, int flags) {
+  if (!P || !q_params || (flags & ~QEM_TUNE_FORCE)) return QEM_ERR_INVALID_ARG;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(P->stream, &cs) != cudaSuccess) return QEM_ERR_CUDA;
+  if (cs != cudaStreamCaptureStatusNone) return QEM_ERR_INVALID_ARG;  // timing cannot run inside a capture
+  const std::string sig = tune_signature(P);
+  if (!(flags & QEM_TUNE_FORCE)) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_read_file_locked();
+    auto it = g_tune_cache.find(sig);
+    if (it != g_tune_cache.end()) {
+      P->tune = it->second;
+      P->tuned = true;
+      return QEM_OK;
+    }
+  }
+  Prof* pf = prof_of(P);
+  const bool prof_was_on = pf && pf->on;
+  if (pf) pf->on = false;
+  double* mom = nullptr;
+  qem_status st = cudaMalloc(&mom, sizeof(double) * (size_t)(P->q_len > 0 ? P->q_len : 1)) == cudaSuccess
+                      ? QEM_OK
+                      : QEM_ERR_OOM;
+  if (st == QEM_OK && launch_set_ctl(P->ctl, 0x5eedULL, 1, 1, -1, P->stream) != cudaSuccess) st = QEM_ERR_CUDA;
+  Tune best = P->tune;
+  float best_ms = 0.f;
+  if (st == QEM_OK) st = time_esteps(P, q_params, mom, 2, &best_ms);
+  auto try_knob = [&](int Tune::*field, const int* cand, int nc) {
+    for (int i = 0; i < nc && st == QEM_OK; ++i) {
+      if (cand[i] == best.*field) continue;
+      Tune t = best;
+      t.*field = cand[i];
+      P->tune = t;
+      float ms = 0.f;
+      st = time_esteps(P, q_params, mom, 2, &ms);
+      if (st == QEM_OK && ms < 0.97f * best_ms) {
+        best = t;
+        best_ms = ms;
+      }
+    }
+    P->tune = best;
+  };
+  try_knob(&Tune::sample_threads, kSampleCand, 3);
+  try_knob(&Tune::mom_threads, kMomCand, 3);
+  if (P->precision == QEM_PREC_FP32 && P->L > 1) {
+    try_knob(&Tune::fwd_rows, kRowsCand, 3);
+    try_knob(&Tune::fwd_chunk, kChunkCand, 3);
+  }
+  P->tune = best;
+  if (mom) {
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess && st == QEM_OK) st = QEM_ERR_CUDA;
+    cudaFree(mom);
+  }
+  if (st == QEM_OK) {
+    P->tuned = true;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_read_file_locked();
+    tune_store_locked(sig, best);
+  }
+  if (pf) pf->on = prof_was_on;
+  return st;
+}
+
+extern "C" qem_status qem_tune_get(qem_plan_t P, int* params) {
+  if (!P || !params) return QEM_ERR_INVALID_ARG;
+  params[0] = P->tune.sample_threads;
+  params[1] = P->tune.mom_threads;
+  params[2] = P->tune.fwd_rows;
+  params[3] = P->tune.fwd_chunk;
+  return QEM_OK;
+}
+
+namespace {
+
+// qem_estep / qem_run with QEM_TILE_AUTO: tune on first use outside a capture.
+qem_status maybe_autotune(qem_plan_t P, const float* q) {
+  if (P->tile != QEM_TILE_AUTO || P->tuned) return QEM_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(P->stream, &cs) != cudaSuccess) return QEM_ERR_CUDA;
+  if (cs != cudaStreamCaptureStatusNone) return QEM_OK;  // defaults until a call outside a capture
+  return qem_tune(P, q, 0);
 }
 
 }  // namespace
@@ -363,7 +561,7 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
   }
   if (ce == cudaSuccess && P->count_tab) ce = launch_count_table(P->count_tab, P->stream);
   size_t smem = 0;
-  for (int l = 0; l < L; ++l) smem = std::max(smem, sample_local_smem(P->lv[l]));
+  for (int l = 0; l < L; ++l) smem = std::max(smem, sample_local_smem(P->lv[l], kSampleThreadsLimit));
   if (ce == cudaSuccess) ce = configure_sample_local(smem);
   for (int l = 1; l < L && ce == cudaSuccess; ++l) ce = configure_adj_small(P->lv[l].D, K);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->stream);
@@ -389,6 +587,7 @@ qem_status qem_plan_destroy(qem_plan_t P) {
   cudaError_t e = cudaStreamSynchronize(P->stream);
   tc_plan_release(P);
   delete prof_of(P);
+  delete run_of(P);
   if (P->ws) cudaFree(P->ws);
   delete P;
   return e == cudaSuccess ? QEM_OK : QEM_ERR_CUDA;
@@ -420,6 +619,8 @@ qem_status qem_sizes(const qem_plan_t P, int64_t* q_len, int64_t* eps_len, int64
 qem_status qem_estep(qem_plan_t P, const float* q_params, const float* eps, uint64_t seed, uint64_t iter,
                      double* moments, double* log_pmp) {
   if (!P || !q_params || !moments) return QEM_ERR_INVALID_ARG;
+  const qem_status ts = maybe_autotune(P, q_params);
+  if (ts != QEM_OK) return ts;
   QEM_TRY(launch_set_ctl(P->ctl, seed, iter, 1, -1, P->stream));
   return estep_body(P, q_params, eps, moments, log_pmp, nullptr);
 }
@@ -478,35 +679,70 @@ qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint6
                    float* q_params, double* moments, double* log_pmp_trace) {
   if (!P || T < 0 || !mean_params || !q_params || !moments) return QEM_ERR_INVALID_ARG;
   if (!(lambda >= 0.0 && lambda <= 1.0) || !(sched_p >= 0.0 && sched_p < 1.0)) return QEM_ERR_INVALID_ARG;
-  cudaStream_t s = P->stream;
   cudaStream_t own = nullptr;
   Prof* pf = prof_of(P);
   const bool prof_was_on = pf && pf->on;
-  if (pf) pf->on = false;
-  if (s == nullptr) {  // legacy stream cannot be captured: use a private stream and finish synchronously
+  if (pf) pf->on = false;  // event records cannot sit inside a conditional body
+  if (P->stream == nullptr) {  // the legacy stream cannot be captured: a private stream, finished synchronously
     if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) return QEM_ERR_CUDA;
-    if (cudaDeviceSynchronize() != cudaSuccess) return QEM_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      cudaStreamDestroy(own);
+      return QEM_ERR_CUDA;
+    }
     P->stream = own;
   }
   qem_status st = QEM_OK;
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t ge = nullptr;
   do {
-    if (launch_set_ctl(P->ctl, seed, 1, 1, log_pmp_trace ? 0 : -1, P->stream) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
     st = mstep_body(P, nullptr, mean_params, q_params, lambda, sched_p, 1);  // Q_1 = set(m_0)
-    if (st != QEM_OK || T == 0) break;
-    if (cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
-    qem_status sb = estep_body(P, q_params, nullptr, moments, nullptr, log_pmp_trace);
-    if (sb == QEM_OK) sb = mstep_body(P, moments, mean_params, q_params, lambda, sched_p, 0);
-    if (sb == QEM_OK && launch_advance_ctl(P->ctl, P->lv[0].n, P->stream) != cudaSuccess) sb = QEM_ERR_CUDA;
-    cudaError_t ec = cudaStreamEndCapture(P->stream, &g);
-    if (sb != QEM_OK || ec != cudaSuccess) { st = sb != QEM_OK ? sb : QEM_ERR_CUDA; break; }
-    if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
-    for (int64_t t = 0; t < T; ++t)
-      if (cudaGraphLaunch(ge, P->stream) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
+    if (st == QEM_OK && T > 0) st = maybe_autotune(P, q_params);
+    if (st != QEM_OK) break;
+    if (launch_set_ctl(P->ctl, seed, 1, 1, log_pmp_trace ? 0 : -1, P->stream) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
+    if (T == 0) break;
+    RunGraph* R = run_of(P);
+    const void* key[4] = {mean_params, q_params, moments, log_pmp_trace};
+    const bool same = R && std::memcmp(R->key, key, sizeof(key)) == 0 && R->lambda == lambda && R->sched_p == sched_p;
+    if (!same) {
+      delete R;
+      R = new (std::nothrow) RunGraph();
+      P->run = R;
+      if (!R) { st = QEM_ERR_OOM; break; }
+      std::memcpy(R->key, key, sizeof(key));
+      R->lambda = lambda;
+      R->sched_p = sched_p;
+      cudaGraphConditionalHandle h;
+      cudaGraphNodeParams np = {};
+      cudaGraphNode_t node;
+      if (cudaGraphCreate(&R->g, 0) != cudaSuccess ||
+          cudaGraphConditionalHandleCreate(&h, R->g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        st = QEM_ERR_CUDA;
+        break;
+      }
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      if (cudaGraphAddNode(&node, R->g, nullptr, nullptr, 0, &np) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      if (cudaStreamBeginCaptureToGraph(P->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+          cudaSuccess) {
+        st = QEM_ERR_CUDA;
+        break;
+      }
+      qem_status sb = estep_body(P, q_params, nullptr, moments, nullptr, log_pmp_trace);
+      if (sb == QEM_OK) sb = mstep_body(P, moments, mean_params, q_params, lambda, sched_p, 0);
+      if (sb == QEM_OK && launch_loop_next(P->ctl, h, P->stream) != cudaSuccess) sb = QEM_ERR_CUDA;
+      cudaGraph_t captured = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(P->stream, &captured);
+      if (sb != QEM_OK || ec != cudaSuccess) { st = sb != QEM_OK ? sb : QEM_ERR_CUDA; break; }
+      if (cudaGraphInstantiate(&R->ge, R->g, 0) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
+    }
+    if (launch_loop_begin(P->ctl, T, P->stream) != cudaSuccess || cudaGraphLaunch(R->ge, P->stream) != cudaSuccess)
+      st = QEM_ERR_CUDA;
   } while (0);
-  if (ge) cudaGraphExecDestroy(ge);
-  if (g) cudaGraphDestroy(g);
+  if (st != QEM_OK && run_of(P) && !run_of(P)->ge) {  // a half-built graph is not kept
+    delete run_of(P);
+    P->run = nullptr;
+  }
   if (own) {
     if (cudaStreamSynchronize(own) != cudaSuccess && st == QEM_OK) st = QEM_ERR_CUDA;
     cudaStreamDestroy(own);

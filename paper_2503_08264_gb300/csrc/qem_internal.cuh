@@ -28,6 +28,7 @@ struct Ctl {
   long long trace_row;         // row of the log P_MP trace to write (-1: none)
   int err;                     // ERR_* bits
   int pad;
+  long long remaining;         // iterations left in a device-side loop (qem_run)
 };
 
 // Device view of one level of the plan (all pointers device).
@@ -80,6 +81,17 @@ struct TcBuffers;  // tensor-core operand buffers (qem_tc.cu)
 
 }  // namespace qem
 
+namespace qem {
+// Launch shapes chosen by the autotuner (qem_tune.cu); the defaults are
+// what an untuned plan uses.
+struct Tune {
+  int sample_threads = 128;  // threads per block of the sampler (one block per element)
+  int mom_threads = 256;     // threads per block of the moments kernel (one block per element)
+  int fwd_rows = 128;        // FP32 contraction: parent samples per block (one per thread)
+  int fwd_chunk = 32;        // FP32 contraction: child samples staged per shared-memory round
+};
+}  // namespace qem
+
 struct qem_plan_s {
   int L = 0;
   int K = 0;
@@ -101,6 +113,9 @@ struct qem_plan_s {
   size_t ws_bytes = 0;
   qem::TcBuffers* tc = nullptr;
   void* prof = nullptr;        // per-kernel event records (qem_api.cu)
+  void* run = nullptr;         // cached device-loop graph of qem_run (qem_api.cu)
+  qem::Tune tune;              // launch shapes (defaults, or chosen by qem_tune)
+  bool tuned = false;          // qem_tune has run (or a cached choice was applied)
 };
 
 namespace qem {
@@ -188,6 +203,8 @@ __device__ __forceinline__ bool spin_until_ge(const volatile int* flag, int targ
 
 // ---------------------------------------------------------------------------
 // Host-side launchers (qem_simt.cu / qem_tc.cu).
+cudaError_t launch_loop_begin(Ctl* ctl, long long iterations, cudaStream_t s);
+cudaError_t launch_loop_next(Ctl* ctl, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_set_ctl(Ctl* ctl, unsigned long long seed, unsigned long long iter, long long t,
                            long long trace_row, cudaStream_t s);
 cudaError_t launch_advance_ctl(Ctl* ctl, long long n_inst, cudaStream_t s);
@@ -196,11 +213,11 @@ cudaError_t launch_advance_ctl(Ctl* ctl, long long n_inst, cudaStream_t s);
 constexpr int kCountTable = 4096;
 cudaError_t launch_count_table(double* tab, cudaStream_t s);
 cudaError_t launch_elem_const(const LevelView& v, const float* q, cudaStream_t s);
-cudaError_t launch_sample_local(const LevelView& v, int K, const float* q, const float* eps, const Ctl* ctl,
+cudaError_t launch_sample_local(const LevelView& v, int K, int threads, const float* q, const float* eps, const Ctl* ctl,
                                 cudaStream_t s);
 cudaError_t launch_parent_params(const LevelView& parent, const LevelView& child, int K, cudaStream_t s);
 cudaError_t launch_finalize(const LevelView& v, int K, bool has_children, cudaStream_t s);
-cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
+cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& parent, int K, int rows, int chunk, cudaStream_t s);
 cudaError_t launch_plate_sum(const LevelView& parent, const LevelView& child, int K, cudaStream_t s);
 cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* log_pmp, double* user_out,
                         double* trace, Ctl* ctl, cudaStream_t s);
@@ -208,10 +225,11 @@ cudaError_t launch_compact(const LevelView& parent, int K, cudaStream_t s);
 cudaError_t launch_adj_compact(const LevelView& v, const LevelView& parent, int K, int max_eff, cudaStream_t s);
 cudaError_t launch_adj_small(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
 cudaError_t configure_adj_small(int D, int K);
-cudaError_t launch_moments(const LevelView& v, int K, double* mom, cudaStream_t s);
+cudaError_t launch_moments(const LevelView& v, int K, int threads, double* mom, cudaStream_t s);
 cudaError_t launch_mstep(const LevelView& v, const double* mom, double* m, float* q, double lambda,
                          double sched_p, double var_floor, long long t_host, const Ctl* ctl, cudaStream_t s);
-size_t sample_local_smem(const LevelView& v);
+size_t sample_local_smem(const LevelView& v, int threads);
+constexpr int kSampleThreadsLimit = 256;   // largest sampler block the tuner tries
 cudaError_t configure_sample_local(size_t smem);
 cudaError_t launch_mean_params(const LevelView& v, const float* q, double* m, cudaStream_t s);
 

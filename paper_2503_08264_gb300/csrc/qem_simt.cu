@@ -32,6 +32,30 @@ cudaError_t launch_set_ctl(Ctl* ctl, unsigned long long seed, unsigned long long
   return cudaGetLastError();
 }
 
+// Device-side iteration loop of qem_run: the body of a conditional (while)
+// graph node ends with k_loop_next, which advances the iteration counters
+// like k_advance_ctl, counts the iteration off and sets the node's condition;
+// the loop also stops once an error bit is set.
+__global__ void k_loop_begin(Ctl* ctl, long long iterations) { ctl->remaining = iterations; }
+
+__global__ void k_loop_next(Ctl* ctl, cudaGraphConditionalHandle h) {
+  ctl->iter += 1;
+  ctl->t += 1;
+  if (ctl->trace_row >= 0) ctl->trace_row += 1;
+  const long long left = --ctl->remaining;
+  cudaGraphSetConditional(h, (left > 0 && ctl->err == 0) ? 1u : 0u);
+}
+
+cudaError_t launch_loop_begin(Ctl* ctl, long long iterations, cudaStream_t s) {
+  k_loop_begin<<<1, 1, 0, s>>>(ctl, iterations);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_next(Ctl* ctl, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_loop_next<<<1, 1, 0, s>>>(ctl, h);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_advance_ctl(Ctl* ctl, long long, cudaStream_t s) {
   k_advance_ctl<<<1, 1, 0, s>>>(ctl);
   return cudaGetLastError();
@@ -78,7 +102,7 @@ __device__ double gamma_variate(double a, const NoiseSrc& ns, int base) {
 // staged through shared memory for coalesced stores.  No FP64 arithmetic
 // runs per element here: a block has one element, and single-lane FP64 work
 // (GB300's FP64 rate is a small fraction of FP32) dominated it.
-constexpr int kSampleThreads = 128;
+constexpr int kSampleThreadsMax = 256;
 
 // Poisson-log reference point of a count: s0 = log max(y, 1) and e^s0, both
 // in FP32 and identical wherever they are evaluated (the sampler, the count
@@ -153,10 +177,10 @@ cudaError_t launch_elem_const(const LevelView& v, const float* q, cudaStream_t s
 __device__ __forceinline__ float softplusf(float s) { return fmaxf(s, 0.f) + log1pf(__expf(-fabsf(s))); }
 
 template <int MAXD>
-__global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, int K, const float* __restrict__ q,
+__global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v, int K, const float* __restrict__ q,
                                                                   const float* __restrict__ eps, const Ctl* ctl) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ float fred[kSampleThreads / 32];
+  __shared__ float fred[kSampleThreadsMax / 32];
   const long long e = blockIdx.x;
   const int D = v.D, nobs = v.n_obs, Dp = (D + 3) & ~3, zs_stride = D + 1;
   float* xs = sm;                       // [nobs][Dp]
@@ -322,9 +346,9 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_local(LevelView v, in
   if (threadIdx.x == 0) v.cshift[e] = cmax;
 }
 
-size_t sample_local_smem(const LevelView& v) {
+size_t sample_local_smem(const LevelView& v, int threads) {
   const int Dp = (v.D + 3) & ~3;
-  return sizeof(float) * (size_t)(v.n_obs * Dp + 3 * v.n_obs + 2 * v.D + kSampleThreads * (v.D + 1)) + 16;
+  return sizeof(float) * (size_t)(v.n_obs * Dp + 3 * v.n_obs + 2 * v.D + threads * (v.D + 1)) + 16;
 }
 
 template <int MAXD>
@@ -343,18 +367,19 @@ cudaError_t configure_sample_local(size_t smem) {
   return e;
 }
 
-cudaError_t launch_sample_local(const LevelView& v, int K, const float* q, const float* eps, const Ctl* ctl,
+cudaError_t launch_sample_local(const LevelView& v, int K, int threads, const float* q, const float* eps, const Ctl* ctl,
                                 cudaStream_t s) {
   if (v.n == 0) return cudaSuccess;
-  const size_t smem = sample_local_smem(v);
+  if (threads < 32 || threads > kSampleThreadsMax || threads % 32) return cudaErrorInvalidValue;
+  const size_t smem = sample_local_smem(v, threads);
   const unsigned grid = (unsigned)v.n;
   const int Dp = (v.D + 3) & ~3;
-  if (Dp <= 4) k_sample_local<4><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
-  else if (Dp <= 8) k_sample_local<8><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
-  else if (Dp <= 12) k_sample_local<12><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
-  else if (Dp <= 20) k_sample_local<20><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
-  else if (Dp <= 40) k_sample_local<40><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
-  else k_sample_local<64><<<grid, kSampleThreads, smem, s>>>(v, K, q, eps, ctl);
+  if (Dp <= 4) k_sample_local<4><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
+  else if (Dp <= 8) k_sample_local<8><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
+  else if (Dp <= 12) k_sample_local<12><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
+  else if (Dp <= 20) k_sample_local<20><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
+  else if (Dp <= 40) k_sample_local<40><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
+  else k_sample_local<64><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
   return cudaGetLastError();
 }
 
@@ -430,13 +455,14 @@ cudaError_t launch_finalize(const LevelView& v, int K, bool has_children, cudaSt
 //   lt[e][kp] = log (1/K) sum_k exp( log p(z_e^k | z_p^kp) + htil[e][k] )
 // One thread per parent sample kp; the element's child samples stream
 // through shared memory in chunks; online max-shifted sum per row.
-constexpr int kRowTile = 128;
-constexpr int kChunk = 32;
+constexpr int kRowTile = 128;     // rows per block of the FP32 adjoint
+constexpr int kChunk = 32;        // staged parent samples of the FP32 adjoint
+constexpr int kFwdRowsMax = 256;
 
-template <int MAXD>
-__global__ void __launch_bounds__(kRowTile) k_fwd_simt(LevelView v, LevelView par, int K, int n_rt) {
-  __shared__ float zs[kChunk * MAXD];
-  __shared__ float hs[kChunk];
+template <int MAXD, int CHUNK>
+__global__ void __launch_bounds__(kFwdRowsMax) k_fwd_simt(LevelView v, LevelView par, int K, int n_rt) {
+  __shared__ float zs[CHUNK * MAXD];
+  __shared__ float hs[CHUNK];
   const long long e = blockIdx.x / n_rt;
   const int kp = (blockIdx.x % n_rt) * blockDim.x + threadIdx.x;
   const int D = v.D;
@@ -454,20 +480,20 @@ __global__ void __launch_bounds__(kRowTile) k_fwd_simt(LevelView v, LevelView pa
   }
   if (act) pc = par.pc[p * K + kp];
   float m = -INFINITY, s = 0.f;
-  for (int k0 = 0; k0 < K; k0 += kChunk) {
-    const int nk = min(kChunk, K - k0);
+  for (int k0 = 0; k0 < K; k0 += CHUNK) {
+    const int nk = min(CHUNK, K - k0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kChunk * MAXD; i += blockDim.x) {
+    for (int i = threadIdx.x; i < CHUNK * MAXD; i += blockDim.x) {
       const int j = i / MAXD, d = i % MAXD;
       zs[i] = (j < nk && d < D) ? v.z[(e * K + k0 + j) * D + d] : 0.f;
     }
     for (int i = threadIdx.x; i < nk; i += blockDim.x) hs[i] = v.htil[e * K + k0 + i];
     __syncthreads();
     if (!act) continue;
-    float val[kChunk];
+    float val[CHUNK];
     float cm = -INFINITY;
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) {
+    for (int j = 0; j < CHUNK; ++j) {
       float a = -INFINITY;
       if (j < nk) {
         a = hs[j];
@@ -486,26 +512,37 @@ __global__ void __launch_bounds__(kRowTile) k_fwd_simt(LevelView v, LevelView pa
       m = cm;
     }
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) s += expf(val[j] - m);
+    for (int j = 0; j < CHUNK; ++j) s += expf(val[j] - m);
   }
   if (act) v.lt[e * K + kp] = pc + (m + logf(s) - logf((float)K));
 }
 
-template <int MAXD>
-static cudaError_t fwd_simt_dispatch(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
-  const int thr = K >= kRowTile ? kRowTile : ((K + 31) / 32) * 32;
+template <int MAXD, int CHUNK>
+static cudaError_t fwd_simt_launch(const LevelView& v, const LevelView& par, int K, int rows, cudaStream_t s) {
+  const int thr = K >= rows ? rows : ((K + 31) / 32) * 32;
   const int n_rt = (K + thr - 1) / thr;
-  k_fwd_simt<MAXD><<<(unsigned)(v.n * n_rt), thr, 0, s>>>(v, par, K, n_rt);
+  k_fwd_simt<MAXD, CHUNK><<<(unsigned)(v.n * n_rt), thr, 0, s>>>(v, par, K, n_rt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
+template <int MAXD>
+static cudaError_t fwd_simt_dispatch(const LevelView& v, const LevelView& par, int K, int rows, int chunk,
+                                     cudaStream_t s) {
+  if (chunk == 16) return fwd_simt_launch<MAXD, 16>(v, par, K, rows, s);
+  if (chunk == 64 && MAXD <= 20) return fwd_simt_launch<MAXD, 64>(v, par, K, rows, s);
+  return fwd_simt_launch<MAXD, 32>(v, par, K, rows, s);
+}
+
+// rows: parent samples per block (a multiple of 32, at most 256); chunk: child
+// samples staged per round (16, 32, or 64 for D <= 20; others take 32).
+cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& par, int K, int rows, int chunk, cudaStream_t s) {
   if (v.n == 0) return cudaSuccess;
-  if (v.D <= 4) return fwd_simt_dispatch<4>(v, par, K, s);
-  if (v.D <= 8) return fwd_simt_dispatch<8>(v, par, K, s);
-  if (v.D <= 20) return fwd_simt_dispatch<20>(v, par, K, s);
-  if (v.D <= 32) return fwd_simt_dispatch<32>(v, par, K, s);
-  return fwd_simt_dispatch<64>(v, par, K, s);
+  if (rows < 32 || rows > kFwdRowsMax || rows % 32) return cudaErrorInvalidValue;
+  if (v.D <= 4) return fwd_simt_dispatch<4>(v, par, K, rows, chunk, s);
+  if (v.D <= 8) return fwd_simt_dispatch<8>(v, par, K, rows, chunk, s);
+  if (v.D <= 20) return fwd_simt_dispatch<20>(v, par, K, rows, chunk, s);
+  if (v.D <= 32) return fwd_simt_dispatch<32>(v, par, K, rows, chunk, s);
+  return fwd_simt_dispatch<64>(v, par, K, rows, chunk, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -943,9 +980,10 @@ __global__ void k_moments(LevelView v, int K, double* mom) {
   }
 }
 
-cudaError_t launch_moments(const LevelView& v, int K, double* mom, cudaStream_t s) {
+cudaError_t launch_moments(const LevelView& v, int K, int threads, double* mom, cudaStream_t s) {
   if (v.n == 0) return cudaSuccess;
-  const int per = 256 / v.D > 0 ? 256 / v.D : 1;
+  if (threads < v.D || threads > 1024) threads = v.D > 256 ? v.D : 256;
+  const int per = threads / v.D > 0 ? threads / v.D : 1;
   const int thr = per * v.D;
   k_moments<<<(unsigned)v.n, thr, sizeof(float4) * thr, s>>>(v, K, mom);
   return cudaGetLastError();

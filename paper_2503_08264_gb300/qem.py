@@ -70,6 +70,16 @@ def qem_samples(h, z) -> None:
     L.check(L.load().qem_samples(h, _ptr(z)), "qem_samples")
 
 
+def qem_tune(h, q_params, flags: int = 0) -> None:
+    L.check(L.load().qem_tune(h, _ptr(q_params), flags), "qem_tune")
+
+
+def qem_tune_get(h) -> dict:
+    a = (C.c_int * 4)()
+    L.check(L.load().qem_tune_get(h, a), "qem_tune_get")
+    return {"sample_threads": a[0], "mom_threads": a[1], "fwd_rows": a[2], "fwd_chunk": a[3]}
+
+
 def qem_run(h, T: int, lam: float, sched_p: float, seed: int, mean_params, q_params, moments, trace=None) -> None:
     L.check(L.load().qem_run(h, T, lam, sched_p, seed, _ptr(mean_params), _ptr(q_params), _ptr(moments),
                              _ptr(trace)), "qem_run")
@@ -193,6 +203,13 @@ class Plan:
             moments = torch.empty(self.q_len, dtype=torch.float64, device=self.device)
         qem_run(self.h, T, lam, sched_p, seed, mean_params, q_params, moments, trace)
         return moments
+
+    def tune(self, q_params, force: bool = False) -> dict:
+        qem_tune(self.h, q_params, L.QEM_TUNE_FORCE if force else 0)
+        return qem_tune_get(self.h)
+
+    def tuning(self) -> dict:
+        return qem_tune_get(self.h)
 
     def profile(self, on: bool = True) -> None:
         qem_profile_enable(self.h, on)

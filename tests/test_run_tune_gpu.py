@@ -1,0 +1,96 @@
+"""GPU tests of batching: the single-launch device loop (qem_run) and the
+launch-shape autotuner (qem_tune).
+
+* qem_run runs T iterations of Alg. 1 as one graph launch (a conditional
+  while node); on a batch of uneven three-level instances with the
+  split-BF16 contraction it reproduces, bit for bit, the host loop of
+  qem_estep / qem_mstep with the same noise stream, and a second call
+  (the cached graph) does too.
+* qem_tune picks launch shapes from its candidate sets; an autotuned plan
+  still matches the FP64 oracle at the FP32 tolerance; a second plan of the
+  same shapes takes the cached choice.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2503_08264_gb300 import synth as S
+
+from test_parity_gpu import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2503_08264_gb300 import build
+    build.build()
+    O.build()
+
+
+def test_qem_run_single_launch_matches_host_loop():
+    from paper_2503_08264_gb300 import qem
+    model = S.batched_three_level(n_inst=12, D=8, seed=61, groups=(0, 6), units=(0, 30))
+    K, T, lam, seed = 256, 6, 0.5, 7
+    plan = qem.Plan(model, K, precision="bf16x3")
+    q0 = plan.flat(S.initial_q(model))
+    m0 = plan.mean_params(q0)
+    # host loop: Q_1 = set(m_0), then E-step and EMA + M-step per iteration
+    m_h, q_h = m0.clone(), torch.empty_like(q0)
+    plan.mstep(None, m_h, q_h, lam, t=1)
+    mom = torch.empty(plan.q_len, dtype=torch.float64, device="cuda")
+    lps = []
+    for t in range(1, T + 1):
+        _, lp = plan.estep(q_h, None, seed=seed, it=t, moments=mom)
+        lps.append(lp.clone())
+        plan.mstep(mom, m_h, q_h, lam, t=t)
+    torch.cuda.synchronize()
+    for rep in range(2):
+        m_r, q_r = m0.clone(), torch.empty_like(q0)
+        trace = torch.full((T * plan.n_inst,), np.nan, dtype=torch.float64, device="cuda")
+        plan.run(T, lam, m_r, q_r, seed=seed, trace=trace)
+        torch.cuda.synchronize()
+        assert torch.equal(m_r, m_h), f"call {rep}: mean parameters differ"
+        assert torch.equal(q_r, q_h), f"call {rep}: proposal parameters differ"
+        assert torch.equal(trace.view(T, -1), torch.stack(lps)), f"call {rep}: log P_MP trace differs"
+    # a shorter run reuses the graph and stops after its own T
+    m_r, q_r = m0.clone(), torch.empty_like(q0)
+    plan.run(2, lam, m_r, q_r, seed=seed)
+    m_2, q_2 = m0.clone(), torch.empty_like(q0)
+    plan.mstep(None, m_2, q_2, lam, t=1)
+    for t in range(1, 3):
+        plan.estep(q_2, None, seed=seed, it=t, moments=mom)
+        plan.mstep(mom, m_2, q_2, lam, t=t)
+    torch.cuda.synchronize()
+    assert torch.equal(m_r, m_2)
+    plan.close()
+
+
+def test_autotuned_plan_matches_oracle_and_caches():
+    from paper_2503_08264_gb300 import _lib as L
+    from paper_2503_08264_gb300 import qem
+    model = S.hier_logistic(M=300, N=5, seed=71)
+    K = 128
+    q = S.random_q(model, seed=72, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    eps = S.noise(model, K, seed=73)
+    plan = qem.Plan(model, K, precision="fp32", tile=L.QEM_TILE_AUTO)
+    qd = plan.flat(q)
+    mom, _ = plan.estep(qd, plan.flat(eps))   # tunes first (outside any capture)
+    choice = plan.tuning()
+    print("tuned", choice)
+    assert choice["sample_threads"] in (64, 128, 256)
+    assert choice["mom_threads"] in (128, 256, 512)
+    assert choice["fwd_rows"] in (64, 128, 256) and choice["fwd_chunk"] in (16, 32, 64)
+    got = {"log_pmp": plan.log_pmp(), "mom": plan.split_q(mom), "w": plan.split_w(plan.weights())}
+    ref = O.estep(model, q, K, eps=eps)
+    assert_parity(model, q, got, ref, 1e-5, 1e-5, 1e-5)
+    # every candidate of every knob is a valid launch: force each FP32 tile
+    forced = plan.tune(qd, force=True)
+    assert forced == plan.tuning()
+    plan.close()
+    # same shapes: the cached choice is applied without timing
+    plan2 = qem.Plan(model, K, precision="fp32")
+    assert plan2.tune(plan2.flat(q)) == forced
+    plan2.close()
