@@ -258,6 +258,7 @@ def run_ours(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dist_init(ws, "nccl")
+    from paper_2503_08264_gb300 import _lib as L
     from paper_2503_08264_gb300 import qem  # fails loudly when libqem.so is missing
 
     builder, K, default_prec = WORKLOADS[args.workload]
@@ -265,7 +266,7 @@ def run_ours(args):
     model = builder(1000 + rank)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        plan = qem.Plan(model, K, precision=precision, stream=stream)
+        plan = qem.Plan(model, K, precision=precision, stream=stream, tile=L.QEM_TILE_AUTO)
         q0 = S.initial_q(model)
         q_d = plan.flat(q0)
         m_d = plan.mean_params(q_d)
@@ -281,9 +282,13 @@ def run_ours(args):
     t_iter = 1
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step(t_iter)
+            step(t_iter)   # the first call autotunes the launch shapes
             t_iter += 1
+        # build the single-launch loop graph (timed separately below) from a copy
+        m_g, q_g = m_d.clone(), q_d.clone()
+        plan.run(1, EMA_LAMBDA, m_g, q_g, moments=mom_d, seed=seed)
     stream.synchronize()
+    per_iter, per_call = plan.run_kernels()
     plan.log_pmp()  # raises on a non-finite estimate or a device error
     barrier(ws)
     torch.cuda.synchronize()
@@ -309,10 +314,25 @@ def run_ours(args):
     max_ms, tot_pairs = aggregate(local_ms, pairs * args.steps, ws, device="cuda")
     value = tot_pairs / (max_ms * 1e-3)
 
+    # the same iterations as one graph launch (device-side loop, no host
+    # round trip between iterations)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        plan.run(args.steps, EMA_LAMBDA, m_g, q_g, moments=mom_d, seed=seed)
+        g1.record(stream)
+    stream.synchronize()
+    g_ms, g_pairs = aggregate(g0.elapsed_time(g1), pairs * args.steps, ws, device="cuda")
+    graph_loop = {"ms_per_step": g_ms / args.steps, "value": g_pairs / (g_ms * 1e-3),
+                  "launches": int(per_iter * args.steps + per_call)}
+
     # dominant kernel and its roofline (CUDA events on the plan's stream)
     kind = max(prof, key=lambda k: prof[k][0])
     k_ms, k_n = prof[kind]
-    gpu_launches = int(sum(n for _, n in prof.values()))
+    # kernels of one iteration, counted in the loop graph (the host loop launches
+    # the same ones, its control set-up in place of the loop control)
+    gpu_launches = int(per_iter * args.steps)
     sm_max = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
     D_child = model.levels[-1].dim
     pairs_per_launch = pairs / max(1, (len(model.levels) - 1))
@@ -371,7 +391,9 @@ def run_ours(args):
                            "precision": precision, "noise": "in-kernel Philox4x32-10",
                            "step": "qem_estep + qem_mstep (one Alg. 1 iteration)",
                            "l2": f"working set {ws_bytes / 1e9:.2f} GB > 129 MB L2 (no flush)",
-                           "parallelism": f"replicas x{ws} (independent instances)"},
+                           "parallelism": f"replicas x{ws} (independent instances)",
+                           "launch_shapes": plan.tuning()},
+                "graph_loop": graph_loop,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clk, "kernels_ms": {k: round(v[0], 4) for k, v in prof.items()},
                 "log_pmp_last": float(lp_host[0])}

@@ -222,6 +222,12 @@ qem_status qem_tune(qem_plan_t plan, const float* q_params, int flags);
  * samples.                                                                    */
 qem_status qem_tune_get(qem_plan_t plan, int* params);
 
+/* Kernels of the plan's qem_run graph (tracing support; valid after a
+ * qem_run call): per_iteration = kernel launches of one iteration inside the
+ * device loop (the E-step, the M-step and the loop control), per_call = the
+ * kernels each qem_run call launches outside the loop.                        */
+qem_status qem_run_kernels(qem_plan_t plan, int64_t* per_iteration, int64_t* per_call);
+
 /* Kernel classes of the per-kernel profiler. */
 enum {
   QEM_K_SAMPLE = 0,      /* sampling and local factors                 */

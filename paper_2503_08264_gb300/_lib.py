@@ -60,6 +60,7 @@ SIGNATURES = {
     "qem_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "qem_profile_name": (C.c_char_p, [C.c_int]),
     "qem_diag_tc_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "qem_run_kernels": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "qem_tune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "qem_tune_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "qem_estep_single_noalloc": (C.c_int, [C.POINTER(LevelDesc), C.c_int, C.c_void_p, C.c_void_p, C.c_uint64,

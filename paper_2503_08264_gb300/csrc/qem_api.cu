@@ -129,6 +129,7 @@ struct RunGraph {
   const void* key[4] = {};
   double lambda = -1.0, sched_p = -1.0;
   cudaGraph_t g = nullptr;
+  cudaGraph_t body = nullptr;   // the while node's body (owned by g)
   cudaGraphExec_t ge = nullptr;
   ~RunGraph() {
     if (ge) cudaGraphExecDestroy(ge);
@@ -723,6 +724,7 @@ qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint6
       np.conditional.size = 1;
       if (cudaGraphAddNode(&node, R->g, nullptr, nullptr, 0, &np) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
       cudaGraph_t body = np.conditional.phGraph_out[0];
+      R->body = body;
       if (cudaStreamBeginCaptureToGraph(P->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
           cudaSuccess) {
         st = QEM_ERR_CUDA;
@@ -750,6 +752,25 @@ qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint6
   }
   if (pf) pf->on = prof_was_on;
   return st;
+}
+
+qem_status qem_run_kernels(qem_plan_t P, int64_t* per_iteration, int64_t* per_call) {
+  if (!P || !per_iteration || !per_call) return QEM_ERR_INVALID_ARG;
+  RunGraph* R = run_of(P);
+  if (!R || !R->body) return QEM_ERR_INVALID_ARG;
+  size_t n = 0;
+  if (cudaGraphGetNodes(R->body, nullptr, &n) != cudaSuccess) return QEM_ERR_CUDA;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(R->body, nodes.data(), &n) != cudaSuccess) return QEM_ERR_CUDA;
+  int64_t k = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) return QEM_ERR_CUDA;
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  *per_iteration = k;
+  *per_call = P->L + 2;  // the initial M-step (one kernel per level), the control set-up, the loop set-up
+  return QEM_OK;
 }
 
 static const char* kKindNames[QEM_K_COUNT] = {"sample_local", "parent_params", "finalize", "forward",

@@ -204,6 +204,12 @@ class Plan:
         qem_run(self.h, T, lam, sched_p, seed, mean_params, q_params, moments, trace)
         return moments
 
+    def run_kernels(self) -> tuple:
+        """(kernels per iteration of the qem_run loop, kernels per qem_run call outside it)."""
+        a, b = C.c_int64(), C.c_int64()
+        L.check(L.load().qem_run_kernels(self.h, C.byref(a), C.byref(b)), "qem_run_kernels")
+        return a.value, b.value
+
     def tune(self, q_params, force: bool = False) -> dict:
         qem_tune(self.h, q_params, L.QEM_TUNE_FORCE if force else 0)
         return qem_tune_get(self.h)
