@@ -222,6 +222,54 @@ qem_status qem_tune(qem_plan_t plan, const float* q_params, int flags);
  * samples.                                                                    */
 qem_status qem_tune_get(qem_plan_t plan, int* params);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper: an amortised proposal
+ * network, plain QEM continuing from its prediction).  For a user of the
+ * hierarchical logistic model (dim = QEM_MLP_DIM) with items (x_n, y_n):
+ *   features f = [sum_n x_n y_n (D), sum_n x_n (D), sum_n y_n]        (2D+1)
+ *   h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), o = W3 h2 + b3        (2D)
+ *   q = N(o[:D], diag exp(o[D:])^2)
+ * trained on the KL divergence from the user's QEM proposal N(m, diag s^2)
+ * to q (mean over users, summed over dimensions).  Matrix-product operands
+ * are rounded to BF16, products accumulate in FP32.  Parameters: DEVICE
+ * float [QEM_MLP_PARAMS], W1 [H][2D+1], b1 [H], W2 [H][H], b2 [H],
+ * W3 [2D][H], b3 [2D] (row-major, rows = outputs).  All calls are
+ * asynchronous on `stream` (a cudaStream_t, NULL = default stream).       */
+#define QEM_MLP_DIM 18
+#define QEM_MLP_HIDDEN 128
+#define QEM_MLP_PARAMS 26020
+
+/* Features of n users: x DEVICE float [n][n_obs][dim], y DEVICE float
+ * [n][n_obs] -> feats DEVICE float [n][2 dim + 1].  dim must be QEM_MLP_DIM
+ * (QEM_ERR_UNSUPPORTED otherwise).                                           */
+qem_status qem_mlp_features(const float* x, const float* y, int64_t n, int n_obs, int dim, float* feats,
+                            void* stream);
+
+/* Network output of n users: feats DEVICE float [n][2D+1] -> out DEVICE
+ * float [n][2D] (means, then log scales).                                    */
+qem_status qem_mlp_forward(const float* params, const float* feats, int64_t n, float* out, void* stream);
+
+/* Bytes of the caller-owned workspace qem_mlp_backward needs for n users
+ * (per-block partial gradients).                                             */
+qem_status qem_mlp_workspace_size(int64_t n, size_t* bytes);
+
+/* Loss and gradient of a batch of n >= 1 users: target DEVICE float
+ * [n][2][D] (the users' QEM proposal: means, then scales > 0, the plan's
+ * q_params layout) -> grad DEVICE float [QEM_MLP_PARAMS], loss DEVICE double
+ * [1] (nullable).  Deterministic: blocks' partial sums are added in order. */
+qem_status qem_mlp_backward(const float* params, const float* feats, const float* target, int64_t n, float* grad,
+                            double* loss, void* workspace, void* stream);
+
+/* One Adam step t >= 1 (Kingma & Ba 2015) on params with FP32 moment
+ * estimates m, v (DEVICE float [QEM_MLP_PARAMS] each, zero before t = 1). */
+qem_status qem_mlp_step(float* params, const float* grad, float* m, float* v, int64_t t, double lr, double beta1,
+                        double beta2, double eps, void* stream);
+
+/* Proposal parameters from the network output: out DEVICE float [n][2D] ->
+ * q_params DEVICE float [n][2][D] (means; scales = exp of the log scales,
+ * clamped to [-12, 6]), ready to be copied into a plan's q_params.          */
+qem_status qem_mlp_to_q(const float* out, int64_t n, float* q_params, void* stream);
+
 /* Kernels of the plan's qem_run graph (tracing support; valid after a
  * qem_run call): per_iteration = kernel launches of one iteration inside the
  * device loop (the E-step, the M-step and the loop control), per_call = the

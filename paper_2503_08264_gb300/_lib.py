@@ -18,6 +18,7 @@ QEM_GAMMA_TRIES = 8
 QEM_OK, QEM_ERR_INVALID_ARG, QEM_ERR_UNSUPPORTED, QEM_ERR_OOM, QEM_ERR_CUDA, QEM_ERR_NUMERIC, QEM_ERR_TIMEOUT = range(7)
 QEM_PREC_FP32, QEM_PREC_BF16, QEM_PREC_BF16X3 = 0, 1, 2
 QEM_TILE_AUTO, QEM_TUNE_FORCE = -1, 1
+QEM_MLP_DIM, QEM_MLP_HIDDEN, QEM_MLP_PARAMS = 18, 128, 26020
 
 
 class LevelDesc(C.Structure):
@@ -63,6 +64,14 @@ SIGNATURES = {
     "qem_run_kernels": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "qem_tune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "qem_tune_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "qem_mlp_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "qem_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "qem_mlp_workspace_size": (C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
+    "qem_mlp_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p]),
+    "qem_mlp_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
+                               C.c_double, C.c_double, C.c_double, C.c_void_p]),
+    "qem_mlp_to_q": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "qem_estep_single_noalloc": (C.c_int, [C.POINTER(LevelDesc), C.c_int, C.c_void_p, C.c_void_p, C.c_uint64,
                                            C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
 }

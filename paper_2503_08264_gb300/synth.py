@@ -131,6 +131,32 @@ def hier_logistic(M: int = 300, N: int = 5, D: int = 18, seed: int = 0, p_feat: 
                  truth={"mu": mu, "psi": psi, "z": z})
 
 
+def hier_logistic_batch(n_inst: int, M: int = 300, N: int = 5, D: int = 18, seed: int = 0,
+                        p_feat: float = 0.3) -> Model:
+    """n_inst independent hierarchical logistic instances in one model (instance
+    i is hier_logistic(M, N, D, seed + i); roots are the instances)."""
+    parts = [hier_logistic(M=M, N=N, D=D, seed=seed + i, p_feat=p_feat) for i in range(n_inst)]
+    root = Level(n=n_inst, dim=2 * D, prior=PRIOR_STD_NORMAL, prior_a=1.0)
+    users = Level(n=n_inst * M, dim=D, prior=PRIOR_NORMAL_MEAN_LOGVAR, lik=LIK_BERNOULLI_LOGIT, n_obs=N,
+                  parent=np.repeat(np.arange(n_inst, dtype=np.int64), M),
+                  x=np.concatenate([p.levels[1].x for p in parts]), y=np.concatenate([p.levels[1].y for p in parts]))
+    return Model([root, users], name=f"hier_logistic_batch{n_inst}_M{M}_N{N}")
+
+
+def mlp_init(seed: int, sizes=(37, 128, 128, 36), out_scale: float = 0.1) -> np.ndarray:
+    """Initial warm-start network parameters (flat layout W1, b1, W2, b2, W3,
+    b3): He-normal weights (std sqrt(2 / fan_in)), the output layer scaled by
+    out_scale, zero biases."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for j, (i, o) in enumerate(zip(sizes[:-1], sizes[1:])):
+        W = rng.standard_normal((o, i)) * np.sqrt(2.0 / i)
+        if j == len(sizes) - 2:
+            W *= out_scale
+        out += [W.reshape(-1), np.zeros(o)]
+    return np.concatenate(out).astype(np.float32)
+
+
 def batched_three_level(n_inst: int = 256, D: int = 8, seed: int = 0,
                         groups=(5, 40), units=(10, 200), n_obs: int = 4,
                         unit_var: float = 0.25) -> Model:
