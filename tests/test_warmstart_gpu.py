@@ -1,0 +1,71 @@
+"""GPU tests of the learned warm start and the time-to-tolerance study.
+
+* The study's reference, the plateau of log P_MP under plain FP32 QEM on
+  the GPU, agrees with the same procedure run by the FP64 oracle on the same
+  counter-based noise, well inside the study's tolerance.
+* A network trained on QEM's own proposals of seeded instances brings new
+  instances to their log P_MP plateau in fewer iterations than the cold start
+  (what the trained network gains over the method without it), and the
+  plateaus it reaches are no lower.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2503_08264_gb300 import synth as S
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2503_08264_gb300 import build
+    build.build()
+    O.build()
+
+
+def test_gpu_plateau_matches_oracle_plateau():
+    from paper_2503_08264_gb300 import qem
+    model = S.hier_logistic(M=bench.TOL_M, N=bench.TOL_N, seed=bench.TEST_SEED + 100)
+    T, K, seed = 120, bench.TOL_K, 4242
+    plan = qem.Plan(model, K, precision="fp32")
+    gpu = float(bench.reference_plateau(plan, plan.flat(S.initial_q(model)), T=T, seed=seed)[0])
+    plan.close()
+    q = [x.astype(np.float64) for x in S.initial_q(model)]
+    m = [np.stack([x[:, 0], x[:, 0] ** 2 + x[:, 1] ** 2], 1) for x in q]
+    lps = []
+    for t in range(1, T + 1):
+        r = O.estep(model, q, K, seed=seed, it=t)
+        lps.append(r["log_pmp"][0])
+        m = [O.ema(m[l], r["mom"][l], bench.TOL_LAMBDA) for l in range(2)]
+        q = [O.mstep(O.Q_GAUSS, x) for x in m]
+    ref = float(np.mean(lps[T // 2:]))
+    print("plateau: GPU FP32", gpu, "oracle FP64", ref)
+    assert abs(gpu - ref) < 0.5 * bench.TOL_DELTA
+
+
+def test_warm_start_reaches_plateau_in_fewer_iterations():
+    from paper_2503_08264_gb300 import qem
+    net, secs, losses = bench.train_warm_start(300, epochs=6, batch=2048)
+    print("training", round(secs, 1), "s, losses", [round(x, 3) for x in losses])
+    assert losses[-1] < losses[0]
+    n_test = 4
+    batch = S.hier_logistic_batch(n_test, M=bench.TOL_M, N=bench.TOL_N, seed=bench.TEST_SEED)
+    plan = qem.Plan(batch, bench.TOL_K, precision="bf16x3")
+    cold, pl_cold = bench.iterations_to_tol(plan, plan.flat(S.initial_q(batch)))
+    warm, pl_warm = bench.iterations_to_tol(plan, bench.warm_q0(plan, net))
+    print("iterations to the plateau: cold", cold, "warm", warm)
+    print("plateaus: cold", [round(x, 1) for x in pl_cold], "warm", [round(x, 1) for x in pl_warm])
+    assert sum(warm) < sum(cold)
+    # the warm start changes where QEM starts, not where it ends: its plateaus
+    # are no lower than the cold start's (within the stream-to-stream spread)
+    assert np.mean(np.array(pl_warm) - np.array(pl_cold)) > -bench.TOL_DELTA
+    plan.close()
