@@ -39,6 +39,7 @@ UNIT = "pairs/s"
 
 # workload name -> (builder(seed), K, default precision)
 WORKLOADS = {
+    "conjugate_gaussian_M8_N16_K16": (lambda seed: S.conjugate_gaussian(M=8, N=16, seed=seed), 16, "fp32"),
     "hier_logistic_M5000_N10_K1024": (lambda seed: S.hier_logistic(M=5000, N=10, seed=seed), 1024, "bf16x3"),
     "hier_logistic_M300_N5_K128": (lambda seed: S.hier_logistic(M=300, N=5, seed=seed), 128, "fp32"),
     # profiling case: the large workload's shapes with a fifth of its plate (fits an ncu capture)
@@ -167,6 +168,33 @@ def measured_peaks():
 # launch): FP32 CUDA-core path = FP32 pipe (128 lanes/clk/SM), tensor-core
 # path = MUFU ex2 (1 exponential per pair; 32 per clk per SM on GB300).
 SMS = 152
+
+
+# DRAM bytes per launch of a dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), with the git blob hash of the
+# kernel's source file at capture time: reported only while that file is
+# unchanged (the summary under profiles/ gives the capture command).
+NCU_TRAFFIC = {
+    ("forward", "hier_logistic_M5000_N10_K1024", "bf16x3"): {
+        "bytes": 820.340480e6 + 22.491648e6, "source": "paper_2503_08264_gb300/csrc/qem_tc.cu",
+        "blob": "c10a6701806278c7d2fe2c508cff6eb248d23f4e",
+        "profile": "profiles/contract_forward_bf16x3_hier_logistic_M5000_K1024.md"},
+}
+
+
+def git_blob_hash(path: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, path), "rb") as f:
+        data = f.read()
+    return hashlib.sha1(b"blob %d\0" % len(data) + data).hexdigest()
+
+
+def ncu_traffic(kind: str, workload: str, precision: str):
+    e = NCU_TRAFFIC.get((kind, workload, precision))
+    try:
+        return e["bytes"] if e and git_blob_hash(e["source"]) == e["blob"] else None
+    except OSError:
+        return None
 
 
 def roofline_for(kind: str, precision: str, D: int, pairs: float, ms: float, sm_max_mhz: float):
@@ -516,6 +544,9 @@ def run_ours(args):
     pairs_per_launch = pairs / max(1, (len(model.levels) - 1))
     if kind in ("forward", "adjoint"):
         roof = roofline_for(kind, precision, D_child, pairs_per_launch * k_n, k_ms, sm_max)
+        roof["traffic"] = ncu_traffic(kind, args.workload, precision)
+        if roof["traffic"] is not None:
+            roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
     else:
         roof = {"bound": "hbm", "kernel": kind, "achieved": None, "peak": measured_peaks().get("hbm_gbs"),
                 "unit": "GB/s", "frac": None, "traffic": None}

@@ -562,7 +562,7 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
   }
   if (ce == cudaSuccess && P->count_tab) ce = launch_count_table(P->count_tab, P->stream);
   size_t smem = 0;
-  for (int l = 0; l < L; ++l) smem = std::max(smem, sample_local_smem(P->lv[l], kSampleThreadsLimit));
+  for (int l = 0; l < L; ++l) smem = std::max(smem, sample_local_smem(P->lv[l], K, kSampleThreadsLimit));
   if (ce == cudaSuccess) ce = configure_sample_local(smem);
   for (int l = 1; l < L && ce == cudaSuccess; ++l) ce = configure_adj_small(P->lv[l].D, K);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->stream);

@@ -121,6 +121,47 @@ struct qem_plan_s {
 namespace qem {
 
 // ---------------------------------------------------------------------------
+// Block-wide copy of n consecutive floats (sample rows of width D) from global
+// memory into shared rows of stride D + 1: 16-byte loads when the source is
+// aligned, four of them in flight per thread before their stores (the copies
+// are latency-bound otherwise: one load at a time per thread).
+template <int DC>  // DC > 0: the width known at compile time; 0: D at run time
+__device__ __forceinline__ void stage_rows(const float* __restrict__ src, int n, int Drt, float* dst) {
+  const int D = DC > 0 ? DC : Drt;
+  const int ZS = D + 1;
+  const int nth = blockDim.x;
+  int head = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const int n4 = n >> 2;
+    for (int i0 = threadIdx.x; i0 < n4; i0 += 4 * nth) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u * nth < n4) v[u] = s4[i0 + u * nth];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = i0 + u * nth;
+        if (idx < n4) {
+          const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+          int r = (4 * idx) / D, c = (4 * idx) % D;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            dst[r * ZS + c] = vv[j];
+            if (++c == D) {
+              c = 0;
+              ++r;
+            }
+          }
+        }
+      }
+    }
+    head = n4 << 2;
+  }
+  for (int i = head + threadIdx.x; i < n; i += nth) dst[(i / D) * ZS + (i % D)] = src[i];
+}
+
+// ---------------------------------------------------------------------------
 // Counter-based noise: Philox4x32-10 (Salmon et al., SC'11) with the counter
 // layout key = seed, ctr = (sample lo, sample hi, level<<24 | idx/4, iter).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
@@ -228,7 +269,7 @@ cudaError_t configure_adj_small(int D, int K);
 cudaError_t launch_moments(const LevelView& v, int K, int threads, double* mom, cudaStream_t s);
 cudaError_t launch_mstep(const LevelView& v, const double* mom, double* m, float* q, double lambda,
                          double sched_p, double var_floor, long long t_host, const Ctl* ctl, cudaStream_t s);
-size_t sample_local_smem(const LevelView& v, int threads);
+size_t sample_local_smem(const LevelView& v, int K, int threads);
 constexpr int kSampleThreadsLimit = 256;   // largest sampler block the tuner tries
 cudaError_t configure_sample_local(size_t smem);
 cudaError_t launch_mean_params(const LevelView& v, const float* q, double* m, cudaStream_t s);

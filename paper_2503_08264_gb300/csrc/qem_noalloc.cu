@@ -109,7 +109,7 @@ extern "C" qem_status qem_estep_single_noalloc(const qem_level_desc* level, int 
   if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) return QEM_ERR_CUDA;
   if (launch_set_ctl(ctl, seed, iter, 1, -1, s) != cudaSuccess) return QEM_ERR_CUDA;
   const Tune dflt;
-  if (configure_sample_local(sample_local_smem(v, dflt.sample_threads)) != cudaSuccess) return QEM_ERR_CUDA;
+  if (configure_sample_local(sample_local_smem(v, K, dflt.sample_threads)) != cudaSuccess) return QEM_ERR_CUDA;
   if (tab && launch_count_table(tab, s) != cudaSuccess) return QEM_ERR_CUDA;
   if (launch_sample_local(v, K, dflt.sample_threads, q_params, eps, ctl, s) != cudaSuccess) return QEM_ERR_CUDA;
   if (launch_elem_const(v, q_params, s) != cudaSuccess) return QEM_ERR_CUDA;

@@ -96,12 +96,17 @@ __device__ double gamma_variate(double a, const NoiseSrc& ns, int base) {
 // (Alg. 1 "z ~ Q_t"; the P(x|z)/Q(z) part of r_k in Eq. rmp):
 //   loc[e][k] = sum_n log p(y_en | z_e^k, x_en) - log q(z_e^k) (+ log p(z) at level 0),
 // split into a sample-dependent FP32 part (loc, centred on its maximum) and a
-// sample-independent FP64 part (cst, written by k_elem_const).  One block per
-// element; covariates in shared memory (rows padded to a multiple of 4 for
-// 16-byte loads); each thread keeps its sample in registers; samples are
-// staged through shared memory for coalesced stores.  No FP64 arithmetic
-// runs per element here: a block has one element, and single-lane FP64 work
-// (GB300's FP64 rate is a small fraction of FP32) dominated it.
+// sample-independent FP64 part (cst, written by k_elem_const).  Leaf levels:
+// one block per element, loc staged in shared memory and centred on its
+// maximum before it is written (the contraction reads it in FP32 / BF16).
+// Levels with children: their local factor is re-centred in FP64 by
+// k_finalize (and the root's is summed in FP64), so no centring is needed and
+// the K samples of an element are spread over several blocks (grid.y).
+// Covariates in shared memory (rows padded to a multiple of 4 for 16-byte
+// loads); each thread keeps its sample in registers; samples are staged
+// through shared memory for coalesced stores.  No FP64 arithmetic runs per
+// element here: single-lane FP64 work (GB300's FP64 rate is a small fraction
+// of FP32) dominated the kernel.
 constexpr int kSampleThreadsMax = 256;
 
 // Poisson-log reference point of a count: s0 = log max(y, 1) and e^s0, both
@@ -177,7 +182,8 @@ cudaError_t launch_elem_const(const LevelView& v, const float* q, cudaStream_t s
 __device__ __forceinline__ float softplusf(float s) { return fmaxf(s, 0.f) + log1pf(__expf(-fabsf(s))); }
 
 template <int MAXD>
-__global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v, int K, const float* __restrict__ q,
+__global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v, int K, int kchunk,
+                                                                  const float* __restrict__ q,
                                                                   const float* __restrict__ eps, const Ctl* ctl) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float fred[kSampleThreadsMax / 32];
@@ -189,6 +195,8 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
   float* ey0s = s0s + nobs;             // [nobs] exp(s0)
   float* qs = ey0s + nobs;              // [2][D]
   float* zs = qs + 2 * D;               // [blockDim][D+1]
+  const bool centre = kchunk >= K;      // one block holds all K samples of the element
+  float* ls = zs + blockDim.x * zs_stride;  // [K] loc before centring (centre only)
   for (int i = threadIdx.x; i < nobs * Dp; i += blockDim.x) {
     const int n = i / Dp, d = i % Dp;
     xs[i] = d < D ? v.x[(e * nobs + n) * D + d] : 0.f;
@@ -205,9 +213,10 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
   const unsigned long long seed = ctl->seed, iter = ctl->iter;
   const float4* xs4 = reinterpret_cast<const float4*>(xs);
   float lmax = -INFINITY;
+  const int kbeg = blockIdx.y * kchunk, kend = min(K, kbeg + kchunk);
 
-  for (int k0 = 0; k0 < K; k0 += blockDim.x) {
-    const int nk = min((int)blockDim.x, K - k0);
+  for (int k0 = kbeg; k0 < kend; k0 += blockDim.x) {
+    const int nk = min((int)blockDim.x, kend - k0);
     const int k = k0 + threadIdx.x;
     const bool act = threadIdx.x < nk;
     float z[MAXD];
@@ -319,7 +328,10 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
         }
       }
       const float lv = ll - lq + lp;
-      v.loc[e * K + k] = lv;
+      if (centre)
+        ls[k] = lv;
+      else
+        v.loc[e * K + k] = lv;
       lmax = fmaxf(lmax, lv);
       float* zr = zs + threadIdx.x * zs_stride;
 #pragma unroll
@@ -327,10 +339,27 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
         if (d < D) zr[d] = z[d];
     }
     __syncthreads();
-    // coalesced store of the block's samples
+    // coalesced store of the block's samples (row and column of element i
+    // advanced incrementally: no division per element)
     float* dst = v.z + (e * K + k0) * (long long)D;
-    for (int i = threadIdx.x; i < nk * D; i += blockDim.x) dst[i] = zs[(i / D) * zs_stride + (i % D)];
+    {
+      const int step_r = blockDim.x / D, step_c = blockDim.x % D;
+      int r = threadIdx.x / D, c = threadIdx.x % D;
+      for (int i = threadIdx.x; i < nk * D; i += blockDim.x) {
+        dst[i] = zs[r * zs_stride + c];
+        r += step_r;
+        c += step_c;
+        if (c >= D) {
+          c -= D;
+          ++r;
+        }
+      }
+    }
     __syncthreads();
+  }
+  if (!centre) {
+    if (blockIdx.y == 0 && threadIdx.x == 0) v.cshift[e] = 0.f;
+    return;
   }
   // Centre the element's sample-dependent factor on its maximum (the offset
   // joins the FP64 constant), so every later FP32 step works near zero for
@@ -342,13 +371,13 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
   float cmax = -INFINITY;
   for (int j = 0; j < (int)(blockDim.x >> 5); ++j) cmax = fmaxf(cmax, fred[j]);
   if (!isfinite(cmax)) cmax = 0.f;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) v.loc[e * K + k] -= cmax;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) v.loc[e * K + k] = ls[k] - cmax;
   if (threadIdx.x == 0) v.cshift[e] = cmax;
 }
 
-size_t sample_local_smem(const LevelView& v, int threads) {
+size_t sample_local_smem(const LevelView& v, int K, int threads) {
   const int Dp = (v.D + 3) & ~3;
-  return sizeof(float) * (size_t)(v.n_obs * Dp + 3 * v.n_obs + 2 * v.D + threads * (v.D + 1)) + 16;
+  return sizeof(float) * (size_t)(v.n_obs * Dp + 3 * v.n_obs + 2 * v.D + threads * (v.D + 1) + K) + 16;
 }
 
 template <int MAXD>
@@ -371,15 +400,17 @@ cudaError_t launch_sample_local(const LevelView& v, int K, int threads, const fl
                                 cudaStream_t s) {
   if (v.n == 0) return cudaSuccess;
   if (threads < 32 || threads > kSampleThreadsMax || threads % 32) return cudaErrorInvalidValue;
-  const size_t smem = sample_local_smem(v, threads);
-  const unsigned grid = (unsigned)v.n;
+  const size_t smem = sample_local_smem(v, K, threads);
+  // leaves: one block per element (centred); inner levels: K split over blocks
+  const int kchunk = v.Dc == 0 ? K : threads;
+  const dim3 grid((unsigned)v.n, (unsigned)((K + kchunk - 1) / kchunk));
   const int Dp = (v.D + 3) & ~3;
-  if (Dp <= 4) k_sample_local<4><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
-  else if (Dp <= 8) k_sample_local<8><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
-  else if (Dp <= 12) k_sample_local<12><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
-  else if (Dp <= 20) k_sample_local<20><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
-  else if (Dp <= 40) k_sample_local<40><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
-  else k_sample_local<64><<<grid, threads, smem, s>>>(v, K, q, eps, ctl);
+  if (Dp <= 4) k_sample_local<4><<<grid, threads, smem, s>>>(v, K, kchunk, q, eps, ctl);
+  else if (Dp <= 8) k_sample_local<8><<<grid, threads, smem, s>>>(v, K, kchunk, q, eps, ctl);
+  else if (Dp <= 12) k_sample_local<12><<<grid, threads, smem, s>>>(v, K, kchunk, q, eps, ctl);
+  else if (Dp <= 20) k_sample_local<20><<<grid, threads, smem, s>>>(v, K, kchunk, q, eps, ctl);
+  else if (Dp <= 40) k_sample_local<40><<<grid, threads, smem, s>>>(v, K, kchunk, q, eps, ctl);
+  else k_sample_local<64><<<grid, threads, smem, s>>>(v, K, kchunk, q, eps, ctl);
   return cudaGetLastError();
 }
 
@@ -636,8 +667,7 @@ cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* lo
 // (coalesced global reads; conflict-free row reads for odd strides).
 __device__ __forceinline__ void stage_samples(const LevelView& v, long long e, int K, int k0, int nk, float* zc) {
   const int D = v.D;
-  const float* src = v.z + (e * K + k0) * (long long)D;
-  for (int i = threadIdx.x; i < nk * D; i += blockDim.x) zc[(i / D) * (D + 1) + (i % D)] = src[i];
+  stage_rows<0>(v.z + (e * K + k0) * (long long)D, nk * D, D, zc);
 }
 
 // Compaction of the parent samples that carry weight: kept = w_p[kp] >
@@ -941,7 +971,34 @@ __global__ void k_moments(LevelView v, int K, double* mom) {
   float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
   if (t < per * D) {
     const int d = t % D;
-    for (int k = t / D; k < K; k += per) {
+    int k = t / D;
+    // four samples' loads in flight before their accumulation (the Kahan
+    // chain would otherwise wait for every load in turn)
+    for (; k + 3 * per < K; k += 4 * per) {
+      float wk[4], zv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        wk[u] = v.w[e * K + k + u * per];
+        zv[u] = v.z[(e * K + k + u * per) * D + d];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float t0, t1;
+        if (v.qfam == QEM_Q_GAUSS) {
+          t0 = zv[u];
+          t1 = zv[u] * zv[u];
+        } else if (v.qfam == QEM_Q_GAMMA) {
+          t0 = zv[u];
+          t1 = logf(zv[u]);
+        } else {
+          t0 = logf(zv[u]);
+          t1 = log1pf(-zv[u]);
+        }
+        kahan_add(s0, c0, wk[u] * t0);
+        kahan_add(s1, c1, wk[u] * t1);
+      }
+    }
+    for (; k < K; k += per) {
       const float wk = v.w[e * K + k];
       const float zv = v.z[(e * K + k) * D + d];
       float t0, t1;

@@ -368,8 +368,7 @@ __global__ void __launch_bounds__(128) k_child_features(LevelView ch, int mean_l
   for (int k0 = 0; k0 < K; k0 += blockDim.x) {
     const int nk = min((int)blockDim.x, K - k0);
     __syncthreads();
-    const float* src = ch.z + (e * K + k0) * (long long)D;
-    for (int i = threadIdx.x; i < nk * D; i += blockDim.x) zc[(i / D) * zst + (i % D)] = src[i];
+    stage_rows<0>(ch.z + (e * K + k0) * (long long)D, nk * D, D, zc);
     __syncthreads();
     if ((int)threadIdx.x < nk) {
       const int r = threadIdx.x;
@@ -442,8 +441,7 @@ __global__ void __launch_bounds__(128) k_child_features_t(LevelView ch, float pp
   for (int k0 = 0; k0 < K; k0 += 128) {
     const int nk = min(128, K - k0);
     __syncthreads();
-    const float* src = ch.z + (e * K + k0) * (long long)D;
-    for (int i = threadIdx.x; i < nk * D; i += blockDim.x) zc[(i / D) * ZS + (i % D)] = src[i];
+    stage_rows<D>(ch.z + (e * K + k0) * (long long)D, nk * D, D, zc);
     __syncthreads();
     if ((int)threadIdx.x >= nk) continue;
     const int r = threadIdx.x;
