@@ -185,13 +185,34 @@ __device__ __forceinline__ float neg2_log_unit(uint32_t x) {
 
 __device__ __forceinline__ float unit_of(uint32_t x) { return ((float)x + 0.5f) * 2.3283064365386963e-10f; }
 
-// -2 log u for the Box-Muller radius: the fast logarithm where its relative
-// error is small (u < 1/2), the accurate log1p of -(1-u) near u = 1.
+// log(1 + t) for t in [-1/2, 1] without a library call or a branch:
+// log(1 + t) = 2 atanh(s), s = t / (2 + t) in [-1/3, 1/3], and the odd series
+// of atanh to s^15 (truncation below 1e-8 relative); relative error a few
+// units of FP32 rounding, for every t in the range including tiny |t|.
+__device__ __forceinline__ float log1p_small(float t) {
+  const float s = __fdividef(t, 2.f + t), s2 = s * s;
+  float p = 1.f / 15.f;
+  p = fmaf(p, s2, 1.f / 13.f);
+  p = fmaf(p, s2, 1.f / 11.f);
+  p = fmaf(p, s2, 1.f / 9.f);
+  p = fmaf(p, s2, 1.f / 7.f);
+  p = fmaf(p, s2, 1.f / 5.f);
+  p = fmaf(p, s2, 1.f / 3.f);
+  p = fmaf(p, s2, 1.f);
+  return 2.f * s * p;
+}
+
+// -2 log u for the Box-Muller radius: the fast logarithm for u < 1/2 (small
+// relative error there), log1p of -(1-u) near u = 1 (1-u carries the low
+// bits of the uniform).
 __device__ __forceinline__ float neg2_log_unit_fast(uint32_t x) {
   if (x < 0x80000000u) return -2.f * __logf(((float)x + 0.5f) * 2.3283064365386963e-10f);
   const float one_minus_u = ((float)(0xFFFFFFFFu - x) + 0.5f) * 2.3283064365386963e-10f;
-  return -2.f * log1pf(-one_minus_u);
+  return -2.f * log1p_small(-one_minus_u);
 }
+
+// sqrt(r) for r > 0 from the fast reciprocal square root.
+__device__ __forceinline__ float sqrt_pos_fast(float r) { return r * rsqrtf(r); }
 
 // Four N(0,1) numbers of block `blk` of one sample (Box-Muller on (u0,u1), (u2,u3)).
 // The angle 2 pi u is evaluated as pi + (2 pi u - pi) with the fast sine and
@@ -207,7 +228,7 @@ __device__ __forceinline__ float4 normal4(unsigned long long seed, unsigned long
   float s0, c0, s1, c1;
   __sincosf(t0, &s0, &c0);
   __sincosf(t1, &s1, &c1);
-  const float r0 = sqrtf(neg2_log_unit_fast(r.x)), r1 = sqrtf(neg2_log_unit_fast(r.z));
+  const float r0 = sqrt_pos_fast(neg2_log_unit_fast(r.x)), r1 = sqrt_pos_fast(neg2_log_unit_fast(r.z));
   return make_float4(-r0 * c0, -r0 * s0, -r1 * c1, -r1 * s1);
 }
 

@@ -179,7 +179,7 @@ cudaError_t launch_elem_const(const LevelView& v, const float* q, cudaStream_t s
   return cudaGetLastError();
 }
 
-__device__ __forceinline__ float softplusf(float s) { return fmaxf(s, 0.f) + log1pf(__expf(-fabsf(s))); }
+__device__ __forceinline__ float softplusf(float s) { return fmaxf(s, 0.f) + log1p_small(__expf(-fabsf(s))); }
 
 template <int MAXD>
 __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v, int K, int kchunk,
