@@ -791,21 +791,23 @@ __global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView
 // Small-set adjoint with its own normaliser (used when the forward ran at a
 // different precision): one block per element; for each of the <= kSmallKept
 // kept parent samples the log-factor of every child sample is evaluated once
-// in FP32 (kept in shared memory), its row normaliser log sum_k exp S[kp][k]
-// is reduced over the block, and the marginal weights follow, so every row of
-// P(k | kp) sums to one in the arithmetic that evaluates it.  Elements whose
-// parent keeps more samples are left to the tensor-core adjoint.
+// in FP32 (log2 units, kept in shared memory), its row normaliser
+// log sum_k exp S[kp][k] is reduced over the block (maximum, then the sum of
+// 2^(a - max)), and the marginal weights follow, so every row of P(k | kp)
+// sums to one in the arithmetic that evaluates it.  Elements whose parent
+// keeps more samples are left to the tensor-core adjoint.
 template <int MAXD>
 __global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, int K) {
   extern __shared__ float dyn[];
   float* zc = dyn;                          // [256][D+1] staged samples
-  float* av = zc + 256 * (v.D + 1);         // [kSmallKept][K] log-factors (nats)
+  float* av = zc + 256 * (v.D + 1);         // [kSmallKept][K] log-factors (log2 units)
   __shared__ float pms[kSmallKept * MAXD];
   __shared__ float pps[kSmallKept * MAXD];
   __shared__ float pcs[kSmallKept];
-  __shared__ float red_m[kSmallKept][8];
-  __shared__ float red_s[kSmallKept][8];
+  __shared__ float red[kSmallKept][8];
+  __shared__ float colmax[kSmallKept];
   __shared__ float shift[kSmallKept];
+  constexpr float kL2e = 1.4426950408889634f;
   const long long e = blockIdx.x;
   const int D = v.D;
   const long long p = v.parent[e];
@@ -816,18 +818,20 @@ __global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, i
     const bool ok = j < n_eff && d < D;
     const int kp = ok ? par.cidx[p * K + j] : 0;
     pms[i] = ok ? par.pm[(p * K + kp) * D + d] : 0.f;
-    pps[i] = ok ? par.pp[(p * K + kp) * D + d] : 0.f;
+    pps[i] = ok ? kL2e * par.pp[(p * K + kp) * D + d] : 0.f;
   }
   if (threadIdx.x < kSmallKept) {
     const int j = threadIdx.x;
-    pcs[j] = j < n_eff ? par.pc[p * K + par.cidx[p * K + j]] : 0.f;
+    pcs[j] = j < n_eff ? kL2e * par.pc[p * K + par.cidx[p * K + j]] : 0.f;
   }
-  float m[kSmallKept], sm[kSmallKept];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // pass 1: the log-factors of the kept parent samples (log2 units) from
+  // samples staged through shared memory, with each thread's running maximum
+  // per parent sample
+  float mx[kSmallKept];
 #pragma unroll
-  for (int j = 0; j < kSmallKept; ++j) {
-    m[j] = -INFINITY;
-    sm[j] = 0.f;
-  }
+  for (int j = 0; j < kSmallKept; ++j) mx[j] = -INFINITY;
   for (int k0 = 0; k0 < K; k0 += blockDim.x) {
     const int nk = min((int)blockDim.x, K - k0);
     __syncthreads();
@@ -838,7 +842,7 @@ __global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, i
     float zr[MAXD];
 #pragma unroll
     for (int d = 0; d < MAXD; ++d) zr[d] = d < D ? zc[threadIdx.x * (D + 1) + d] : 0.f;
-    const float hk = v.htil[e * K + k];
+    const float hk = kL2e * v.htil[e * K + k];
 #pragma unroll
     for (int j = 0; j < kSmallKept; ++j) {
       if (j < n_eff) {
@@ -849,47 +853,53 @@ __global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, i
           a = fmaf(pps[j * MAXD + d], t * t, a);
         }
         av[j * K + k] = a;
-        if (a > m[j]) {
-          sm[j] = sm[j] * expf(m[j] - a) + 1.f;
-          m[j] = a;
-        } else {
-          sm[j] += expf(a - m[j]);
-        }
+        mx[j] = fmaxf(mx[j], a);
       }
     }
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < kSmallKept; ++j) {
-    float mj = m[j], sj = sm[j];
-    for (int o = 16; o; o >>= 1) {
-      const float mo = __shfl_xor_sync(0xffffffffu, mj, o), so = __shfl_xor_sync(0xffffffffu, sj, o);
-      const float M = fmaxf(mj, mo);
-      sj = (mj == -INFINITY ? 0.f : sj * expf(mj - M)) + (mo == -INFINITY ? 0.f : so * expf(mo - M));
-      mj = M;
-    }
-    if (lane == 0) {
-      red_m[j][warp] = mj;
-      red_s[j][warp] = sj;
-    }
+    float m = mx[j];
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[j][warp] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x < kSmallKept) {
+    float m = -INFINITY;
+    for (int w = 0; w < nw; ++w) m = fmaxf(m, red[threadIdx.x][w]);
+    colmax[threadIdx.x] = isfinite(m) ? m : 0.f;
+  }
+  __syncthreads();
+  // pass 2: row normalisers sum_k 2^(a - max) of each kept parent sample
+  float sm[kSmallKept];
+#pragma unroll
+  for (int j = 0; j < kSmallKept; ++j) sm[j] = 0.f;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < kSmallKept; ++j)
+      if (j < n_eff) sm[j] += exp2f(av[j * K + k] - colmax[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < kSmallKept; ++j) {
+    float t = sm[j];
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[j][warp] = t;
   }
   __syncthreads();
   if (threadIdx.x < kSmallKept) {
     const int j = threadIdx.x;
-    float M = -INFINITY;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmaxf(M, red_m[j][w]);
     float S = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-      if (red_m[j][w] > -INFINITY) S += red_s[j][w] * expf(red_m[j][w] - M);
-    // ln w_p - log sum_k exp S[kp][k]   (cw = ln w_p - ln K)
-    shift[j] = j < n_eff ? par.cw[p * K + j] + logf((float)K) - (M + logf(S)) : -INFINITY;
+    for (int w = 0; w < nw; ++w) S += red[j][w];
+    // log2 w_p - log2 sum_k 2^a[kp][k]   (cw = ln w_p - ln K)
+    shift[j] = j < n_eff ? kL2e * (par.cw[p * K + j] + logf((float)K)) - (colmax[j] + log2f(S)) : -INFINITY;
   }
   __syncthreads();
+  // pass 3: the marginal weights
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     float acc = 0.f;
 #pragma unroll
     for (int j = 0; j < kSmallKept; ++j)
-      if (j < n_eff) acc += expf(av[j * K + k] + shift[j]);
+      if (j < n_eff) acc += exp2f(av[j * K + k] + shift[j]);
     v.w[e * K + k] = acc;
   }
 }
