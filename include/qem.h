@@ -158,6 +158,28 @@ qem_status qem_sizes(const qem_plan_t plan, int64_t* q_len, int64_t* eps_len, in
 qem_status qem_estep(qem_plan_t plan, const float* q_params, const float* eps, uint64_t seed,
                      uint64_t iter, double* moments, double* log_pmp);
 
+/* log P_MP of q_params from a fresh draw of the samples (the noise stream
+ * keyed by (seed, iter), which the caller chooses distinct from the E-step's):
+ * the forward half of the E-step only (Eq. Prmp; no weights, no moments).
+ * The self-normalised estimate of qem_estep reuses the samples that its
+ * moments came from; an independent draw gives an unbiased estimate of P_MP
+ * for the given q, and with qem_moments_rescale the second-sample moment
+ * estimate of the remark after Theorem 1.  log_pmp: DEVICE
+ * double [n_inst] (nullable: the plan keeps the values for qem_log_pmp).
+ * Overwrites the plan's samples and local factors (qem_weights and
+ * qem_samples then describe no E-step).                                      */
+qem_status qem_log_pmp_fresh(qem_plan_t plan, const float* q_params, uint64_t seed, uint64_t iter,
+                             double* log_pmp);
+
+/* The moment estimate normalised by a second, distinct sample (the remark
+ * after Theorem 1): moments of every element of instance i multiplied by
+ * exp(log_pmp_same[i] - log_pmp_fresh[i]), where log_pmp_same is the E-step's
+ * own log P_MP (the self-normalising one) and log_pmp_fresh that of an
+ * independent draw (qem_log_pmp_fresh).  All DEVICE, double; moments
+ * [q_len] in/out; asynchronous on the plan's stream.                         */
+qem_status qem_moments_rescale(qem_plan_t plan, const double* log_pmp_same, const double* log_pmp_fresh,
+                               double* moments);
+
 /* M-step with EMA (Alg. 1 "m_t = lambda m_hat + (1-lambda) m_{t-1}" followed by
  * the next iteration's "Q = set_exp_family_params(m_t)"; Eq. ema; App. B).
  *   moments      DEVICE double [q_len]  this iteration's E-step estimate m_hat

@@ -155,9 +155,9 @@ inline RunGraph* run_of(qem_plan_t P) { return static_cast<RunGraph*>(P->run); }
     }                                                                      \
   } while (0)
 
-// The E-step body (Eq. mp_iw over the plate tree), enqueued on the plan's stream.
-qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* moments, double* user_lp,
-                      double* trace) {
+// Forward half of the E-step (sampling through log P_MP and the root
+// weights: Eq. Prmp over the plate tree), enqueued on the plan's stream.
+qem_status estep_forward(qem_plan_t P, const float* q, const float* eps, double* user_lp, double* trace) {
   cudaStream_t s = P->stream;
   const int L = P->L, K = P->K;
   for (int l = 0; l < L; ++l) {
@@ -179,6 +179,17 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
     QEM_LAUNCH(P, QEM_K_PLATE_SUM, launch_plate_sum(P->lv[l - 1], P->lv[l], K, s));
   }
   QEM_LAUNCH(P, QEM_K_ROOT, launch_root(P->lv[0], K, L > 1, P->log_pmp, user_lp, trace, P->ctl, s));
+  return QEM_OK;
+}
+
+// The E-step body (Eq. mp_iw over the plate tree): the forward half, then the
+// adjoint (marginal weights, Eq. mmp) and the moments.
+qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* moments, double* user_lp,
+                      double* trace) {
+  const qem_status st = estep_forward(P, q, eps, user_lp, trace);
+  if (st != QEM_OK) return st;
+  cudaStream_t s = P->stream;
+  const int L = P->L, K = P->K;
   for (int l = 1; l < L; ++l) {
     QEM_LAUNCH(P, QEM_K_OPERANDS, launch_compact(P->lv[l - 1], K, s));
     if (P->precision == QEM_PREC_FP32) {
@@ -624,6 +635,22 @@ qem_status qem_estep(qem_plan_t P, const float* q_params, const float* eps, uint
   if (ts != QEM_OK) return ts;
   QEM_TRY(launch_set_ctl(P->ctl, seed, iter, 1, -1, P->stream));
   return estep_body(P, q_params, eps, moments, log_pmp, nullptr);
+}
+
+qem_status qem_log_pmp_fresh(qem_plan_t P, const float* q_params, uint64_t seed, uint64_t iter, double* log_pmp) {
+  if (!P || !q_params) return QEM_ERR_INVALID_ARG;
+  const qem_status ts = maybe_autotune(P, q_params);
+  if (ts != QEM_OK) return ts;
+  QEM_TRY(launch_set_ctl(P->ctl, seed, iter, 1, -1, P->stream));
+  return estep_forward(P, q_params, nullptr, log_pmp, nullptr);
+}
+
+qem_status qem_moments_rescale(qem_plan_t P, const double* log_pmp_same, const double* log_pmp_fresh,
+                               double* moments) {
+  if (!P || !log_pmp_same || !log_pmp_fresh || !moments) return QEM_ERR_INVALID_ARG;
+  for (int l = 0; l < P->L; ++l)
+    QEM_TRY(launch_moments_rescale(P->lv, l, log_pmp_same, log_pmp_fresh, moments + P->q_off[l], P->stream));
+  return QEM_OK;
 }
 
 qem_status qem_mstep(qem_plan_t P, const double* moments, double* mean_params, float* q_params, double lambda,

@@ -294,5 +294,7 @@ size_t sample_local_smem(const LevelView& v, int K, int threads);
 constexpr int kSampleThreadsLimit = 256;   // largest sampler block the tuner tries
 cudaError_t configure_sample_local(size_t smem);
 cudaError_t launch_mean_params(const LevelView& v, const float* q, double* m, cudaStream_t s);
+cudaError_t launch_moments_rescale(const LevelView* lvs, int l, const double* lp_same, const double* lp_fresh,
+                                   double* mom, cudaStream_t s);
 
 }  // namespace qem

@@ -1182,4 +1182,30 @@ cudaError_t launch_mean_params(const LevelView& v, const float* q, double* m, cu
   return cudaGetLastError();
 }
 
+// Moments of level `lv` rescaled by exp(lp_same - lp_fresh) of their instance
+// (the root reached through the parent chain): the self-normalised estimate
+// times P_MP(z) / P_MP(z_new), i.e. the moment estimate normalised by a
+// second, distinct sample (the remark after Theorem 1).
+__global__ void k_moments_rescale(const long long* par1, const long long* par2, const long long* par3, int lv,
+                                  long long n, int D, const double* lp_same, const double* lp_fresh, double* mom) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n * 2 * D) return;
+  long long e = i / (2 * D);
+  if (lv >= 3) e = par3[e];
+  if (lv >= 2) e = par2[e];
+  if (lv >= 1) e = par1[e];
+  mom[i] *= exp(lp_same[e] - lp_fresh[e]);
+}
+
+cudaError_t launch_moments_rescale(const LevelView* lvs, int l, const double* lp_same, const double* lp_fresh,
+                                   double* mom, cudaStream_t s) {
+  const LevelView& v = lvs[l];
+  const long long tot = v.n * 2 * v.D;
+  if (tot == 0) return cudaSuccess;
+  k_moments_rescale<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      l >= 1 ? lvs[1].parent : nullptr, l >= 2 ? lvs[2].parent : nullptr, l >= 3 ? lvs[3].parent : nullptr, l,
+      v.n, v.D, lp_same, lp_fresh, mom);
+  return cudaGetLastError();
+}
+
 }  // namespace qem

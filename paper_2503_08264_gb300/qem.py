@@ -176,6 +176,18 @@ class Plan:
         qem_estep(self.h, q, eps, seed, it, moments, log_pmp)
         return moments, log_pmp
 
+    def log_pmp_fresh(self, q, seed: int, it: int, log_pmp=None):
+        """log P_MP of q from a fresh draw of the samples (device double [n_inst])."""
+        if log_pmp is None:
+            log_pmp = torch.empty(self.n_inst, dtype=torch.float64, device=self.device)
+        L.check(L.load().qem_log_pmp_fresh(self.h, _ptr(q), seed, it, _ptr(log_pmp)), "qem_log_pmp_fresh")
+        return log_pmp
+
+    def moments_rescale(self, log_pmp_same, log_pmp_fresh, moments):
+        L.check(L.load().qem_moments_rescale(self.h, _ptr(log_pmp_same), _ptr(log_pmp_fresh), _ptr(moments)),
+                "qem_moments_rescale")
+        return moments
+
     def mstep(self, moments, mean_params, q_params, lam: float, sched_p: float = 0.0, t: int = 1):
         qem_mstep(self.h, moments, mean_params, q_params, lam, sched_p, t)
 
