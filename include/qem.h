@@ -126,9 +126,14 @@ const char* qem_status_string(qem_status s);
 
 /* Build a plan: validate the model (parents non-decreasing and in range, prior
  * and dimension compatible with the parent level), copy its plate structure
- * to the device and allocate the workspace (the only allocation the library
- * makes; no later call allocates).  The model's x and y pointers are kept and
- * read by every E-step.  *out is set to NULL on failure.                    */
+ * to the device and allocate the workspace, the plan's only device-memory
+ * allocation: qem_estep, qem_mstep and qem_log_pmp_fresh allocate nothing
+ * (graph-capturable), except that a plan made with tile = QEM_TILE_AUTO tunes
+ * on its first call outside a capture; qem_run creates its graph (and, on the
+ * legacy stream, a private stream), qem_tune a scratch buffer, and the
+ * profiler its events.
+ * The model's x and y pointers are kept and read by every E-step.  *out is
+ * set to NULL on failure.                                                   */
 qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_plan_t* out);
 
 /* Release the plan and its workspace (synchronises the plan's stream). NULL is a no-op. */
