@@ -176,8 +176,8 @@ SMS = 152
 # unchanged (the summary under profiles/ gives the capture command).
 NCU_TRAFFIC = {
     ("forward", "hier_logistic_M5000_N10_K1024", "bf16x3"): {
-        "bytes": 820.340480e6 + 22.491648e6, "source": "paper_2503_08264_gb300/csrc/qem_tc.cu",
-        "blob": "c10a6701806278c7d2fe2c508cff6eb248d23f4e",
+        "bytes": 819584512 + 21048320, "source": "paper_2503_08264_gb300/csrc/qem_tc.cu",
+        "blob": "be44ead0ccfa511117e4b235f57e0baa52d67762",
         "profile": "profiles/contract_forward_bf16x3_hier_logistic_M5000_K1024.md"},
 }
 
