@@ -671,8 +671,9 @@ __device__ __forceinline__ void stage_samples(const LevelView& v, long long e, i
 }
 
 // Compaction of the parent samples that carry weight: kept = w_p[kp] >
-// 2^-60 max_kp w_p, in index order.  A dropped sample changes no marginal
-// weight by more than K 2^-60 relative.  cw = ln w_p - ln K of each kept
+// 2^-40 max_kp w_p, in index order.  The dropped samples change the marginal
+// weights by less than K 2^-40 in total (about 1e-9 at K = 1024, far below
+// FP32 rounding).  cw = ln w_p - ln K of each kept
 // sample; the list is padded to a multiple of 16 with cw = -inf.
 __global__ void k_compact(LevelView par, int K) {
   const long long p = blockIdx.x;
@@ -686,7 +687,7 @@ __global__ void k_compact(LevelView par, int K) {
   __syncthreads();
   float wmax = 0.f;
   for (int j = 0; j < (int)(blockDim.x >> 5); ++j) wmax = fmaxf(wmax, red[j]);
-  const float thr = wmax * 8.673617379884035e-19f;  // 2^-60
+  const float thr = wmax * 9.094947017729282e-13f;  // 2^-40
   const int per = (K + blockDim.x - 1) / blockDim.x;
   const int k0 = threadIdx.x * per, k1 = min(K, k0 + per);
   int cnt = 0;

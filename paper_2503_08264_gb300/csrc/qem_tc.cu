@@ -12,7 +12,7 @@
 //   forward : lt[e][kp] = rowc[kp] + ln 2 * log2 sum_k 2^(A B^T + h)[kp][k] - ln K   (online max shift)
 //   adjoint : w[e][k]   = sum_kp 2^(B A^T + h + d)[k][kp],  d = log2 e (rowc + ln w_p - lt - ln K)
 // The adjoint runs over the parent samples with non-negligible weight only
-// (compacted list; the dropped terms are below 2^-60 of the largest weight).
+// (compacted list; the dropped terms are below 2^-40 of the largest weight).
 //
 // Operand layout: the canonical K-major no-swizzle layout of tcgen05
 // (8 x 8 bf16 core matrices of 128 contiguous bytes, core matrices of a row
