@@ -185,6 +185,19 @@ qem_status qem_log_pmp_fresh(qem_plan_t plan, const float* q_params, uint64_t se
 qem_status qem_moments_rescale(qem_plan_t plan, const double* log_pmp_same, const double* log_pmp_fresh,
                                double* moments);
 
+/* Predictive log-likelihood of held-out observations of every element of
+ * `level` (the paper's diagnostic on held-out data), from the samples and
+ * marginal weights of the last E-step:
+ *   out[e] = log sum_k w_e[k] prod_n p(y_new[e][n] | z_e^k, x_new[e][n])
+ * with the level's likelihood.  x_new DEVICE float [n][n_obs_new][dim]
+ * (NULL allowed for the Poisson-rate and Bernoulli-probability likelihoods),
+ * y_new DEVICE float [n][n_obs_new], out DEVICE double [n]; asynchronous on
+ * the plan's stream.  QEM_ERR_INVALID_ARG for a level without likelihood,
+ * QEM_ERR_UNSUPPORTED when n_obs_new * (dim + 2) floats exceed 48 KB.  No
+ * counterpart of this entry point's exact form in the paper's code.         */
+qem_status qem_predictive(qem_plan_t plan, int level, const float* x_new, const float* y_new, int n_obs_new,
+                          double* out);
+
 /* M-step with EMA (Alg. 1 "m_t = lambda m_hat + (1-lambda) m_{t-1}" followed by
  * the next iteration's "Q = set_exp_family_params(m_t)"; Eq. ema; App. B).
  *   moments      DEVICE double [q_len]  this iteration's E-step estimate m_hat

@@ -168,3 +168,36 @@ def draw_noise_at(seed: int, it: int, level: int, idx, K: int, nps: int, qfam: i
 
 def max_threads() -> int:
     return lib().orc_max_threads()
+
+
+def predictive(z: np.ndarray, w: np.ndarray, lik: int, x_new, y_new, lik_var: float = 1.0) -> np.ndarray:
+    """Predictive log-likelihood of held-out data from weighted samples (FP64):
+
+        out[e] = log sum_k w[e, k] prod_n p(y_new[e, n] | z[e, k], x_new[e, n])
+
+    z [n, K, D], w [n, K] (each row summing to one), x_new [n, N, D] (unused by
+    the Poisson-rate and Bernoulli-probability likelihoods), y_new [n, N].
+    Densities from scipy (library routines independent of the C oracle).
+    """
+    from scipy import special, stats
+    z = np.asarray(z, np.float64)
+    w = np.asarray(w, np.float64)
+    y = np.asarray(y_new, np.float64)
+    if lik in (4, 5):                       # Poisson-rate, Bernoulli-probability: z is the parameter
+        zz = z[:, :, 0][:, :, None]
+        if lik == 4:
+            ll = stats.poisson.logpmf(y[:, None, :], zz).sum(-1)
+        else:
+            ll = (y[:, None, :] * np.log(zz) + (1 - y[:, None, :]) * np.log1p(-zz)).sum(-1)
+    else:
+        s = np.einsum("ekd,end->ekn", z, np.asarray(x_new, np.float64))
+        yy = y[:, None, :]
+        if lik == 1:                        # Gaussian
+            ll = stats.norm.logpdf(yy, s, np.sqrt(lik_var)).sum(-1)
+        elif lik == 2:                      # Bernoulli-logit
+            ll = (yy * special.log_expit(s) + (1 - yy) * special.log_expit(-s)).sum(-1)
+        elif lik == 3:                      # Poisson-log
+            ll = stats.poisson.logpmf(yy, np.exp(s)).sum(-1)
+        else:
+            raise ValueError("no likelihood")
+    return special.logsumexp(ll, b=w, axis=1)

@@ -645,6 +645,17 @@ qem_status qem_log_pmp_fresh(qem_plan_t P, const float* q_params, uint64_t seed,
   return estep_forward(P, q_params, nullptr, log_pmp, nullptr);
 }
 
+qem_status qem_predictive(qem_plan_t P, int level, const float* x_new, const float* y_new, int n_obs_new,
+                          double* out) {
+  if (!P || level < 0 || level >= P->L || n_obs_new < 1 || !y_new || !out) return QEM_ERR_INVALID_ARG;
+  const LevelView& v = P->lv[level];
+  if (v.lik == QEM_LIK_NONE) return QEM_ERR_INVALID_ARG;
+  if (!x_new && v.lik != QEM_LIK_POISSON_RATE && v.lik != QEM_LIK_BERNOULLI_PROB) return QEM_ERR_INVALID_ARG;
+  if (sizeof(float) * ((size_t)n_obs_new * v.D + 2 * (size_t)n_obs_new) > 48 * 1024) return QEM_ERR_UNSUPPORTED;
+  QEM_TRY(launch_predictive(v, P->K, x_new, y_new, n_obs_new, out, P->stream));
+  return QEM_OK;
+}
+
 qem_status qem_moments_rescale(qem_plan_t P, const double* log_pmp_same, const double* log_pmp_fresh,
                                double* moments) {
   if (!P || !log_pmp_same || !log_pmp_fresh || !moments) return QEM_ERR_INVALID_ARG;

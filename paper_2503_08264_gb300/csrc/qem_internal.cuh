@@ -296,5 +296,7 @@ cudaError_t configure_sample_local(size_t smem);
 cudaError_t launch_mean_params(const LevelView& v, const float* q, double* m, cudaStream_t s);
 cudaError_t launch_moments_rescale(const LevelView* lvs, int l, const double* lp_same, const double* lp_fresh,
                                    double* mom, cudaStream_t s);
+cudaError_t launch_predictive(const LevelView& v, int K, const float* xn, const float* yn, int nn, double* out,
+                              cudaStream_t s);
 
 }  // namespace qem

@@ -1209,4 +1209,98 @@ cudaError_t launch_moments_rescale(const LevelView* lvs, int l, const double* lp
   return cudaGetLastError();
 }
 
+// Predictive log-likelihood of held-out observations of each element from
+// the last E-step's samples and marginal weights (the paper's diagnostic of
+// held-out data):  out[e] = log sum_k w_e[k] prod_n p(y_n | z_e^k, x_n).
+// One block per element; FP32 terms with a block-wide max shift.
+template <int MAXD>
+__global__ void __launch_bounds__(256) k_predictive(LevelView v, int K, const float* __restrict__ xn,
+                                                  const float* __restrict__ yn, int nn, double* out) {
+  extern __shared__ __align__(16) float psm[];
+  __shared__ float red_m[8], red_s[8];
+  const long long e = blockIdx.x;
+  const int D = v.D;
+  float* xs = psm;                 // [nn][D]
+  float* ys = xs + nn * D;         // [nn]
+  float* cs = ys + nn;             // [nn] per-observation constant
+  for (int i = threadIdx.x; i < nn * D; i += blockDim.x) xs[i] = xn ? xn[e * (long long)nn * D + i] : 0.f;
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+    const float y = yn[e * nn + n];
+    ys[n] = y;
+    float c = 0.f;
+    if (v.lik == QEM_LIK_GAUSS) c = -0.5f * logf(6.283185307179586f * v.lik_var);
+    if (v.lik == QEM_LIK_POISSON_LOG || v.lik == QEM_LIK_POISSON_RATE) c = -lgammaf(y + 1.f);
+    cs[n] = c;
+  }
+  __syncthreads();
+  float m = -INFINITY, sacc = 0.f;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const float wk = v.w[e * K + k];
+    if (!(wk > 0.f)) continue;
+    const float* zr = v.z + (e * K + k) * (long long)D;
+    float z[MAXD];
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) z[d] = d < D ? zr[d] : 0.f;
+    float ll = 0.f;
+    for (int n = 0; n < nn; ++n) {
+      float sdot = 0.f;
+#pragma unroll
+      for (int d = 0; d < MAXD; ++d)
+        if (d < D) sdot = fmaf(z[d], xs[n * D + d], sdot);
+      const float y = ys[n];
+      float t = cs[n];
+      switch (v.lik) {
+        case QEM_LIK_GAUSS: t += -0.5f * (y - sdot) * (y - sdot) / v.lik_var; break;
+        case QEM_LIK_BERNOULLI_LOGIT: t += y * sdot - (fmaxf(sdot, 0.f) + log1pf(expf(-fabsf(sdot)))); break;
+        case QEM_LIK_POISSON_LOG: t += y * sdot - expf(sdot); break;
+        case QEM_LIK_POISSON_RATE: t += y * logf(z[0]) - z[0]; break;
+        case QEM_LIK_BERNOULLI_PROB: t += y * logf(z[0]) + (1.f - y) * log1pf(-z[0]); break;
+        default: break;
+      }
+      ll += t;
+    }
+    const float a = logf(wk) + ll;
+    if (a > m) {
+      sacc = (m == -INFINITY ? 0.f : sacc * expf(m - a)) + 1.f;
+      m = a;
+    } else if (a > -INFINITY) {
+      sacc += expf(a - m);
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int o = 16; o; o >>= 1) {
+    const float mo = __shfl_xor_sync(0xffffffffu, m, o), so = __shfl_xor_sync(0xffffffffu, sacc, o);
+    const float M = fmaxf(m, mo);
+    sacc = (m == -INFINITY ? 0.f : sacc * expf(m - M)) + (mo == -INFINITY ? 0.f : so * expf(mo - M));
+    m = M;
+  }
+  if (lane == 0) {
+    red_m[warp] = m;
+    red_s[warp] = sacc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float M = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmaxf(M, red_m[w]);
+    double S = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      if (red_m[w] > -INFINITY) S += (double)red_s[w] * exp((double)red_m[w] - (double)M);
+    out[e] = (double)M + log(S);
+  }
+}
+
+cudaError_t launch_predictive(const LevelView& v, int K, const float* xn, const float* yn, int nn, double* out,
+                              cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  const size_t sm = sizeof(float) * ((size_t)nn * v.D + 2 * (size_t)nn);
+  if (sm > 48 * 1024) return cudaErrorInvalidValue;
+  const unsigned g = (unsigned)v.n;
+  if (v.D <= 4) k_predictive<4><<<g, 256, sm, s>>>(v, K, xn, yn, nn, out);
+  else if (v.D <= 8) k_predictive<8><<<g, 256, sm, s>>>(v, K, xn, yn, nn, out);
+  else if (v.D <= 20) k_predictive<20><<<g, 256, sm, s>>>(v, K, xn, yn, nn, out);
+  else if (v.D <= 40) k_predictive<40><<<g, 256, sm, s>>>(v, K, xn, yn, nn, out);
+  else k_predictive<64><<<g, 256, sm, s>>>(v, K, xn, yn, nn, out);
+  return cudaGetLastError();
+}
+
 }  // namespace qem

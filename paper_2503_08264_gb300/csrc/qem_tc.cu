@@ -917,9 +917,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
           if (ts == 0) tph ^= 1;
         }
       }
-      // every issued MMA has completed before the teardown
+      // every issued MMA has completed before the teardown, also after an
+      // abort (the wait ignores the abort flag; it is still bounded)
       mma_commit(s.done);
-      mbar_wait(s.done, 0, lim, s.abort_flag);
+      volatile int never = 0;
+      mbar_wait(s.done, 0, lim, &never);
     }
     __syncwarp();
   } else {
@@ -1081,7 +1083,14 @@ __global__ void __launch_bounds__(128, 1) k_diag_gemm(const __nv_bfloat16* A, co
       for (int j = 0; j < 8; ++j) out[(long long)row * n + c + j] = v[j];
     }
   }
-  if (*abort_flag && threadIdx.x == 0) atomicOr(&ctl->err, ERR_TIMEOUT);
+  if (threadIdx.x == 0) {
+    if (*abort_flag) atomicOr(&ctl->err, ERR_TIMEOUT);
+    // neither the bulk copies nor the MMAs may still be in flight at the
+    // teardown, also after an abort (bounded waits that ignore the flag)
+    volatile int never = 0;
+    mbar_wait(&bars[0], 0, lim, &never);
+    mbar_wait(&bars[1], 0, lim, &never);
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {

@@ -183,6 +183,15 @@ class Plan:
         L.check(L.load().qem_log_pmp_fresh(self.h, _ptr(q), seed, it, _ptr(log_pmp)), "qem_log_pmp_fresh")
         return log_pmp
 
+    def predictive(self, level: int, x_new, y_new):
+        """Predictive log-likelihood of held-out (x_new [n, N, D], y_new [n, N]) per element."""
+        out = torch.empty(self.model.levels[level].n, dtype=torch.float64, device=self.device)
+        xd = None if x_new is None else torch.as_tensor(x_new, dtype=torch.float32).to(self.device).contiguous()
+        yd = torch.as_tensor(y_new, dtype=torch.float32).to(self.device).contiguous()
+        L.check(L.load().qem_predictive(self.h, level, _ptr(xd), _ptr(yd), yd.shape[1], _ptr(out)), "qem_predictive")
+        torch.cuda.current_stream().synchronize()
+        return out
+
     def moments_rescale(self, log_pmp_same, log_pmp_fresh, moments):
         L.check(L.load().qem_moments_rescale(self.h, _ptr(log_pmp_same), _ptr(log_pmp_fresh), _ptr(moments)),
                 "qem_moments_rescale")

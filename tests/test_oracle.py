@@ -312,3 +312,27 @@ def test_instances_are_independent_and_subset_noise_matches():
     for l in range(3):
         np.testing.assert_allclose(got["mom"][l], ref["mom"][l][keep[l]], rtol=1e-12, atol=1e-14)
         np.testing.assert_allclose(got["w"][l], ref["w"][l][keep[l]], rtol=1e-12, atol=1e-15)
+
+
+def test_predictive_special_cases():
+    """A weight vector on one sample gives that sample's log-likelihood; equal
+    samples give it whatever the weights; Jensen's inequality against the
+    weighted mean of the log-likelihoods."""
+    rng = np.random.default_rng(61)
+    n, K, D, N = 3, 7, 4, 5
+    z = rng.standard_normal((n, K, D)) * 0.5
+    x = rng.standard_normal((n, N, D))
+    y = (rng.random((n, N)) < 0.4).astype(np.float64)
+    one = np.zeros((n, K))
+    one[:, 2] = 1.0
+    s = np.einsum("ekd,end->ekn", z, x)
+    ll = (y[:, None, :] * s - np.logaddexp(0.0, s)).sum(-1)      # Bernoulli-logit by hand
+    np.testing.assert_allclose(O.predictive(z, one, 2, x, y), ll[:, 2], rtol=1e-12)
+    same = np.repeat(z[:, :1], K, axis=1)
+    w = rng.dirichlet(np.ones(K), size=n)
+    np.testing.assert_allclose(O.predictive(same, w, 2, x, y), ll[:, 0] * 0 + (y * (x @ z[:, 0][..., None])[..., 0]
+                               - np.logaddexp(0.0, (x @ z[:, 0][..., None])[..., 0])).sum(-1), rtol=1e-12)
+    assert np.all(O.predictive(z, w, 2, x, y) >= (w * ll).sum(1) - 1e-12)
+    yc = rng.poisson(2.0, (n, N)).astype(np.float64)
+    lp = (yc[:, None, :] * s - np.exp(s) - np.vectorize(math.lgamma)(yc + 1.0)[:, None, :]).sum(-1)
+    np.testing.assert_allclose(O.predictive(z, one, 3, x, yc), lp[:, 2], rtol=1e-12)
