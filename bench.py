@@ -61,6 +61,8 @@ def parse(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--ref-seconds", type=float, default=150.0,
+                   help="reference arm: total oracle time the samples are sized for")
     p.add_argument("--metric", choices=["pairs", "time_to_tol"], default="pairs",
                    help="pairs: E-step throughput (default); time_to_tol: the warm-start study")
     p.add_argument("--train-instances", type=int, default=2000)
@@ -262,7 +264,7 @@ def run_reference(args):
     O.build()
     builder, K, _ = WORKLOADS[args.workload]
     # size one step's sample so that warmup + steps fit in about three minutes
-    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    per_step = max(0.2, args.ref_seconds / max(1, args.steps + args.warmup))
     base, model = cpu_oracle_sample(args.workload, per_step)
     times = []
     for i in range(args.warmup + args.steps):
