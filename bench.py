@@ -178,8 +178,8 @@ SMS = 152
 # unchanged (the summary under profiles/ gives the capture command).
 NCU_TRAFFIC = {
     ("forward", "hier_logistic_M5000_N10_K1024", "bf16x3"): {
-        "bytes": 820014080 + 21017856, "source": "paper_2503_08264_gb300/csrc/qem_tc.cu",
-        "blob": "984610bf62e0d262760d81478b44a7c357e44ba3",
+        "bytes": 819579904 + 21370624, "source": "paper_2503_08264_gb300/csrc/qem_tc.cu",
+        "blob": "f35ba41dc5179f8fbdfdc7012d1fc54b19f4599f",
         "profile": "profiles/contract_forward_bf16x3_hier_logistic_M5000_K1024.md"},
 }
 

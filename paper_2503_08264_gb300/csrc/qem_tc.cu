@@ -540,6 +540,20 @@ __global__ void k_dcol(LevelView ch, LevelView par, int K, int small, const floa
 // in place; a partial sum above 2^32 (a group far above the shift) is redone
 // from TMEM at the group's exact maximum, so the running sum never overflows.
 // Called by all 32 lanes of a warp together (it issues warp-collective loads).
+// Packed FP32 pair arithmetic (two lanes of work per instruction).
+__device__ __forceinline__ void sub2(float& a0, float& a1, float b) {
+  asm("{\n .reg .b64 x, y, r;\n mov.b64 x, {%0, %1};\n mov.b64 y, {%2, %2};\n"
+      " sub.rn.ftz.f32x2 r, x, y;\n mov.b64 {%0, %1}, r;\n}\n"
+      : "+f"(a0), "+f"(a1)
+      : "f"(b));
+}
+__device__ __forceinline__ void add2(float& a0, float& a1, float b0, float b1) {
+  asm("{\n .reg .b64 x, y, r;\n mov.b64 x, {%0, %1};\n mov.b64 y, {%2, %3};\n"
+      " add.rn.ftz.f32x2 r, x, y;\n mov.b64 {%0, %1}, r;\n}\n"
+      : "+f"(a0), "+f"(a1)
+      : "f"(b0), "f"(b1));
+}
+
 __device__ __forceinline__ void lse_group32(uint32_t taddr, float& m, float& sacc) {
   float v[32];
   tmem_ld32(taddr, v);
@@ -550,14 +564,15 @@ __device__ __forceinline__ void lse_group32(uint32_t taddr, float& m, float& sac
     m = mx;
   }
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] -= m;
+  for (int j = 0; j < 32; j += 2) sub2(v[j], v[j + 1], m);
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = ex2f(v[j]);
+  // pairwise tree on pairs: (v[2i], v[2i+1]) += (v[2i+w], v[2i+w+1])
 #pragma unroll
-  for (int w = 16; w >= 1; w >>= 1)
+  for (int w = 16; w >= 2; w >>= 1)
 #pragma unroll
-    for (int j = 0; j < w; ++j) v[j] += v[j + w];
-  float pt = v[0];
+    for (int j = 0; j < w; j += 2) add2(v[j], v[j + 1], v[j + w], v[j + w + 1]);
+  float pt = v[0] + v[1];
   const bool redo = !(pt <= 4294967296.0f);
   // tcgen05.ld is warp-collective: the reload runs on the whole warp whenever
   // any lane needs it, and only those lanes use it.
@@ -969,12 +984,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
               const float4 dv = d4[j >> 2];
-              p0 += ex2f(v[j] + dv.x);
-              p1 += ex2f(v[j + 1] + dv.y);
-              p2 += ex2f(v[j + 2] + dv.z);
-              p3 += ex2f(v[j + 3] + dv.w);
+              add2(v[j], v[j + 1], dv.x, dv.y);
+              add2(v[j + 2], v[j + 3], dv.z, dv.w);
+              float e0 = ex2f(v[j]), e1 = ex2f(v[j + 1]), e2 = ex2f(v[j + 2]), e3 = ex2f(v[j + 3]);
+              add2(p0, p1, e0, e1);
+              add2(p2, p3, e2, e3);
             }
-            sacc += (p0 + p1) + (p2 + p3);
+            add2(p0, p1, p2, p3);
+            sacc += p0 + p1;
           }
           for (; c < qw; c += 4) {
             float v[4];
