@@ -983,17 +983,17 @@ __global__ void k_moments(LevelView v, int K, double* mom) {
   if (t < per * D) {
     const int d = t % D;
     int k = t / D;
-    // four samples' loads in flight before their accumulation (the Kahan
+    // eight samples' loads in flight before their accumulation (the Kahan
     // chain would otherwise wait for every load in turn)
-    for (; k + 3 * per < K; k += 4 * per) {
-      float wk[4], zv[4];
+    for (; k + 7 * per < K; k += 8 * per) {
+      float wk[8], zv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         wk[u] = v.w[e * K + k + u * per];
         zv[u] = v.z[(e * K + k + u * per) * D + d];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         float t0, t1;
         if (v.qfam == QEM_Q_GAUSS) {
           t0 = zv[u];
