@@ -121,6 +121,28 @@ struct qem_plan_s {
 namespace qem {
 
 // ---------------------------------------------------------------------------
+// Packed FP32 pair arithmetic (one instruction for two lanes of work):
+// (a0, a1) <- (a0, a1) + (b0, b1) * (c0, c1), and (d0, d1) = (x0 - y0, x1 - y1).
+__device__ __forceinline__ void fma2(float& a0, float& a1, float b0, float b1, float c0, float c1) {
+  asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n mov.b64 z, {%0, %1};\n"
+      " fma.rn.f32x2 z, x, y, z;\n mov.b64 {%0, %1}, z;\n}\n"
+      : "+f"(a0), "+f"(a1)
+      : "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
+__device__ __forceinline__ void diff2(float& d0, float& d1, float x0, float x1, float y0, float y1) {
+  asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+      " sub.rn.f32x2 z, x, y;\n mov.b64 {%0, %1}, z;\n}\n"
+      : "=f"(d0), "=f"(d1)
+      : "f"(x0), "f"(x1), "f"(y0), "f"(y1));
+}
+__device__ __forceinline__ void mul2(float& d0, float& d1, float x0, float x1, float y0, float y1) {
+  asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+      " mul.rn.f32x2 z, x, y;\n mov.b64 {%0, %1}, z;\n}\n"
+      : "=f"(d0), "=f"(d1)
+      : "f"(x0), "f"(x1), "f"(y0), "f"(y1));
+}
+
+// ---------------------------------------------------------------------------
 // Block-wide copy of n consecutive floats (sample rows of width D) from global
 // memory into shared rows of stride D + 1: 16-byte loads when the source is
 // aligned, four of them in flight per thread before their stores (the copies

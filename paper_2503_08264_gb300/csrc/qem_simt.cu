@@ -527,12 +527,16 @@ __global__ void __launch_bounds__(kFwdRowsMax) k_fwd_simt(LevelView v, LevelView
     for (int j = 0; j < CHUNK; ++j) {
       float a = -INFINITY;
       if (j < nk) {
-        a = hs[j];
+        // dimensions in pairs (packed FP32): a += pp_d (z_d - pm_d)^2
+        float a0 = hs[j], a1 = 0.f;
 #pragma unroll
-        for (int d = 0; d < MAXD; ++d) {
-          const float t = zs[j * MAXD + d] - pm[d];
-          a = fmaf(pp[d], t * t, a);
+        for (int d = 0; d < MAXD; d += 2) {
+          float t0, t1, q0, q1;
+          diff2(t0, t1, zs[j * MAXD + d], zs[j * MAXD + d + 1], pm[d], pm[d + 1]);
+          mul2(q0, q1, t0, t1, t0, t1);
+          fma2(a0, a1, pp[d], pp[d + 1], q0, q1);
         }
+        a = a0 + a1;
       }
       val[j] = a;
       cm = fmaxf(cm, a);
