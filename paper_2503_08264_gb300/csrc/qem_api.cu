@@ -191,7 +191,10 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
   cudaStream_t s = P->stream;
   const int L = P->L, K = P->K;
   for (int l = 1; l < L; ++l) {
-    QEM_LAUNCH(P, QEM_K_OPERANDS, launch_compact(P->lv[l - 1], K, s));
+    // parent samples below rel * the largest weight are dropped from the
+    // adjoint: 2^-40 on the FP32 path, 2^-24 on the mixed-precision paths
+    const float rel = P->precision == QEM_PREC_FP32 ? 9.094947017729282e-13f : 5.9604644775390625e-08f;
+    QEM_LAUNCH(P, QEM_K_OPERANDS, launch_compact(P->lv[l - 1], K, rel, s));
     if (P->precision == QEM_PREC_FP32) {
       QEM_LAUNCH(P, QEM_K_ADJOINT, launch_adj_compact(P->lv[l], P->lv[l - 1], K, 0, s));
     } else {

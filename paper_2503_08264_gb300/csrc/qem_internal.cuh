@@ -305,7 +305,7 @@ cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& parent, int K, 
 cudaError_t launch_plate_sum(const LevelView& parent, const LevelView& child, int K, cudaStream_t s);
 cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* log_pmp, double* user_out,
                         double* trace, Ctl* ctl, cudaStream_t s);
-cudaError_t launch_compact(const LevelView& parent, int K, cudaStream_t s);
+cudaError_t launch_compact(const LevelView& parent, int K, float rel, cudaStream_t s);
 cudaError_t launch_adj_compact(const LevelView& v, const LevelView& parent, int K, int max_eff, cudaStream_t s);
 cudaError_t launch_adj_small(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
 cudaError_t configure_adj_small(int D, int K);

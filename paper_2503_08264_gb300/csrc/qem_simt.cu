@@ -675,11 +675,12 @@ __device__ __forceinline__ void stage_samples(const LevelView& v, long long e, i
 }
 
 // Compaction of the parent samples that carry weight: kept = w_p[kp] >
-// 2^-40 max_kp w_p, in index order.  The dropped samples change the marginal
-// weights by less than K 2^-40 in total (about 1e-9 at K = 1024, far below
-// FP32 rounding).  cw = ln w_p - ln K of each kept
+// rel * max_kp w_p, in index order.  The dropped samples change the marginal
+// weights by less than K rel in total (the plan takes rel = 2^-40 for the FP32
+// path, ~1e-9 at K = 1024, and 2^-24 for the mixed-precision paths, ~6e-5,
+// both below the path's error).  cw = ln w_p - ln K of each kept
 // sample; the list is padded to a multiple of 16 with cw = -inf.
-__global__ void k_compact(LevelView par, int K) {
+__global__ void k_compact(LevelView par, int K, float rel) {
   const long long p = blockIdx.x;
   __shared__ float red[32];
   __shared__ int scan[1024];
@@ -691,7 +692,7 @@ __global__ void k_compact(LevelView par, int K) {
   __syncthreads();
   float wmax = 0.f;
   for (int j = 0; j < (int)(blockDim.x >> 5); ++j) wmax = fmaxf(wmax, red[j]);
-  const float thr = wmax * 9.094947017729282e-13f;  // 2^-40
+  const float thr = wmax * rel;
   const int per = (K + blockDim.x - 1) / blockDim.x;
   const int k0 = threadIdx.x * per, k1 = min(K, k0 + per);
   int cnt = 0;
@@ -722,9 +723,9 @@ __global__ void k_compact(LevelView par, int K) {
   if (threadIdx.x == 0) par.ccnt[p] = total;
 }
 
-cudaError_t launch_compact(const LevelView& parent, int K, cudaStream_t s) {
+cudaError_t launch_compact(const LevelView& parent, int K, float rel, cudaStream_t s) {
   if (parent.n == 0) return cudaSuccess;
-  k_compact<<<(unsigned)parent.n, 256, 0, s>>>(parent, K);
+  k_compact<<<(unsigned)parent.n, 256, 0, s>>>(parent, K, rel);
   return cudaGetLastError();
 }
 
