@@ -133,3 +133,54 @@ def estep_instance(model, q, z, K: int, inst: int = 0) -> dict:
         T = _T(lv, np.asarray(z[l][e], np.float64))      # [2, K, dim]
         mom[(l, e)] = np.einsum("k,skd->sd", wi, T)
     return {"log_pmp": log_pmp, "w": w, "mom": mom, "n": n}
+
+
+def estep_instance_split_root(model, q, z, K: int, inst: int = 0) -> dict:
+    """Enumeration for a two-level model whose root halves are separate latents.
+
+    The root sample rows z[0][inst, k] = (mu^k, psi^k) are read as two latents,
+    mu (dimensions [0, D)) and psi ([D, 2D)), each with its own index, so the
+    index vector is (k_mu, k_psi, k_1, ..., k_M) and a user's prior factor
+    N(z_m; mu^{k_mu}, diag exp(psi^{k_psi})) takes both parent indices.  The
+    root prior N(0, v I) and the proposal are products over dimensions, so
+    each half keeps its own part of them.  Returns log_pmp, w_mu, w_psi,
+    w / mom of the users keyed by element, n.
+    """
+    r, u = model.levels
+    D = u.dim
+    q0 = np.asarray(q[0][inst], np.float64)
+    users = [int(e) for e in np.nonzero(np.asarray(u.parent) == inst)[0]]
+    n = 2 + len(users)
+    mu = np.asarray(z[0][inst][:, :D], np.float64)
+    psi = np.asarray(z[0][inst][:, D:], np.float64)
+    sd0 = math.sqrt(r.prior_a)
+    un_mu = np.array([stats.norm.logpdf(mu[k], 0.0, sd0).sum() - stats.norm.logpdf(mu[k], q0[0, :D], q0[1, :D]).sum()
+                      for k in range(K)])
+    un_psi = np.array([stats.norm.logpdf(psi[k], 0.0, sd0).sum()
+                       - stats.norm.logpdf(psi[k], q0[0, D:], q0[1, D:]).sum() for k in range(K)])
+    un_u, pair = [], []
+    for e in users:
+        ze = np.asarray(z[1][e], np.float64)
+        un_u.append(np.array([_log_lik(u, e, ze[k]) - _log_q(u, q[1][e], ze[k]) for k in range(K)]))
+        f = np.zeros((K, K, K))
+        for a in range(K):
+            for b in range(K):
+                zp = np.concatenate([mu[a], psi[b]])
+                for k in range(K):
+                    f[a, b, k] = _log_prior(u, ze[k], zp)
+        pair.append(f)
+    combos = np.array(list(itertools.product(range(K), repeat=n)))
+    logr = un_mu[combos[:, 0]] + un_psi[combos[:, 1]]
+    for j in range(len(users)):
+        logr = logr + un_u[j][combos[:, 2 + j]] + pair[j][combos[:, 0], combos[:, 1], combos[:, 2 + j]]
+    mx = logr.max()
+    terms = np.exp(logr - mx)
+    tot = math.fsum(terms)
+    out = {"log_pmp": mx + math.log(tot) - n * math.log(K), "n": n, "w": {}, "mom": {}}
+    marg = [np.array([math.fsum(terms[combos[:, i] == k]) for k in range(K)]) / tot for i in range(n)]
+    out["w_mu"], out["w_psi"] = marg[0], marg[1]
+    for j, e in enumerate(users):
+        ze = np.asarray(z[1][e], np.float64)
+        out["w"][e] = marg[2 + j]
+        out["mom"][e] = np.stack([marg[2 + j] @ ze, marg[2 + j] @ ze ** 2])
+    return out
