@@ -163,6 +163,31 @@ qem_status qem_sizes(const qem_plan_t plan, int64_t* q_len, int64_t* eps_len, in
 qem_status qem_estep(qem_plan_t plan, const float* q_params, const float* eps, uint64_t seed,
                      uint64_t iter, double* moments, double* log_pmp);
 
+/* E-step with the root's two halves as separate latents (the paper's own
+ * form of App. F's MovieLens model: the global mean mu and the global
+ * log-variance psi each carry their own sample index, so a user's prior
+ * factor N(z_m; mu^a, diag exp(psi^b)) takes two parent indices and is
+ * summed into a K x K table per user -- the K^(number of parents) tables of
+ * the Limitations section; qem_estep groups (mu, psi) into one latent with
+ * one index instead).  Eq. mp_iw over all (a, b, k_1, ..., k_M):
+ *   log P_MP = log (1/K^2) sum_{a,b} exp(f_mu[a] + f_psi[b] + sum_m L_m[a][b]).
+ * The plan must have two levels: level 0 of dimension 2D with the
+ * QEM_PRIOR_STD_NORMAL prior, a Gaussian proposal and no likelihood; level 1
+ * with QEM_PRIOR_NORMAL_MEAN_LOGVAR (mu = dimensions [0, D), psi = [D, 2D)
+ * of the root sample rows, the same samples as qem_estep draws), D <= 32
+ * and K <= 1024; otherwise QEM_ERR_UNSUPPORTED.  The contraction runs on the
+ * CUDA cores in FP32 whatever the plan's precision (FP64 root sums).
+ * Arguments as qem_estep; moments of the root take the mu weights for
+ * dimensions [0, D) and the psi weights for [D, 2D).  root_weights: DEVICE
+ * float [n_inst][2][K] (nullable) receives (w_mu, w_psi); qem_weights then
+ * returns w_mu at level 0 and the users' marginal weights at level 1.
+ * Workspace: n_1 K^2 floats of per-user tables plus n_0 K^2 root values,
+ * allocated by the first call (QEM_ERR_OOM when it does not fit; that call
+ * must not be inside a stream capture, QEM_ERR_UNSUPPORTED otherwise) and
+ * kept by the plan.                                                         */
+qem_status qem_estep_split_root(qem_plan_t plan, const float* q_params, const float* eps, uint64_t seed,
+                                uint64_t iter, double* moments, double* log_pmp, float* root_weights);
+
 /* log P_MP of q_params from a fresh draw of the samples (the noise stream
  * keyed by (seed, iter), which the caller chooses distinct from the E-step's):
  * the forward half of the E-step only (Eq. Prmp; no weights, no moments).

@@ -49,6 +49,8 @@ SIGNATURES = {
                             C.POINTER(C.c_int64)]),
     "qem_estep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p,
                             C.c_void_p]),
+    "qem_estep_split_root": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]),
     "qem_log_pmp_fresh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p]),
     "qem_predictive": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "qem_moments_rescale": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

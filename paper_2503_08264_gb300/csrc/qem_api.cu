@@ -393,6 +393,49 @@ qem_status maybe_autotune(qem_plan_t P, const float* q) {
   return qem_tune(P, q, 0);
 }
 
+// Split-root workspace (qem_estep_split_root): carved from one allocation.
+qem_status split_alloc(qem_plan_t P) {
+  if (P->split) return QEM_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(P->stream, &cs) != cudaSuccess) return QEM_ERR_CUDA;
+  if (cs != cudaStreamCaptureStatusNone) return QEM_ERR_UNSUPPORTED;
+  SplitWs* W = new (std::nothrow) SplitWs();
+  if (!W) return QEM_ERR_OOM;
+  const size_t K = (size_t)P->K, KK = K * K, n0 = (size_t)P->lv[0].n, n1 = (size_t)P->lv[1].n;
+  const size_t nch = (size_t)P->lv[1].n_chunks;
+  for (int pass = 0; pass < 2; ++pass) {
+    Carver cv;
+    if (pass == 1) {
+      if (cudaMalloc(&W->base, W->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete W;
+        return QEM_ERR_OOM;
+      }
+      cv.base = (char*)W->base;
+    }
+    W->fa = cv.take<double>(n0 * K);
+    W->fb = cv.take<double>(n0 * K);
+    W->lt = cv.take<float>(n1 * KK);
+    W->partial = cv.take<double>(nch * KK);
+    W->hsum = cv.take<double>(n0 * KK);
+    W->W = cv.take<float>(n0 * KK);
+    W->cidx = cv.take<int>(n0 * KK);
+    W->ccnt = cv.take<int>(n0);
+    W->cw = cv.take<float>(n0 * KK);
+    W->wab = cv.take<float>(n0 * 2 * K);
+    if (pass == 0) W->bytes = std::max<size_t>(cv.off, 256);
+  }
+  P->split = W;
+  return QEM_OK;
+}
+
+void split_free(qem_plan_t P) {
+  if (!P->split) return;
+  if (P->split->base) cudaFree(P->split->base);
+  delete P->split;
+  P->split = nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -601,6 +644,7 @@ qem_status qem_plan_destroy(qem_plan_t P) {
   if (!P) return QEM_OK;
   cudaError_t e = cudaStreamSynchronize(P->stream);
   tc_plan_release(P);
+  split_free(P);
   delete prof_of(P);
   delete run_of(P);
   if (P->ws) cudaFree(P->ws);
@@ -646,6 +690,53 @@ qem_status qem_log_pmp_fresh(qem_plan_t P, const float* q_params, uint64_t seed,
   if (ts != QEM_OK) return ts;
   QEM_TRY(launch_set_ctl(P->ctl, seed, iter, 1, -1, P->stream));
   return estep_forward(P, q_params, nullptr, log_pmp, nullptr);
+}
+
+qem_status qem_estep_split_root(qem_plan_t P, const float* q_params, const float* eps, uint64_t seed, uint64_t iter,
+                                double* moments, double* log_pmp, float* root_weights) {
+  if (!P || !q_params || !moments) return QEM_ERR_INVALID_ARG;
+  if (P->L != 2) return QEM_ERR_UNSUPPORTED;
+  const LevelView& r = P->lv[0];
+  const LevelView& u = P->lv[1];
+  if (r.prior != QEM_PRIOR_STD_NORMAL || r.qfam != QEM_Q_GAUSS || r.lik != QEM_LIK_NONE ||
+      u.prior != QEM_PRIOR_NORMAL_MEAN_LOGVAR || r.D != 2 * u.D || u.D > 32 || P->K > 1024)
+    return QEM_ERR_UNSUPPORTED;
+  qem_status st = split_alloc(P);
+  if (st != QEM_OK) return st;
+  SplitWs& W = *P->split;
+  cudaStream_t s = P->stream;
+  const int K = P->K, KK = K * K;
+  QEM_TRY(launch_set_ctl(P->ctl, seed, iter, 1, -1, s));
+  for (int l = 0; l < 2; ++l) {
+    QEM_LAUNCH(P, QEM_K_SAMPLE,
+               launch_sample_local(P->lv[l], K, P->tune.sample_threads, q_params + P->q_off[l],
+                                   eps ? eps + P->eps_off[l] : nullptr, P->ctl, s));
+    QEM_LAUNCH(P, QEM_K_SAMPLE, launch_elem_const(P->lv[l], q_params + P->q_off[l], s));
+  }
+  QEM_LAUNCH(P, QEM_K_PARENT, launch_parent_params(r, u, K, s));
+  QEM_LAUNCH(P, QEM_K_ROOT, launch_split_unary(r, K, q_params + P->q_off[0], W.fa, W.fb, s));
+  // users: K^2-row tables, their plate sums, the root over the pairs
+  LevelView uk = u;
+  uk.lt = W.lt;
+  uk.partial = W.partial;
+  LevelView rk = r;
+  rk.hsum = W.hsum;
+  rk.w = W.W;
+  rk.cidx = W.cidx;
+  rk.ccnt = W.ccnt;
+  rk.cw = W.cw;
+  QEM_LAUNCH(P, QEM_K_FORWARD, launch_fwd_simt(uk, r, K, P->tune.fwd_rows, P->tune.fwd_chunk, s, true));
+  QEM_LAUNCH(P, QEM_K_PLATE_SUM, launch_plate_sum(rk, uk, KK, s));
+  QEM_LAUNCH(P, QEM_K_ROOT,
+             launch_split_root((int)r.n, K, W.fa, W.fb, W.hsum, W.W, root_weights ? root_weights : W.wab, r.w,
+                               P->log_pmp, log_pmp, P->ctl, s));
+  // adjoint over the kept pairs (2^-40 of the largest joint weight: FP32 path)
+  QEM_LAUNCH(P, QEM_K_OPERANDS, launch_compact(rk, KK, 9.094947017729282e-13f, s, K));
+  QEM_LAUNCH(P, QEM_K_ADJOINT, launch_adj_compact(uk, rk, K, 0, s, true));
+  QEM_LAUNCH(P, QEM_K_MOMENTS, launch_moments(u, K, P->tune.mom_threads, moments + P->q_off[1], s));
+  QEM_LAUNCH(P, QEM_K_MOMENTS,
+             launch_split_root_moments(r, K, root_weights ? root_weights : W.wab, moments + P->q_off[0], s));
+  return QEM_OK;
 }
 
 qem_status qem_predictive(qem_plan_t P, int level, const float* x_new, const float* y_new, int n_obs_new,

@@ -79,6 +79,22 @@ struct LevelView {
 
 struct TcBuffers;  // tensor-core operand buffers (qem_tc.cu)
 
+// Workspace of the split-root E-step (qem_split.cu), allocated on first use.
+struct SplitWs {
+  void* base = nullptr;
+  size_t bytes = 0;
+  double* fa = nullptr;        // [n0][K]   root factor of the mu half of each root sample
+  double* fb = nullptr;        // [n0][K]   the same for the psi half
+  float* lt = nullptr;         // [n1][K^2] user tables L_m[a K + b] (relative, as lt)
+  double* partial = nullptr;   // [n1 chunks][K^2] plate-sum partials
+  double* hsum = nullptr;      // [n0][K^2] sum over users
+  float* W = nullptr;          // [n0][K^2] joint root weights
+  int* cidx = nullptr;         // [n0][K^2] kept pairs
+  int* ccnt = nullptr;         // [n0]
+  float* cw = nullptr;         // [n0][K^2]
+  float* wab = nullptr;        // [n0][2][K] (w_mu, w_psi)
+};
+
 }  // namespace qem
 
 namespace qem {
@@ -115,6 +131,7 @@ struct qem_plan_s {
   void* prof = nullptr;        // per-kernel event records (qem_api.cu)
   void* run = nullptr;         // cached device-loop graph of qem_run (qem_api.cu)
   qem::Tune tune;              // launch shapes (defaults, or chosen by qem_tune)
+  qem::SplitWs* split = nullptr; // split-root workspace (qem_estep_split_root), allocated on first use
   bool tuned = false;          // qem_tune has run (or a cached choice was applied)
 };
 
@@ -301,12 +318,16 @@ cudaError_t launch_sample_local(const LevelView& v, int K, int threads, const fl
                                 cudaStream_t s);
 cudaError_t launch_parent_params(const LevelView& parent, const LevelView& child, int K, cudaStream_t s);
 cudaError_t launch_finalize(const LevelView& v, int K, bool has_children, cudaStream_t s);
-cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& parent, int K, int rows, int chunk, cudaStream_t s);
+// split: the parent's rows are the K^2 pairs of its two halves (qem_split.cu).
+cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& parent, int K, int rows, int chunk, cudaStream_t s,
+                            bool split = false);
 cudaError_t launch_plate_sum(const LevelView& parent, const LevelView& child, int K, cudaStream_t s);
 cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* log_pmp, double* user_out,
                         double* trace, Ctl* ctl, cudaStream_t s);
-cudaError_t launch_compact(const LevelView& parent, int K, float rel, cudaStream_t s);
-cudaError_t launch_adj_compact(const LevelView& v, const LevelView& parent, int K, int max_eff, cudaStream_t s);
+// Kc: sample count of the children (0: K).
+cudaError_t launch_compact(const LevelView& parent, int K, float rel, cudaStream_t s, int Kc = 0);
+cudaError_t launch_adj_compact(const LevelView& v, const LevelView& parent, int K, int max_eff, cudaStream_t s,
+                               bool split = false);
 cudaError_t launch_adj_small(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
 cudaError_t configure_adj_small(int D, int K);
 cudaError_t launch_moments(const LevelView& v, int K, int threads, double* mom, cudaStream_t s);
@@ -318,6 +339,10 @@ cudaError_t configure_sample_local(size_t smem);
 cudaError_t launch_mean_params(const LevelView& v, const float* q, double* m, cudaStream_t s);
 cudaError_t launch_moments_rescale(const LevelView* lvs, int l, const double* lp_same, const double* lp_fresh,
                                    double* mom, cudaStream_t s);
+cudaError_t launch_split_unary(const LevelView& root, int K, const float* q, double* fa, double* fb, cudaStream_t s);
+cudaError_t launch_split_root(int n_inst, int K, const double* fa, const double* fb, const double* hsum, float* W,
+                              float* wab, float* w0, double* log_pmp, double* user_out, Ctl* ctl, cudaStream_t s);
+cudaError_t launch_split_root_moments(const LevelView& root, int K, const float* wab, double* mom, cudaStream_t s);
 cudaError_t launch_predictive(const LevelView& v, int K, const float* xn, const float* yn, int nn, double* out,
                               cudaStream_t s);
 

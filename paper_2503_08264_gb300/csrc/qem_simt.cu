@@ -1,6 +1,6 @@
-// libqem CUDA-core kernels: sampling and local factors, the FP32 log-factor
-// contraction (forward log-mean-exp and its adjoint), plate sums, the root,
-// moments and the M-step.  Every kernel cites the passage of arXiv
+// libqem CUDA-core kernels: sampling and local factors, plate sums, the root,
+// compaction, moments and the M-step (the FP32 log-factor contraction and its
+// adjoint are in qem_simt_contract.cu).  Every kernel cites the passage of arXiv
 // 2503.08264 it realises.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -481,106 +481,6 @@ cudaError_t launch_finalize(const LevelView& v, int K, bool has_children, cudaSt
 }
 
 // ---------------------------------------------------------------------------
-// K3 (FP32): forward contraction of one plate element (Eq. Prmp summed over
-// the child index, Sec. 7):
-//   lt[e][kp] = log (1/K) sum_k exp( log p(z_e^k | z_p^kp) + htil[e][k] )
-// One thread per parent sample kp; the element's child samples stream
-// through shared memory in chunks; online max-shifted sum per row.
-constexpr int kRowTile = 128;     // rows per block of the FP32 adjoint
-constexpr int kChunk = 32;        // staged parent samples of the FP32 adjoint
-constexpr int kFwdRowsMax = 256;
-
-template <int MAXD, int CHUNK>
-__global__ void __launch_bounds__(kFwdRowsMax) k_fwd_simt(LevelView v, LevelView par, int K, int n_rt) {
-  __shared__ float zs[CHUNK * MAXD];
-  __shared__ float hs[CHUNK];
-  const long long e = blockIdx.x / n_rt;
-  const int kp = (blockIdx.x % n_rt) * blockDim.x + threadIdx.x;
-  const int D = v.D;
-  const long long p = v.parent[e];
-  const bool act = kp < K;
-  float pm[MAXD], pp[MAXD], pc = 0.f;
-#pragma unroll
-  for (int d = 0; d < MAXD; ++d) {
-    pm[d] = 0.f;
-    pp[d] = 0.f;
-    if (act && d < D) {
-      pm[d] = par.pm[(p * K + kp) * D + d];
-      pp[d] = par.pp[(p * K + kp) * D + d];
-    }
-  }
-  if (act) pc = par.pc[p * K + kp];
-  float m = -INFINITY, s = 0.f;
-  for (int k0 = 0; k0 < K; k0 += CHUNK) {
-    const int nk = min(CHUNK, K - k0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < CHUNK * MAXD; i += blockDim.x) {
-      const int j = i / MAXD, d = i % MAXD;
-      zs[i] = (j < nk && d < D) ? v.z[(e * K + k0 + j) * D + d] : 0.f;
-    }
-    for (int i = threadIdx.x; i < nk; i += blockDim.x) hs[i] = v.htil[e * K + k0 + i];
-    __syncthreads();
-    if (!act) continue;
-    float val[CHUNK];
-    float cm = -INFINITY;
-#pragma unroll
-    for (int j = 0; j < CHUNK; ++j) {
-      float a = -INFINITY;
-      if (j < nk) {
-        // dimensions in pairs (packed FP32): a += pp_d (z_d - pm_d)^2
-        float a0 = hs[j], a1 = 0.f;
-#pragma unroll
-        for (int d = 0; d < MAXD; d += 2) {
-          float t0, t1, q0, q1;
-          diff2(t0, t1, zs[j * MAXD + d], zs[j * MAXD + d + 1], pm[d], pm[d + 1]);
-          mul2(q0, q1, t0, t1, t0, t1);
-          fma2(a0, a1, pp[d], pp[d + 1], q0, q1);
-        }
-        a = a0 + a1;
-      }
-      val[j] = a;
-      cm = fmaxf(cm, a);
-    }
-    if (cm == -INFINITY) continue;
-    if (cm > m) {
-      s *= expf(m - cm);
-      m = cm;
-    }
-#pragma unroll
-    for (int j = 0; j < CHUNK; ++j) s += expf(val[j] - m);
-  }
-  if (act) v.lt[e * K + kp] = pc + (m + logf(s) - logf((float)K));
-}
-
-template <int MAXD, int CHUNK>
-static cudaError_t fwd_simt_launch(const LevelView& v, const LevelView& par, int K, int rows, cudaStream_t s) {
-  const int thr = K >= rows ? rows : ((K + 31) / 32) * 32;
-  const int n_rt = (K + thr - 1) / thr;
-  k_fwd_simt<MAXD, CHUNK><<<(unsigned)(v.n * n_rt), thr, 0, s>>>(v, par, K, n_rt);
-  return cudaGetLastError();
-}
-
-template <int MAXD>
-static cudaError_t fwd_simt_dispatch(const LevelView& v, const LevelView& par, int K, int rows, int chunk,
-                                     cudaStream_t s) {
-  if (chunk == 16) return fwd_simt_launch<MAXD, 16>(v, par, K, rows, s);
-  if (chunk == 64 && MAXD <= 20) return fwd_simt_launch<MAXD, 64>(v, par, K, rows, s);
-  return fwd_simt_launch<MAXD, 32>(v, par, K, rows, s);
-}
-
-// rows: parent samples per block (a multiple of 32, at most 256); chunk: child
-// samples staged per round (16, 32, or 64 for D <= 20; others take 32).
-cudaError_t launch_fwd_simt(const LevelView& v, const LevelView& par, int K, int rows, int chunk, cudaStream_t s) {
-  if (v.n == 0) return cudaSuccess;
-  if (rows < 32 || rows > kFwdRowsMax || rows % 32) return cudaErrorInvalidValue;
-  if (v.D <= 4) return fwd_simt_dispatch<4>(v, par, K, rows, chunk, s);
-  if (v.D <= 8) return fwd_simt_dispatch<8>(v, par, K, rows, chunk, s);
-  if (v.D <= 20) return fwd_simt_dispatch<20>(v, par, K, rows, chunk, s);
-  if (v.D <= 32) return fwd_simt_dispatch<32>(v, par, K, rows, chunk, s);
-  return fwd_simt_dispatch<64>(v, par, K, rows, chunk, s);
-}
-
-// ---------------------------------------------------------------------------
 // Plate sum (Sec. 7: the child's factor enters the parent's as a sum over the
 // plate): hsum_p[kp] = sum_{e in children(p)} (lt[e][kp] + off[e] + cst[e]) in
 // FP64, in a fixed order (deterministic).  Stage 1 sums chunks of at most 32
@@ -667,20 +567,15 @@ cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* lo
 }
 
 // ---------------------------------------------------------------------------
-// Loads samples [k0, k0+nk) of element e into shared rows of stride D+1
-// (coalesced global reads; conflict-free row reads for odd strides).
-__device__ __forceinline__ void stage_samples(const LevelView& v, long long e, int K, int k0, int nk, float* zc) {
-  const int D = v.D;
-  stage_rows<0>(v.z + (e * K + k0) * (long long)D, nk * D, D, zc);
-}
-
 // Compaction of the parent samples that carry weight: kept = w_p[kp] >
 // rel * max_kp w_p, in index order.  The dropped samples change the marginal
 // weights by less than K rel in total (the plan takes rel = 2^-40 for the FP32
 // path, ~1e-9 at K = 1024, and 2^-24 for the mixed-precision paths, ~6e-5,
-// both below the path's error).  cw = ln w_p - ln K of each kept
-// sample; the list is padded to a multiple of 16 with cw = -inf.
-__global__ void k_compact(LevelView par, int K, float rel) {
+// both below the path's error).  cw = ln w_p - ln Kc of each kept
+// sample (Kc = the child's sample count; K = the row length, K^2 for the
+// pairs of a split parent); the list is padded to a multiple of 16 with
+// cw = -inf.
+__global__ void k_compact(LevelView par, int K, int Kc, float rel) {
   const long long p = blockIdx.x;
   __shared__ float red[32];
   __shared__ int scan[1024];
@@ -707,7 +602,7 @@ __global__ void k_compact(LevelView par, int K, float rel) {
   }
   int pos = scan[threadIdx.x] - cnt;
   const int total = scan[blockDim.x - 1];
-  const float lnK = logf((float)K);
+  const float lnK = logf((float)Kc);
   for (int kp = k0; kp < k1; ++kp) {
     if (w[kp] > thr && w[kp] > 0.f) {
       par.cidx[p * K + pos] = kp;
@@ -723,236 +618,10 @@ __global__ void k_compact(LevelView par, int K, float rel) {
   if (threadIdx.x == 0) par.ccnt[p] = total;
 }
 
-cudaError_t launch_compact(const LevelView& parent, int K, float rel, cudaStream_t s) {
+cudaError_t launch_compact(const LevelView& parent, int K, float rel, cudaStream_t s, int Kc) {
   if (parent.n == 0) return cudaSuccess;
-  k_compact<<<(unsigned)parent.n, 256, 0, s>>>(parent, K, rel);
+  k_compact<<<(unsigned)parent.n, 256, 0, s>>>(parent, K, Kc > 0 ? Kc : K, rel);
   return cudaGetLastError();
-}
-
-// K5 (FP32): adjoint of the contraction = marginal weights (Eq. mmp with the
-// indicator moment; Sec. 3.2's source-term trick in closed form):
-//   w_e[k] = sum_kp w_p[kp] exp( S_e[kp][k] - log sum_k' exp S_e[kp][k'] ),
-// over the compacted parent samples.  One thread per child sample k; the kept
-// parent samples stream through shared memory with the per-(e, kp) shift
-// pc[kp] + ln w_p[kp] - ln K - lt[e][kp] folded in.  Elements whose parent
-// keeps more than max_eff samples are left to the tensor-core adjoint
-// (max_eff = 0: no limit).
-template <int MAXD>
-__global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView par, int K, int n_rt, int max_eff) {
-  __shared__ float pms[kChunk * MAXD];
-  __shared__ float pps[kChunk * MAXD];
-  __shared__ float pcs[kChunk];
-  const long long e = blockIdx.x / n_rt;
-  const int k = (blockIdx.x % n_rt) * blockDim.x + threadIdx.x;
-  const int D = v.D;
-  const long long p = v.parent[e];
-  const int n_eff = par.ccnt[p];
-  if (max_eff > 0 && n_eff > max_eff) return;  // uniform over the block
-  const bool act = k < K;
-  extern __shared__ float zc[];  // [blockDim][D+1]
-  const int k0 = (int)(blockIdx.x % n_rt) * blockDim.x;
-  stage_samples(v, e, K, k0, min((int)blockDim.x, K - k0), zc);
-  __syncthreads();
-  float zr[MAXD];
-#pragma unroll
-  for (int d = 0; d < MAXD; ++d) zr[d] = (act && d < D) ? zc[threadIdx.x * (D + 1) + d] : 0.f;
-  const float hk = act ? v.htil[e * K + k] : 0.f;
-  float acc = 0.f;
-  for (int j0 = 0; j0 < n_eff; j0 += kChunk) {
-    const int nj = min(kChunk, n_eff - j0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kChunk * MAXD; i += blockDim.x) {
-      const int j = i / MAXD, d = i % MAXD;
-      const bool ok = j < nj && d < D;
-      const int kp = ok ? par.cidx[p * K + j0 + j] : 0;
-      pms[i] = ok ? par.pm[(p * K + kp) * D + d] : 0.f;
-      pps[i] = ok ? par.pp[(p * K + kp) * D + d] : 0.f;
-    }
-    for (int j = threadIdx.x; j < kChunk; j += blockDim.x) {
-      float sh = -INFINITY;
-      if (j < nj) {
-        const int kp = par.cidx[p * K + j0 + j];
-        sh = par.pc[p * K + kp] + par.cw[p * K + j0 + j] - v.lt[e * K + kp];
-      }
-      pcs[j] = sh;
-    }
-    __syncthreads();
-    if (!act) continue;
-#pragma unroll 4
-    for (int j = 0; j < kChunk; ++j) {
-      const float c = pcs[j];
-      if (c == -INFINITY) continue;
-      float a = c + hk;
-#pragma unroll
-      for (int d = 0; d < MAXD; ++d) {
-        const float t = zr[d] - pms[j * MAXD + d];
-        a = fmaf(pps[j * MAXD + d], t * t, a);
-      }
-      acc += expf(a);
-    }
-  }
-  if (act) v.w[e * K + k] = acc;
-}
-
-// Small-set adjoint with its own normaliser (used when the forward ran at a
-// different precision): one block per element; for each of the <= kSmallKept
-// kept parent samples the log-factor of every child sample is evaluated once
-// in FP32 (log2 units, kept in shared memory), its row normaliser
-// log sum_k exp S[kp][k] is reduced over the block (maximum, then the sum of
-// 2^(a - max)), and the marginal weights follow, so every row of P(k | kp)
-// sums to one in the arithmetic that evaluates it.  Elements whose parent
-// keeps more samples are left to the tensor-core adjoint.
-template <int MAXD>
-__global__ void __launch_bounds__(256) k_adj_small(LevelView v, LevelView par, int K) {
-  extern __shared__ float dyn[];
-  float* zc = dyn;                          // [256][D+1] staged samples
-  float* av = zc + 256 * (v.D + 1);         // [kSmallKept][K] log-factors (log2 units)
-  __shared__ float pms[kSmallKept * MAXD];
-  __shared__ float pps[kSmallKept * MAXD];
-  __shared__ float pcs[kSmallKept];
-  __shared__ float red[kSmallKept][8];
-  __shared__ float colmax[kSmallKept];
-  __shared__ float shift[kSmallKept];
-  constexpr float kL2e = 1.4426950408889634f;
-  const long long e = blockIdx.x;
-  const int D = v.D;
-  const long long p = v.parent[e];
-  const int n_eff = par.ccnt[p];
-  if (n_eff > kSmallKept) return;
-  for (int i = threadIdx.x; i < kSmallKept * MAXD; i += blockDim.x) {
-    const int j = i / MAXD, d = i % MAXD;
-    const bool ok = j < n_eff && d < D;
-    const int kp = ok ? par.cidx[p * K + j] : 0;
-    pms[i] = ok ? par.pm[(p * K + kp) * D + d] : 0.f;
-    pps[i] = ok ? kL2e * par.pp[(p * K + kp) * D + d] : 0.f;
-  }
-  if (threadIdx.x < kSmallKept) {
-    const int j = threadIdx.x;
-    pcs[j] = j < n_eff ? kL2e * par.pc[p * K + par.cidx[p * K + j]] : 0.f;
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // pass 1: the log-factors of the kept parent samples (log2 units) from
-  // samples staged through shared memory, with each thread's running maximum
-  // per parent sample
-  float mx[kSmallKept];
-#pragma unroll
-  for (int j = 0; j < kSmallKept; ++j) mx[j] = -INFINITY;
-  for (int k0 = 0; k0 < K; k0 += blockDim.x) {
-    const int nk = min((int)blockDim.x, K - k0);
-    __syncthreads();
-    stage_samples(v, e, K, k0, nk, zc);
-    __syncthreads();
-    if ((int)threadIdx.x >= nk) continue;
-    const int k = k0 + threadIdx.x;
-    float zr[MAXD];
-#pragma unroll
-    for (int d = 0; d < MAXD; ++d) zr[d] = d < D ? zc[threadIdx.x * (D + 1) + d] : 0.f;
-    const float hk = kL2e * v.htil[e * K + k];
-#pragma unroll
-    for (int j = 0; j < kSmallKept; ++j) {
-      if (j < n_eff) {
-        float a = pcs[j] + hk;
-#pragma unroll
-        for (int d = 0; d < MAXD; ++d) {
-          const float t = zr[d] - pms[j * MAXD + d];
-          a = fmaf(pps[j * MAXD + d], t * t, a);
-        }
-        av[j * K + k] = a;
-        mx[j] = fmaxf(mx[j], a);
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kSmallKept; ++j) {
-    float m = mx[j];
-    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) red[j][warp] = m;
-  }
-  __syncthreads();
-  if (threadIdx.x < kSmallKept) {
-    float m = -INFINITY;
-    for (int w = 0; w < nw; ++w) m = fmaxf(m, red[threadIdx.x][w]);
-    colmax[threadIdx.x] = isfinite(m) ? m : 0.f;
-  }
-  __syncthreads();
-  // pass 2: row normalisers sum_k 2^(a - max) of each kept parent sample
-  float sm[kSmallKept];
-#pragma unroll
-  for (int j = 0; j < kSmallKept; ++j) sm[j] = 0.f;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-#pragma unroll
-    for (int j = 0; j < kSmallKept; ++j)
-      if (j < n_eff) sm[j] += exp2f(av[j * K + k] - colmax[j]);
-  }
-#pragma unroll
-  for (int j = 0; j < kSmallKept; ++j) {
-    float t = sm[j];
-    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[j][warp] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < kSmallKept) {
-    const int j = threadIdx.x;
-    float S = 0.f;
-    for (int w = 0; w < nw; ++w) S += red[j][w];
-    // log2 w_p - log2 sum_k 2^a[kp][k]   (cw = ln w_p - ln K)
-    shift[j] = j < n_eff ? kL2e * (par.cw[p * K + j] + logf((float)K)) - (colmax[j] + log2f(S)) : -INFINITY;
-  }
-  __syncthreads();
-  // pass 3: the marginal weights
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    float acc = 0.f;
-#pragma unroll
-    for (int j = 0; j < kSmallKept; ++j)
-      if (j < n_eff) acc += exp2f(av[j * K + k] + shift[j]);
-    v.w[e * K + k] = acc;
-  }
-}
-
-cudaError_t launch_adj_small(const LevelView& v, const LevelView& par, int K, cudaStream_t s) {
-  if (v.n == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)v.n;
-  const size_t sm = sizeof(float) * (256 * (size_t)(v.D + 1) + (size_t)kSmallKept * K);
-  if (v.D <= 4) k_adj_small<4><<<grid, 256, sm, s>>>(v, par, K);
-  else if (v.D <= 8) k_adj_small<8><<<grid, 256, sm, s>>>(v, par, K);
-  else if (v.D <= 20) k_adj_small<20><<<grid, 256, sm, s>>>(v, par, K);
-  else if (v.D <= 32) k_adj_small<32><<<grid, 256, sm, s>>>(v, par, K);
-  else k_adj_small<64><<<grid, 256, sm, s>>>(v, par, K);
-  return cudaGetLastError();
-}
-
-template <int MAXD>
-static cudaError_t adj_small_cfg(size_t sm) {
-  return cudaFuncSetAttribute(k_adj_small<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-}
-
-cudaError_t configure_adj_small(int D, int K) {
-  const size_t sm = sizeof(float) * (256 * (size_t)(D + 1) + (size_t)kSmallKept * K);
-  if (sm <= 48 * 1024) return cudaSuccess;
-  if (D <= 4) return adj_small_cfg<4>(sm);
-  if (D <= 8) return adj_small_cfg<8>(sm);
-  if (D <= 20) return adj_small_cfg<20>(sm);
-  if (D <= 32) return adj_small_cfg<32>(sm);
-  return adj_small_cfg<64>(sm);
-}
-
-template <int MAXD>
-static cudaError_t adj_compact_dispatch(const LevelView& v, const LevelView& par, int K, int max_eff, cudaStream_t s) {
-  const int thr = K >= kRowTile ? kRowTile : ((K + 31) / 32) * 32;
-  const int n_rt = (K + thr - 1) / thr;
-  k_adj_compact<MAXD><<<(unsigned)(v.n * n_rt), thr, sizeof(float) * thr * (size_t)(v.D + 1), s>>>(v, par, K, n_rt,
-                                                                                                  max_eff);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adj_compact(const LevelView& v, const LevelView& par, int K, int max_eff, cudaStream_t s) {
-  if (v.n == 0) return cudaSuccess;
-  if (v.D <= 4) return adj_compact_dispatch<4>(v, par, K, max_eff, s);
-  if (v.D <= 8) return adj_compact_dispatch<8>(v, par, K, max_eff, s);
-  if (v.D <= 20) return adj_compact_dispatch<20>(v, par, K, max_eff, s);
-  if (v.D <= 32) return adj_compact_dispatch<32>(v, par, K, max_eff, s);
-  return adj_compact_dispatch<64>(v, par, K, max_eff, s);
 }
 
 // ---------------------------------------------------------------------------

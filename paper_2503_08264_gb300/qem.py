@@ -48,6 +48,11 @@ def qem_estep(h, q_params, eps, seed: int, it: int, moments, log_pmp=None) -> No
     L.check(L.load().qem_estep(h, _ptr(q_params), _ptr(eps), seed, it, _ptr(moments), _ptr(log_pmp)), "qem_estep")
 
 
+def qem_estep_split_root(h, q_params, eps, seed: int, it: int, moments, log_pmp=None, root_weights=None) -> None:
+    L.check(L.load().qem_estep_split_root(h, _ptr(q_params), _ptr(eps), seed, it, _ptr(moments), _ptr(log_pmp),
+                                          _ptr(root_weights)), "qem_estep_split_root")
+
+
 def qem_mstep(h, moments, mean_params, q_params, lam: float, sched_p: float = 0.0, t: int = 1) -> None:
     L.check(L.load().qem_mstep(h, _ptr(moments), _ptr(mean_params), _ptr(q_params), lam, sched_p, t), "qem_mstep")
 
@@ -175,6 +180,19 @@ class Plan:
             log_pmp = torch.empty(self.n_inst, dtype=torch.float64, device=self.device)
         qem_estep(self.h, q, eps, seed, it, moments, log_pmp)
         return moments, log_pmp
+
+    def estep_split_root(self, q, eps=None, seed: int = 0, it: int = 0, moments=None, log_pmp=None,
+                         root_weights=None):
+        """E-step with the root's mean and log-variance halves as separate latents
+        (K^2 parent index pairs); returns (moments, log_pmp, root_weights [n_inst, 2, K])."""
+        if moments is None:
+            moments = torch.empty(self.q_len, dtype=torch.float64, device=self.device)
+        if log_pmp is None:
+            log_pmp = torch.empty(self.n_inst, dtype=torch.float64, device=self.device)
+        if root_weights is None:
+            root_weights = torch.empty((self.n_inst, 2, self.K), dtype=torch.float32, device=self.device)
+        qem_estep_split_root(self.h, q, eps, seed, it, moments, log_pmp, root_weights)
+        return moments, log_pmp, root_weights
 
     def log_pmp_fresh(self, q, seed: int, it: int, log_pmp=None):
         """log P_MP of q from a fresh draw of the samples (device double [n_inst])."""
