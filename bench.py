@@ -65,6 +65,8 @@ def parse(argv=None):
                    help="reference arm: total oracle time the samples are sized for")
     p.add_argument("--metric", choices=["pairs", "time_to_tol"], default="pairs",
                    help="pairs: E-step throughput (default); time_to_tol: the warm-start study")
+    p.add_argument("--root", choices=["grouped", "split"], default="grouped",
+                   help="split: the root's mean and log-variance as separate latents (K^2 parent pairs)")
     p.add_argument("--train-instances", type=int, default=2000)
     p.add_argument("--test-instances", type=int, default=16)
     return p.parse_args(argv)
@@ -620,12 +622,96 @@ def run_ours(args):
     return 0
 
 
+def run_split_root(args):
+    """E-step + M-step with the split root (qem_estep_split_root): pairs per
+    step = users x K^2 parent pairs x K child samples.  One GPU; FP32."""
+    import torch
+
+    from paper_2503_08264_gb300 import qem
+
+    builder, K, _ = WORKLOADS[args.workload]
+    model = builder(1000)
+    if len(model.levels) != 2 or model.levels[1].prior != S.PRIOR_NORMAL_MEAN_LOGVAR:
+        raise SystemExit("--root split needs a two-level mean/log-variance model")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan = qem.Plan(model, K, precision="fp32", stream=stream)
+        q_d = plan.flat(S.initial_q(model))
+        m_d = plan.mean_params(q_d)
+        mom_d = torch.empty(plan.q_len, dtype=torch.float64, device="cuda")
+        lp_d = torch.empty(plan.n_inst, dtype=torch.float64, device="cuda")
+        rw_d = torch.empty((plan.n_inst, 2, K), dtype=torch.float32, device="cuda")
+    n_users = model.levels[1].n
+    pairs = float(n_users) * K ** 3
+    seed = 4321
+
+    def step(t):
+        plan.estep_split_root(q_d, None, seed=seed, it=t, moments=mom_d, log_pmp=lp_d, root_weights=rw_d)
+        plan.mstep(mom_d, m_d, q_d, EMA_LAMBDA, t=t)
+
+    t_iter = 1
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(t_iter)
+            t_iter += 1
+    stream.synchronize()
+    plan.log_pmp()
+    clocks = ClockSampler(0)
+    clocks.start()
+    plan.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(t_iter)
+            t_iter += 1
+        ev1.record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = plan.profile_read()
+    plan.profile(False)
+    lp_host = plan.log_pmp()
+    sm_max = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    f_ms, f_n = prof["forward"]
+    roof = roofline_for("forward", "fp32", model.levels[1].dim, pairs * f_n, f_ms, sm_max)
+    roof["traffic"] = None
+    roof["share_of_step"] = f_ms / ms if ms else None
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import split_root as R
+        m_s = max(1, min(n_users, 40))
+        sub = S.hier_logistic(M=m_s, N=model.levels[1].n_obs, D=model.levels[1].dim, seed=7)
+        q_s = S.initial_q(sub)
+        eps_s = S.noise(sub, K, seed=8)
+        t0 = time.perf_counter()
+        R.estep(sub, q_s, K, eps_s)
+        dt = time.perf_counter() - t0
+        cpu = {"value": m_s * K ** 3 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 split-root E-step of {m_s} users (numpy; the oracle's BLAS may use more "
+                         f"threads), {dt:.1f} s"}
+    line = {"metric": METRIC, "value": pairs * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "root": "split (mean and log-variance as separate latents)",
+                       "K": K, "pairs_per_step_per_gpu": pairs, "precision": "fp32",
+                       "noise": "in-kernel Philox4x32-10",
+                       "step": "qem_estep_split_root + qem_mstep (one Alg. 1 iteration)"},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "kernels_ms": {k: round(v[0], 4) for k, v in prof.items()}, "log_pmp_last": float(lp_host[0])}
+    print(json.dumps(line))
+    plan.close()
+    return 0
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.metric == "time_to_tol":
         return run_time_to_tol(args)
+    if args.root == "split":
+        return run_split_root(args)
     return run_ours(args)
 
 

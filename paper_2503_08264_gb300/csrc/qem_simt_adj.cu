@@ -33,8 +33,8 @@ __device__ __forceinline__ void stage_samples(const LevelView& v, long long e, i
 // K^2 entries per element.
 template <int MAXD, bool SPLIT>
 __global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView par, int K, int n_rt, int max_eff) {
-  __shared__ float pms[kChunk * MAXD];
-  __shared__ float pps[kChunk * MAXD];
+  constexpr int DP = MAXD / 2;       // dimension pairs
+  __shared__ float4 pq[kChunk * DP];  // per kept parent sample and pair: (pm_d, pm_d+1, pp_d, pp_d+1)
   __shared__ float pcs[kChunk];
   const long long e = blockIdx.x / n_rt;
   const int k = (blockIdx.x % n_rt) * blockDim.x + threadIdx.x;
@@ -56,13 +56,22 @@ __global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView
   for (int j0 = 0; j0 < n_eff; j0 += kChunk) {
     const int nj = min(kChunk, n_eff - j0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kChunk * MAXD; i += blockDim.x) {
-      const int j = i / MAXD, d = i % MAXD;
-      const bool ok = j < nj && d < D;
-      const int kp = ok ? par.cidx[p * Kp + j0 + j] : 0;
-      const int ka = SPLIT ? kp / K : kp, kb = SPLIT ? kp % K : kp;
-      pms[i] = ok ? par.pm[(p * K + ka) * D + d] : 0.f;
-      pps[i] = ok ? par.pp[(p * K + kb) * D + d] : 0.f;
+    for (int i = threadIdx.x; i < kChunk * DP; i += blockDim.x) {
+      const int j = i / DP, d = 2 * (i % DP);
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < nj && d < D) {
+        const int kp = par.cidx[p * Kp + j0 + j];
+        const int ka = SPLIT ? kp / K : kp, kb = SPLIT ? kp % K : kp;
+        const float* pm = par.pm + (p * K + ka) * D;
+        const float* pp = par.pp + (p * K + kb) * D;
+        t.x = pm[d];
+        t.z = pp[d];
+        if (d + 1 < D) {
+          t.y = pm[d + 1];
+          t.w = pp[d + 1];
+        }
+      }
+      pq[i] = t;
     }
     for (int j = threadIdx.x; j < kChunk; j += blockDim.x) {
       float sh = -INFINITY;
@@ -79,13 +88,18 @@ __global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView
     for (int j = 0; j < kChunk; ++j) {
       const float c = pcs[j];
       if (c == -INFINITY) continue;
-      float a = c + hk;
+      // dimensions in pairs (packed FP32, one 16-byte shared load per pair):
+      // a += pp_d (z_d - pm_d)^2
+      float a0 = c + hk, a1 = 0.f;
 #pragma unroll
-      for (int d = 0; d < MAXD; ++d) {
-        const float t = zr[d] - pms[j * MAXD + d];
-        a = fmaf(pps[j * MAXD + d], t * t, a);
+      for (int dp = 0; dp < DP; ++dp) {
+        const float4 t = pq[j * DP + dp];
+        float t0, t1, q0, q1;
+        diff2(t0, t1, zr[2 * dp], zr[2 * dp + 1], t.x, t.y);
+        mul2(q0, q1, t0, t1, t0, t1);
+        fma2(a0, a1, t.z, t.w, q0, q1);
       }
-      acc += expf(a);
+      acc += expf(a0 + a1);
     }
   }
   if (act) v.w[e * K + k] = acc;
