@@ -184,3 +184,54 @@ def estep_instance_split_root(model, q, z, K: int, inst: int = 0) -> dict:
         out["w"][e] = marg[2 + j]
         out["mom"][e] = np.stack([marg[2 + j] @ ze, marg[2 + j] @ ze ** 2])
     return out
+
+
+def estep_instance_chain(model, q, z, K: int, inst: int = 0) -> dict:
+    """Enumeration for a two-level model whose leaf level is a chain plate.
+
+    Latents: the instance's root and every (region, day) element of its
+    chains (element c T + d), each with its own index.  The first day of a
+    region takes the level's prior given the root sample; day d >= 1 takes
+    N(z_{c,d-1}, prior_b I).  Returns log_pmp, w / mom keyed by (level,
+    element), n.
+    """
+    r, u = model.levels
+    T = int(u.chain)
+    elems = [int(e) for e in np.nonzero(np.asarray(u.parent) == inst)[0]]
+    lat = [(0, inst)] + [(1, e) for e in elems]
+    idx = {le: i for i, le in enumerate(lat)}
+    n = len(lat)
+    unary = np.zeros((n, K))
+    pair = {}
+    for i, (l, e) in enumerate(lat):
+        lv = model.levels[l]
+        for k in range(K):
+            zk = np.asarray(z[l][e, k], np.float64)
+            unary[i, k] = _log_lik(lv, e, zk) - _log_q(lv, q[l][e], zk) + (_log_prior(lv, zk, None) if l == 0 else 0.0)
+        if l == 1:
+            first = e % T == 0
+            pi = idx[(0, inst)] if first else idx[(1, e - 1)]
+            f = np.zeros((K, K))
+            for kp in range(K):
+                zp = np.asarray(z[0][inst, kp] if first else z[1][e - 1, kp], np.float64)
+                for k in range(K):
+                    zk = np.asarray(z[1][e, k], np.float64)
+                    f[kp, k] = (_log_prior(u, zk, zp) if first
+                                else stats.norm.logpdf(zk, zp, math.sqrt(u.prior_b)).sum())
+            pair[i] = (pi, f)
+    combos = np.array(list(itertools.product(range(K), repeat=n)))
+    logr = np.zeros(len(combos))
+    for i in range(n):
+        logr += unary[i][combos[:, i]]
+    for i, (pi, f) in pair.items():
+        logr += f[combos[:, pi], combos[:, i]]
+    mx = logr.max()
+    terms = np.exp(logr - mx)
+    tot = math.fsum(terms)
+    w, mom = {}, {}
+    for i, (l, e) in enumerate(lat):
+        wi = np.array([math.fsum(terms[combos[:, i] == k]) for k in range(K)]) / tot
+        w[(l, e)] = wi
+        ze = np.asarray(z[l][e], np.float64)
+        mom[(l, e)] = np.stack([wi @ ze, wi @ ze ** 2])
+    return {"log_pmp": mx + math.log(tot) - n * math.log(K), "w": w, "mom": mom, "n": n}

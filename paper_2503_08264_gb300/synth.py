@@ -20,6 +20,13 @@ App. F.2) and the conjugate hierarchies used to pin the estimator:
 * ``batched_three_level`` mu~N(0,I_8), z_g~N(mu,I), z_u~N(z_g,0.5^2 I), y~Pois(exp(w.z_u))
 * ``gamma_poisson`` / ``beta_bernoulli``  single-latent conjugate pairs for the
   Gamma and Beta proposal families.
+* ``chain_poisson``       g~N(0,I); per region a daily random walk z_{c,0}~N(g,a I),
+  z_{c,d}~N(z_{c,d-1},b I); y~Pois(exp(z.x)) (the Covid model's chain plate, App. F)
+
+A chain level (``chain`` = T > 1, the leaf level of a two-level model) holds
+T consecutive elements per region, element c T + d for day d; all T share the
+region's parent, the first day's prior is the level's prior given the parent
+and every later day's is N(previous day, prior_b I).
 """
 from __future__ import annotations
 
@@ -65,6 +72,7 @@ class Level:
     parent: np.ndarray | None = None   # int64 [n], non-decreasing
     x: np.ndarray | None = None        # float32 [n, n_obs, dim]
     y: np.ndarray | None = None        # float32 [n, n_obs]
+    chain: int = 1                     # T > 1: elements form chains of T days (leaf level)
 
     def noise_per_sample(self) -> int:
         """Number of N(0,1)/U(0,1) numbers one sample of this level consumes."""
@@ -204,6 +212,37 @@ def beta_bernoulli(n_inst: int = 4, N: int = 20, a0: float = 2.0, b0: float = 3.
                  lik=LIK_BERNOULLI_PROB, n_obs=N, qfam=Q_BETA,
                  x=np.ones((n_inst, N, 1), np.float32), y=y)
     return Model([root], name="beta_bernoulli", truth={"theta": th})
+
+
+def chain_poisson(n_inst: int = 1, R: int = 92, T: int = 109, D: int = 1, seed: int = 0, first_var: float = 0.5,
+                  step_var: float = 0.05, n_obs: int = 1, lik: int = LIK_POISSON_LOG, lik_var: float = 1.0) -> Model:
+    """Daily random walks under a global latent (the Covid model's chain plate,
+    App. F, with Poisson counts in place of its negative binomial):
+    g ~ N(0, I_D) per instance; per region c, z_{c,0} ~ N(g, first_var I),
+    z_{c,d} ~ N(z_{c,d-1}, step_var I); y_{c,d,n} ~ Poisson(exp(z_{c,d} . x)) with
+    x = 1 for D = 1 and x ~ N(0, I/D) otherwise (or Gaussian y, lik = LIK_GAUSS)."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((n_inst, D))
+    z = np.empty((n_inst, R, T, D))
+    z[:, :, 0] = g[:, None, :] + np.sqrt(first_var) * rng.standard_normal((n_inst, R, D))
+    for d in range(1, T):
+        z[:, :, d] = z[:, :, d - 1] + np.sqrt(step_var) * rng.standard_normal((n_inst, R, D))
+    n = n_inst * R * T
+    z = z.reshape(n, D)
+    if D == 1:
+        x = np.ones((n, n_obs, 1), np.float32)
+    else:
+        x = (rng.standard_normal((n, n_obs, D)) / np.sqrt(D)).astype(np.float32)
+    s = np.einsum("end,ed->en", x.astype(np.float64), z)
+    if lik == LIK_GAUSS:
+        y = (s + np.sqrt(lik_var) * rng.standard_normal(s.shape)).astype(np.float32)
+    else:
+        y = rng.poisson(np.exp(np.minimum(s, 20.0))).astype(np.float32)
+    root = Level(n=n_inst, dim=D, prior=PRIOR_STD_NORMAL, prior_a=1.0)
+    days = Level(n=n, dim=D, prior=PRIOR_NORMAL_FIXED_VAR, prior_a=first_var, prior_b=step_var, lik=lik,
+                 lik_var=lik_var, n_obs=n_obs, parent=np.repeat(np.arange(n_inst, dtype=np.int64), R * T),
+                 x=x, y=y, chain=T)
+    return Model([root, days], name=f"chain_poisson_R{R}_T{T}", truth={"g": g, "z": z})
 
 
 def subset(model: Model, inst_ids) -> tuple:
