@@ -45,6 +45,8 @@ WORKLOADS = {
     # profiling case: the large workload's shapes with a fifth of its plate (fits an ncu capture)
     "hier_logistic_M1000_N10_K1024": (lambda seed: S.hier_logistic(M=1000, N=10, seed=seed), 1024, "bf16x3"),
     "batched_three_level_256_K256": (lambda seed: S.batched_three_level(n_inst=256, seed=seed), 256, "bf16x3"),
+    # the Covid model's chain plate: 92 regions x 109 days of a random walk under a global latent
+    "chain_poisson_R92_T109_K128": (lambda seed: S.chain_poisson(R=92, T=109, seed=seed), 128, "fp32"),
 }
 DEFAULT_WORKLOAD = "hier_logistic_M5000_N10_K1024"
 EMA_LAMBDA = 0.5
@@ -226,23 +228,28 @@ def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7):
     The sample keeps the workload's shapes (K, dimensions, observations per
     element) and takes a prefix of its plate elements (2-level workloads) or a
     smaller batch of instances (batched workloads), sized from a short
-    calibration run so that the timed run takes about target_s seconds."""
+    calibration run so that the timed run takes about target_s seconds.
+    Chain workloads take whole regions and the chain oracle (numpy, one
+    thread for its own loops)."""
     import numpy as np
     from oracle import oracle as O
     O.build()
     builder, K, _ = WORKLOADS[workload]
     full = builder(seed)
     two_level = len(full.levels) == 2
-    total = full.levels[1].n if two_level else full.n_inst
+    T = int(getattr(full.levels[1], "chain", 1) or 1) if two_level else 1
+    total = full.levels[1].n // T if two_level else full.n_inst
 
     def sub(count):
         count = int(max(1, min(total, count)))
         if two_level:
             lv = full.levels[1]
-            users = S.Level(n=count, dim=lv.dim, prior=lv.prior, prior_a=lv.prior_a, lik=lv.lik,
+            n = count * T
+            users = S.Level(n=n, dim=lv.dim, prior=lv.prior, prior_a=lv.prior_a, prior_b=lv.prior_b, lik=lv.lik,
                             lik_var=lv.lik_var, n_obs=lv.n_obs, qfam=lv.qfam,
-                            parent=np.zeros(count, np.int64), x=lv.x[:count], y=lv.y[:count])
-            return S.Model([full.levels[0], users]), f"{count} of {total} plate elements"
+                            parent=np.zeros(n, np.int64), x=lv.x[:n], y=lv.y[:n], chain=T)
+            what = "regions" if T > 1 else "plate elements"
+            return S.Model([full.levels[0], users]), f"{count} of {total} {what}"
         return S.batched_three_level(n_inst=count, seed=seed), f"{count} of {total} instances"
 
     # grow the sample until one run takes at least 60% of the target (the
@@ -250,15 +257,29 @@ def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7):
     count = 4 if two_level else 1
     for _ in range(5):
         model, desc = sub(count)
-        t0 = time.perf_counter()
-        O.estep(model, S.initial_q(model), K, seed=1, it=1)
-        t = time.perf_counter() - t0
+        t = oracle_estep_seconds(model, K, 1)
         if t >= 0.6 * target_s or count >= total:
             break
         count = min(total, count * min(50.0, target_s / max(t, 1e-3)))
     pairs = model.pairs(K)
-    return {"value": pairs / t, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
-            "sample": f"one FP64 E-step on {desc} of {workload} (counter-based noise), {t:.1f} s"}, model
+    cores = 1 if T > 1 else O.max_threads()
+    noise = "supplied noise" if T > 1 else "counter-based noise"
+    return {"value": pairs / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one FP64 E-step on {desc} of {workload} ({noise}), {t:.1f} s"}, model
+
+
+def oracle_estep_seconds(model, K: int, it: int) -> float:
+    """Seconds of one FP64 oracle E-step of `model` (the chain oracle for chain plates)."""
+    if len(model.levels) == 2 and int(getattr(model.levels[1], "chain", 1) or 1) > 1:
+        from oracle import chain as C
+        eps = S.noise(model, K, seed=it)
+        t0 = time.perf_counter()
+        C.estep(model, S.initial_q(model), K, eps)
+        return time.perf_counter() - t0
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.estep(model, S.initial_q(model), K, seed=1, it=it)
+    return time.perf_counter() - t0
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -274,10 +295,9 @@ def run_reference(args):
     base, model = cpu_oracle_sample(args.workload, per_step)
     times = []
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        O.estep(model, S.initial_q(model), K, seed=1, it=i + 1)
+        t = oracle_estep_seconds(model, K, i + 1)
         if i >= args.warmup:
-            times.append(time.perf_counter() - t0)
+            times.append(t)
     pairs = model.pairs(K)
     value = pairs * len(times) / sum(times)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

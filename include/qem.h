@@ -100,6 +100,14 @@ typedef struct {
   const int64_t* parent;/* HOST [n]: parent element at level-1, non-decreasing; NULL at level 0 */
   const float* x;       /* DEVICE [n][n_obs][dim] covariates (read at every E-step)            */
   const float* y;       /* DEVICE [n][n_obs] observations                                      */
+  int chain;            /* 0 or 1: plain plate.  T > 1: a chain plate (App. F's Covid model:
+                         * a daily autoregressive timeseries per region): the level's elements
+                         * are n / T regions of T consecutive days, element c*T + d, each day
+                         * its own latent; the T elements of a region share its parent; day 0
+                         * takes the level's prior given the parent, day d >= 1 the prior
+                         * N(z_{c,d-1}, prior_b I).  Only as level 1 of a two-level model,
+                         * with a FP32 plan, a Gaussian proposal, dim <= 8 and K <= 1024
+                         * (QEM_ERR_UNSUPPORTED otherwise).                                    */
 } qem_level_desc;
 
 typedef struct {

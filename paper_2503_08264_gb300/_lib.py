@@ -25,7 +25,7 @@ class LevelDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("dim", C.c_int), ("prior", C.c_int),
                 ("prior_a", C.c_double), ("prior_b", C.c_double),
                 ("lik", C.c_int), ("lik_var", C.c_double), ("n_obs", C.c_int), ("qfam", C.c_int),
-                ("parent", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p)]
+                ("parent", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p), ("chain", C.c_int)]
 
 
 class ModelDesc(C.Structure):

@@ -61,6 +61,15 @@ qem_status validate(const qem_model_desc* desc, const qem_plan_opts* o) {
         (d.lik == QEM_LIK_BERNOULLI_PROB && (d.qfam != QEM_Q_BETA || d.dim != 1)))
       return QEM_ERR_INVALID_ARG;
     if (L > 1 && d.qfam != QEM_Q_GAUSS) return QEM_ERR_UNSUPPORTED;
+    if (d.chain < 0) return QEM_ERR_INVALID_ARG;
+    if (d.chain > 1) {
+      if (l != 1 || L != 2 || o->precision != QEM_PREC_FP32 || d.dim > 8 || d.qfam != QEM_Q_GAUSS || o->K > 1024)
+        return QEM_ERR_UNSUPPORTED;
+      if (d.n % d.chain != 0 || !(d.prior_b > 0)) return QEM_ERR_INVALID_ARG;
+      if (d.n > 0 && d.parent)
+        for (int64_t e = 0; e < d.n; ++e)
+          if (d.parent[e] != d.parent[e - e % d.chain]) return QEM_ERR_INVALID_ARG;
+    }
     if (l == 0) {
       if (d.parent) return QEM_ERR_INVALID_ARG;
       if (d.prior == QEM_PRIOR_STD_NORMAL) {
@@ -170,7 +179,9 @@ qem_status estep_forward(qem_plan_t P, const float* q, const float* eps, double*
   for (int l = L - 1; l >= 1; --l) {
     const bool has_children = l + 1 < L;
     if (has_children) QEM_LAUNCH(P, QEM_K_FINALIZE, launch_finalize(P->lv[l], K, has_children, s));
-    if (P->precision == QEM_PREC_FP32) {
+    if (P->lv[l].chain > 1) {
+      QEM_LAUNCH(P, QEM_K_FORWARD, launch_chain_forward(P->lv[l], P->lv[l - 1], K, s));
+    } else if (P->precision == QEM_PREC_FP32) {
       QEM_LAUNCH(P, QEM_K_FORWARD, launch_fwd_simt(P->lv[l], P->lv[l - 1], K, P->tune.fwd_rows, P->tune.fwd_chunk, s));
     } else {
       QEM_LAUNCH(P, QEM_K_OPERANDS, tc_features(P, l));
@@ -191,6 +202,10 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
   cudaStream_t s = P->stream;
   const int L = P->L, K = P->K;
   for (int l = 1; l < L; ++l) {
+    if (P->lv[l].chain > 1) {
+      QEM_LAUNCH(P, QEM_K_ADJOINT, launch_chain_adjoint(P->lv[l], P->lv[l - 1], K, s));
+      continue;
+    }
     // parent samples below rel * the largest weight are dropped from the
     // adjoint: 2^-40 on the FP32 path, 2^-24 on the mixed-precision paths
     const float rel = P->precision == QEM_PREC_FP32 ? 9.094947017729282e-13f : 5.9604644775390625e-08f;
@@ -557,6 +572,7 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
       lv.qfam = d.qfam;
       lv.nps = noise_per_sample(d);
       lv.level = l;
+      lv.chain = d.chain > 1 ? d.chain : 1;
       lv.x = d.x;
       lv.y = d.y;
       lv.Dc = has_children ? desc->levels[l + 1].dim : 0;
@@ -572,6 +588,7 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
       lv.off = has_children ? cv.take<double>((size_t)d.n) : nullptr;
       lv.lt = l > 0 ? cv.take<float>(nK) : nullptr;
       lv.w = cv.take<float>(nK);
+      lv.beta = d.chain > 1 ? cv.take<float>(nK) : nullptr;
       lv.pm = has_children ? cv.take<float>(nK * lv.Dc) : nullptr;
       lv.pp = has_children ? cv.take<float>(nK * lv.Dc) : nullptr;
       lv.pc = has_children ? cv.take<float>(nK) : nullptr;
@@ -699,7 +716,7 @@ qem_status qem_estep_split_root(qem_plan_t P, const float* q_params, const float
   const LevelView& r = P->lv[0];
   const LevelView& u = P->lv[1];
   if (r.prior != QEM_PRIOR_STD_NORMAL || r.qfam != QEM_Q_GAUSS || r.lik != QEM_LIK_NONE ||
-      u.prior != QEM_PRIOR_NORMAL_MEAN_LOGVAR || r.D != 2 * u.D || u.D > 32 || P->K > 1024)
+      u.prior != QEM_PRIOR_NORMAL_MEAN_LOGVAR || r.D != 2 * u.D || u.D > 32 || u.chain > 1 || P->K > 1024)
     return QEM_ERR_UNSUPPORTED;
   qem_status st = split_alloc(P);
   if (st != QEM_OK) return st;

@@ -43,6 +43,7 @@ struct LevelView {
   int qfam;
   int nps;            // noise numbers per sample
   int level;          // index of this level
+  int chain;          // days per region of a chain plate (1: plain plate)
   const float* x;     // [n][n_obs][D]
   const float* y;     // [n][n_obs]
   const long long* parent;     // [n] (level > 0)
@@ -58,6 +59,7 @@ struct LevelView {
   double* off;        // [n]     constant removed from htil
   float* lt;          // [n][K]  (level > 0) relative log mean_k exp S_e[kp][k], per parent sample kp
   float* w;           // [n][K]  marginal weights
+  float* beta;        // [n][K]  chain plates: relative log mean_k exp S of day d >= 1 per sample of day d-1
   // conditional parameters of this level's children given each of its samples
   float* pm;          // [n][K][Dc] child-prior mean
   float* pp;          // [n][K][Dc] -0.5 * child-prior precision
@@ -343,6 +345,10 @@ cudaError_t launch_split_unary(const LevelView& root, int K, const float* q, dou
 cudaError_t launch_split_root(int n_inst, int K, const double* fa, const double* fb, const double* hsum, float* W,
                               float* wab, float* w0, double* log_pmp, double* user_out, Ctl* ctl, cudaStream_t s);
 cudaError_t launch_split_root_moments(const LevelView& root, int K, const float* wab, double* mom, cudaStream_t s);
+// Chain plates (qem_chain.cu): the forward over each region's days and the
+// root-to-leaf adjoint; one block per region.
+cudaError_t launch_chain_forward(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
+cudaError_t launch_chain_adjoint(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
 cudaError_t launch_predictive(const LevelView& v, int K, const float* xn, const float* yn, int nn, double* out,
                               cudaStream_t s);
 

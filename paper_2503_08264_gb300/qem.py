@@ -125,6 +125,7 @@ class Plan:
             d.n, d.dim, d.prior = lv.n, lv.dim, lv.prior
             d.prior_a, d.prior_b = float(lv.prior_a), float(lv.prior_b)
             d.lik, d.lik_var, d.n_obs, d.qfam = lv.lik, float(lv.lik_var), lv.n_obs if lv.lik else 0, lv.qfam
+            d.chain = int(getattr(lv, "chain", 1) or 1)
             if lv.parent is not None:
                 par = np.ascontiguousarray(lv.parent, np.int64)
                 self._keep.append(par)

@@ -76,6 +76,10 @@ def _child(**kw):
     ([ROOT_LV, _child(parent=None)], 8),                       # missing parents
     ([dict(ROOT_LV, prior=1)], 8),                             # root with a parent-relative prior
     ([dict(ROOT_LV, n=-1)], 8),                                # negative size
+    ([ROOT_LV, _child(n=4, parent=[0] * 4, chain=3, prior_b=0.1)], 8),          # days not whole chains
+    ([ROOT_LV, _child(n=4, parent=[0] * 4, chain=2)], 8),                        # chain without a step variance
+    ([dict(ROOT_LV, n=2), _child(n=4, parent=[0, 0, 0, 1], chain=2, prior_b=0.1)], 8),  # parent changes in a chain
+    ([ROOT_LV, _child(chain=-1)], 8),                          # negative chain length
 ])
 def test_invalid_descriptors_rejected_on_host(lib, levels, K):
     d, keep = _desc(levels)
@@ -90,6 +94,9 @@ def test_invalid_descriptors_rejected_on_host(lib, levels, K):
 @pytest.mark.parametrize("levels", [
     [dict(ROOT_LV, dim=65)],                                                            # dimension too large
     [dict(ROOT_LV, dim=1, qfam=1, prior=3, prior_a=2.0, prior_b=1.0), _child(dim=1)],  # Gamma q inside a tree
+    [dict(ROOT_LV, chain=2)],                                                           # chain at the root
+    [ROOT_LV, _child(n=4, parent=[0] * 4, chain=2, prior_b=0.1), _child(n=1, parent=[0])],  # chain not the leaf
+    [dict(ROOT_LV, dim=9), _child(n=4, dim=9, parent=[0] * 4, chain=2, prior_b=0.1)],   # chain dimension above 8
 ])
 def test_unsupported_requests(lib, levels):
     d, keep = _desc(levels)
@@ -104,3 +111,15 @@ def test_null_arguments(lib):
     assert lib.qem_estep(None, None, None, 0, 0, None, None) == L.QEM_ERR_INVALID_ARG
     assert lib.qem_mstep(None, None, None, None, 0.5, 0.0, 1) == L.QEM_ERR_INVALID_ARG
     assert lib.qem_plan_destroy(None) == L.QEM_OK
+
+
+def test_chain_plans_need_the_fp32_path(lib):
+    d, keep = _desc([ROOT_LV, _child(n=4, parent=[0] * 4, chain=2, prior_b=0.1)])
+    o = L.PlanOpts()
+    o.K = 128
+    o.precision = L.QEM_PREC_BF16X3
+    h = C.c_void_p()
+    assert lib.qem_plan(C.byref(d), C.byref(o), C.byref(h)) == L.QEM_ERR_UNSUPPORTED
+    o.precision = L.QEM_PREC_FP32
+    o.K = 2048
+    assert lib.qem_plan(C.byref(d), C.byref(o), C.byref(h)) == L.QEM_ERR_UNSUPPORTED
