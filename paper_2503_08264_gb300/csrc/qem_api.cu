@@ -585,7 +585,7 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
       lv.ltab = d.lik == QEM_LIK_POISSON_LOG ? P->count_tab : nullptr;
       lv.htil = has_children ? cv.take<float>(nK) : lv.loc;
       lv.hsum = has_children ? cv.take<double>(nK) : nullptr;
-      lv.off = has_children ? cv.take<double>((size_t)d.n) : nullptr;
+      lv.off = (has_children || d.chain > 1) ? cv.take<double>((size_t)d.n) : nullptr;
       lv.lt = l > 0 ? cv.take<float>(nK) : nullptr;
       lv.w = cv.take<float>(nK);
       lv.beta = d.chain > 1 ? cv.take<float>(nK) : nullptr;

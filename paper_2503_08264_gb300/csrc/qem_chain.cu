@@ -12,10 +12,16 @@
 //     w_0[k] = sum_p w_par[p] exp(S_0[p][k] - lt_0[p] - log K),
 //     w_d[k] = sum_j w_{d-1}[j] exp(S_d[j][k] - beta_d[j] - log K).
 // h = the relative local factor htil (the sampler's shift joins cst, which
-// the plate sum adds for every day); lt of days >= 1 is written 0 so that the
-// parent's plate sum takes lt_0 plus every day's constant.  One block per
-// region, one thread per row (forward) or per sample (adjoint), K <= 1024;
-// the column samples stream through shared memory in chunks.
+// the plate sum adds for every day).  beta_d accumulates the evidence of all
+// later days, so its size grows along the chain; each day's beta is stored
+// relative to its maximum over j, the maximum kept in FP64 in the day's off
+// (the parent's plate sum adds lt + off + cst of every element, and lt of
+// days >= 1 is written 0), so every FP32 argument of an exponential stays near
+// zero for the samples that carry weight.  The shifts are constant over each
+// day's rows and columns, so the adjoint drops them and renormalises each
+// day's weights to sum to one (exact: every row of P(k | j) sums to one).
+// One block per region, one thread per row (forward) or per sample
+// (adjoint), K <= 1024; the column samples stream through shared memory.
 #include <math.h>
 
 #include "qem_internal.cuh"
@@ -25,11 +31,32 @@ namespace qem {
 constexpr int kChainChunk = 32;
 constexpr int kChainThreadsMax = 1024;
 
+// Block-wide maximum / sum (every thread of the block calls; red holds 32).
+__device__ __forceinline__ float chain_block_max(float x, float* red) {
+  for (int o = 16; o; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  float r = -INFINITY;
+  for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) r = fmaxf(r, red[w]);
+  __syncthreads();
+  return r;
+}
+__device__ __forceinline__ float chain_block_sum(float x, float* red) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  float r = 0.f;
+  for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) r += red[w];
+  __syncthreads();
+  return r;
+}
+
 template <int MAXD>
 __global__ void __launch_bounds__(kChainThreadsMax) k_chain_forward(LevelView v, LevelView par, int K) {
   constexpr int CH = MAXD > 2 ? 16 : kChainChunk;  // fits the 64 registers of a 1024-thread block
   __shared__ float zs[CH * MAXD];
   __shared__ float gs[CH];
+  __shared__ float red[32];
   const int T = v.chain, D = v.D;
   const long long e0 = (long long)blockIdx.x * T;
   const long long p = v.parent[e0];
@@ -95,14 +122,18 @@ __global__ void __launch_bounds__(kChainThreadsMax) k_chain_forward(LevelView v,
 #pragma unroll
       for (int jj = 0; jj < CH; ++jj) s += expf(val[jj] - m);
     }
-    if (act) {
-      const float r = pc + (m + logf(s) - lnK);
-      if (d > 0) {
-        v.beta[e * K + j] = r;
+    const float r = act ? pc + (m + logf(s) - lnK) : -INFINITY;
+    if (d > 0) {
+      float c = chain_block_max(r, red);
+      c = isfinite(c) ? c : 0.f;
+      if (act) {
+        v.beta[e * K + j] = r - c;
         v.lt[e * K + j] = 0.f;
-      } else {
-        v.lt[e * K + j] = r;
       }
+      if (threadIdx.x == 0) v.off[e] = (double)c;
+    } else {
+      if (act) v.lt[e * K + j] = r;
+      if (threadIdx.x == 0) v.off[e] = 0.0;
     }
     __syncthreads();  // beta of day d is complete before day d-1 stages it
   }
@@ -113,6 +144,7 @@ __global__ void __launch_bounds__(kChainThreadsMax) k_chain_adjoint(LevelView v,
   __shared__ float pms[kChainChunk * MAXD];
   __shared__ float pps[kChainChunk * MAXD];
   __shared__ float cfs[kChainChunk];
+  __shared__ float red[32];
   const int T = v.chain, D = v.D;
   const long long e0 = (long long)blockIdx.x * T;
   const long long p = v.parent[e0];
@@ -170,7 +202,8 @@ __global__ void __launch_bounds__(kChainThreadsMax) k_chain_adjoint(LevelView v,
         acc += expf(a0 + a1);
       }
     }
-    if (act) v.w[e * K + k] = acc;
+    const float tot = chain_block_sum(act ? acc : 0.f, red);
+    if (act) v.w[e * K + k] = tot > 0.f ? acc / tot : 0.f;
     __syncthreads();  // day d's weights are complete before day d+1 stages them
   }
 }

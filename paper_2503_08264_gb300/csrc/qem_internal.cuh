@@ -56,7 +56,7 @@ struct LevelView {
   const double* ltab; // [kCountTable] per-count Poisson-log constants (levels with that likelihood)
   float* htil;        // [n][K]  loc + children's sum - off  (relative local factor)
   double* hsum;       // [n][K]  sum over children of their log mean-exp (FP64)
-  double* off;        // [n]     constant removed from htil
+  double* off;        // [n]     constant removed from htil (chain plates: from that day's beta)
   float* lt;          // [n][K]  (level > 0) relative log mean_k exp S_e[kp][k], per parent sample kp
   float* w;           // [n][K]  marginal weights
   float* beta;        // [n][K]  chain plates: relative log mean_k exp S of day d >= 1 per sample of day d-1
