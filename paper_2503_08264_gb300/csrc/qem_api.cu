@@ -639,6 +639,8 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
   for (int l = 0; l < L; ++l) smem = std::max(smem, sample_local_smem(P->lv[l], K, kSampleThreadsLimit));
   if (ce == cudaSuccess) ce = configure_sample_local(smem);
   for (int l = 1; l < L && ce == cudaSuccess; ++l) ce = configure_adj_small(P->lv[l].D, K);
+  for (int l = 1; l < L && ce == cudaSuccess; ++l)
+    if (P->lv[l].chain > 1) ce = configure_chain(P->lv[l].D, K);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->stream);
   if (ce == cudaSuccess) {
     st = tc_plan_init(P, desc);

@@ -349,6 +349,7 @@ cudaError_t launch_split_root_moments(const LevelView& root, int K, const float*
 // root-to-leaf adjoint; one block per region.
 cudaError_t launch_chain_forward(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
 cudaError_t launch_chain_adjoint(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
+cudaError_t configure_chain(int D, int K);
 cudaError_t launch_predictive(const LevelView& v, int K, const float* xn, const float* yn, int nn, double* out,
                               cudaStream_t s);
 
