@@ -235,3 +235,50 @@ def estep_instance_chain(model, q, z, K: int, inst: int = 0) -> dict:
         ze = np.asarray(z[l][e], np.float64)
         mom[(l, e)] = np.stack([wi @ ze, wi @ ze ** 2])
     return {"log_pmp": mx + math.log(tot) - n * math.log(K), "w": w, "mom": mom, "n": n}
+
+
+def estep_instance_conditional(model, q, z, perm, K: int, inst: int = 0) -> dict:
+    """Enumeration for a two-level model whose children use the parent-
+    conditioned proposal N(z_p^{s(k)}[:D] + loc, diag scale^2) with the
+    permutation copy scheme: copy k of child i was drawn from parent copy
+    perm[i][k], so Eq. rmp's proposal term of copy k is that density.
+    Returns log_pmp, w / mom ((E z, E z^2)) keyed by (level, element), the
+    pairwise moment cross[e] = E[z_e z_parent[:D]], n.
+    """
+    r, u = model.levels
+    D = u.dim
+    users = [int(e) for e in np.nonzero(np.asarray(u.parent) == inst)[0]]
+    lat = [(0, inst)] + [(1, e) for e in users]
+    n = len(lat)
+    z0 = np.asarray(z[0][inst], np.float64)
+    unary = np.zeros((n, K))
+    for k in range(K):
+        unary[0, k] = _log_prior(r, z0[k], None) - _log_q(r, q[0][inst], z0[k])
+    pair = []
+    for i, e in enumerate(users, start=1):
+        ze = np.asarray(z[1][e], np.float64)
+        loc, sc = np.asarray(q[1][e][0], np.float64), np.asarray(q[1][e][1], np.float64)
+        for k in range(K):
+            mean = z0[int(perm[e][k])][:D] + loc
+            unary[i, k] = _log_lik(u, e, ze[k]) - stats.norm.logpdf(ze[k], mean, sc).sum()
+        f = np.array([[_log_prior(u, ze[k], z0[kp]) for k in range(K)] for kp in range(K)])
+        pair.append(f)
+    combos = np.array(list(itertools.product(range(K), repeat=n)))
+    logr = np.zeros(len(combos))
+    for i in range(n):
+        logr += unary[i][combos[:, i]]
+    for i, f in enumerate(pair, start=1):
+        logr += f[combos[:, 0], combos[:, i]]
+    mx = logr.max()
+    terms = np.exp(logr - mx)
+    tot = math.fsum(terms)
+    out = {"log_pmp": mx + math.log(tot) - n * math.log(K), "n": n, "w": {}, "mom": {}, "cross": {}}
+    for i, (l, e) in enumerate(lat):
+        wi = np.array([math.fsum(terms[combos[:, i] == k]) for k in range(K)]) / tot
+        ze = np.asarray(z[l][e], np.float64)
+        out["w"][(l, e)] = wi
+        out["mom"][(l, e)] = np.stack([wi @ ze, wi @ ze ** 2])
+        if l == 1:
+            prod = ze[combos[:, i]] * z0[combos[:, 0]][:, :D]            # [combos, D]
+            out["cross"][e] = np.array([math.fsum(terms * prod[:, d]) for d in range(D)]) / tot
+    return out
