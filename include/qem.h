@@ -108,6 +108,15 @@ typedef struct {
                          * N(z_{c,d-1}, prior_b I).  Only as level 1 of a two-level model,
                          * with a FP32 plan, a Gaussian proposal, dim <= 8 and K <= 1024
                          * (QEM_ERR_UNSUPPORTED otherwise).                                    */
+  int qcond;            /* 0: factorised proposal.  1: parent-conditioned proposal (App. A.2's
+                         * non-factorised Q_MP with the permutation copy scheme): copy k is
+                         * drawn from N(z_parent^{s(k)}[0:D] + loc, diag scale^2), s a uniformly
+                         * random permutation of the parent's K copies per element (counter-
+                         * based, or supplied by qem_set_perm); moments of the level are then
+                         * the residual's (E d, E d^2), d = z - z_parent[0:D], which the
+                         * Gaussian M-step turns into (loc, scale).  Only as level 1 of a
+                         * two-level model with a FP32 plan, a Gaussian proposal, a normal
+                         * prior given the parent and dim <= 32 (QEM_ERR_UNSUPPORTED else).  */
 } qem_level_desc;
 
 typedef struct {
@@ -195,6 +204,16 @@ qem_status qem_estep(qem_plan_t plan, const float* q_params, const float* eps, u
  * kept by the plan.                                                         */
 qem_status qem_estep_split_root(qem_plan_t plan, const float* q_params, const float* eps, uint64_t seed,
                                 uint64_t iter, double* moments, double* log_pmp, float* root_weights);
+
+/* Parent-copy permutations of the qcond level for the following E-steps:
+ * perm DEVICE int32 [n_1][K], row e a permutation of 0..K-1 (copy k of element
+ * e is drawn from parent copy perm[e][k]); kept by pointer (the caller keeps
+ * it valid); NULL returns to the counter-based draw: per element the K keys
+ * word (k mod 4) of Philox4x32-10 (Salmon et al. 2011) with counter
+ * (k div 4, e mod 2^32, (e div 2^32) | 2^30, iter) and key seed, the copies
+ * ordered by (key, k) ascending.  Invalidates qem_run's cached graph.
+ * QEM_ERR_INVALID_ARG when the plan has no qcond level.                     */
+qem_status qem_set_perm(qem_plan_t plan, const int32_t* perm);
 
 /* log P_MP of q_params from a fresh draw of the samples (the noise stream
  * keyed by (seed, iter), which the caller chooses distinct from the E-step's):

@@ -80,6 +80,24 @@ def child_prior(u, z, zp):
     raise ValueError("child prior must be N(parent, a I) or N(mean, diag exp logvar)")
 
 
+def draw_perm(seed: int, it: int, n: int, K: int) -> np.ndarray:
+    """The counter-based parent-copy permutations [n, K]: per element e the K
+    keys are word (k mod 4) of Philox4x32-10 (the oracle's own generator) with
+    counter (k div 4, e mod 2^32, (e div 2^32) | 2^30, it) and key seed; copies
+    ordered by (key, k), perm[e][rank] = k."""
+    from oracle import oracle as O
+    key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+    out = np.zeros((n, K), np.int64)
+    for e in range(n):
+        keys = np.zeros(K, np.uint64)
+        for k0 in range(0, K, 4):
+            w = O.philox4x32_10([k0 >> 2, e & 0xFFFFFFFF, ((e >> 32) & 0xFFFFFFFF) | 0x40000000, it & 0xFFFFFFFF], key)
+            for j in range(min(4, K - k0)):
+                keys[k0 + j] = w[j]
+        out[e] = np.lexsort((np.arange(K), keys))
+    return out
+
+
 def samples(model, q, K: int, eps, perm):
     """The reparameterised draws: root z = loc + scale eps; child z^k = z_p^{s(k)}[:D] + loc + scale eps^k."""
     r, u = model.levels

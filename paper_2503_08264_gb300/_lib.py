@@ -25,7 +25,8 @@ class LevelDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("dim", C.c_int), ("prior", C.c_int),
                 ("prior_a", C.c_double), ("prior_b", C.c_double),
                 ("lik", C.c_int), ("lik_var", C.c_double), ("n_obs", C.c_int), ("qfam", C.c_int),
-                ("parent", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p), ("chain", C.c_int)]
+                ("parent", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p), ("chain", C.c_int),
+                ("qcond", C.c_int)]
 
 
 class ModelDesc(C.Structure):
@@ -51,6 +52,7 @@ SIGNATURES = {
                             C.c_void_p]),
     "qem_estep_split_root": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p,
                                        C.c_void_p, C.c_void_p]),
+    "qem_set_perm": (C.c_int, [C.c_void_p, C.c_void_p]),
     "qem_log_pmp_fresh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p]),
     "qem_predictive": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "qem_moments_rescale": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

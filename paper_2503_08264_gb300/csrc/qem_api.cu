@@ -61,7 +61,11 @@ qem_status validate(const qem_model_desc* desc, const qem_plan_opts* o) {
         (d.lik == QEM_LIK_BERNOULLI_PROB && (d.qfam != QEM_Q_BETA || d.dim != 1)))
       return QEM_ERR_INVALID_ARG;
     if (L > 1 && d.qfam != QEM_Q_GAUSS) return QEM_ERR_UNSUPPORTED;
-    if (d.chain < 0) return QEM_ERR_INVALID_ARG;
+    if (d.chain < 0 || d.qcond < 0 || d.qcond > 1) return QEM_ERR_INVALID_ARG;
+    if (d.qcond) {
+      if (l != 1 || L != 2 || o->precision != QEM_PREC_FP32 || d.dim > 32 || d.qfam != QEM_Q_GAUSS || d.chain > 1)
+        return QEM_ERR_UNSUPPORTED;
+    }
     if (d.chain > 1) {
       if (l != 1 || L != 2 || o->precision != QEM_PREC_FP32 || d.dim > 8 || d.qfam != QEM_Q_GAUSS || o->K > 1024)
         return QEM_ERR_UNSUPPORTED;
@@ -170,6 +174,7 @@ qem_status estep_forward(qem_plan_t P, const float* q, const float* eps, double*
   cudaStream_t s = P->stream;
   const int L = P->L, K = P->K;
   for (int l = 0; l < L; ++l) {
+    if (P->lv[l].qcond && !P->perm_user) QEM_LAUNCH(P, QEM_K_SAMPLE, launch_draw_perm(P->lv[l], K, P->perm_own, P->ctl, s));
     QEM_LAUNCH(P, QEM_K_SAMPLE,
                launch_sample_local(P->lv[l], K, P->tune.sample_threads, q + P->q_off[l],
                                    eps ? eps + P->eps_off[l] : nullptr, P->ctl, s));
@@ -218,7 +223,12 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
       QEM_LAUNCH(P, QEM_K_ADJOINT, tc_adjoint(P, l));
     }
   }
-  for (int l = 0; l < L; ++l) QEM_LAUNCH(P, QEM_K_MOMENTS, launch_moments(P->lv[l], K, P->tune.mom_threads, moments + P->q_off[l], s));
+  for (int l = 0; l < L; ++l) {
+    QEM_LAUNCH(P, QEM_K_MOMENTS, launch_moments(P->lv[l], K, P->tune.mom_threads, moments + P->q_off[l], s));
+    if (P->lv[l].qcond)
+      QEM_LAUNCH(P, QEM_K_MOMENTS,
+                 launch_residual_moments(P->lv[l], K, moments + P->q_off[l - 1], moments + P->q_off[l], s));
+  }
   return QEM_OK;
 }
 
@@ -573,6 +583,8 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
       lv.nps = noise_per_sample(d);
       lv.level = l;
       lv.chain = d.chain > 1 ? d.chain : 1;
+      lv.qcond = d.qcond;
+      lv.pD = l > 0 ? desc->levels[l - 1].dim : 0;
       lv.x = d.x;
       lv.y = d.y;
       lv.Dc = has_children ? desc->levels[l + 1].dim : 0;
@@ -589,6 +601,12 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
       lv.lt = l > 0 ? cv.take<float>(nK) : nullptr;
       lv.w = cv.take<float>(nK);
       lv.beta = d.chain > 1 ? cv.take<float>(nK) : nullptr;
+      lv.cz = d.qcond ? cv.take<float>(nK * d.dim) : nullptr;
+      if (d.qcond) {
+        P->perm_own = cv.take<int>(nK);
+        lv.perm = P->perm_own;
+        lv.pz = P->lv[l - 1].z;
+      }
       lv.pm = has_children ? cv.take<float>(nK * lv.Dc) : nullptr;
       lv.pp = has_children ? cv.take<float>(nK * lv.Dc) : nullptr;
       lv.pc = has_children ? cv.take<float>(nK) : nullptr;
@@ -711,6 +729,20 @@ qem_status qem_log_pmp_fresh(qem_plan_t P, const float* q_params, uint64_t seed,
   return estep_forward(P, q_params, nullptr, log_pmp, nullptr);
 }
 
+qem_status qem_set_perm(qem_plan_t P, const int32_t* perm) {
+  if (!P) return QEM_ERR_INVALID_ARG;
+  int lq = -1;
+  for (int l = 0; l < P->L; ++l)
+    if (P->lv[l].qcond) lq = l;
+  if (lq < 0) return QEM_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEM_ERR_CUDA;
+  P->perm_user = perm;
+  P->lv[lq].perm = perm ? perm : P->perm_own;
+  delete run_of(P);  // the loop graph holds the old pointer
+  P->run = nullptr;
+  return QEM_OK;
+}
+
 qem_status qem_estep_split_root(qem_plan_t P, const float* q_params, const float* eps, uint64_t seed, uint64_t iter,
                                 double* moments, double* log_pmp, float* root_weights) {
   if (!P || !q_params || !moments) return QEM_ERR_INVALID_ARG;
@@ -718,7 +750,8 @@ qem_status qem_estep_split_root(qem_plan_t P, const float* q_params, const float
   const LevelView& r = P->lv[0];
   const LevelView& u = P->lv[1];
   if (r.prior != QEM_PRIOR_STD_NORMAL || r.qfam != QEM_Q_GAUSS || r.lik != QEM_LIK_NONE ||
-      u.prior != QEM_PRIOR_NORMAL_MEAN_LOGVAR || r.D != 2 * u.D || u.D > 32 || u.chain > 1 || P->K > 1024)
+      u.prior != QEM_PRIOR_NORMAL_MEAN_LOGVAR || r.D != 2 * u.D || u.D > 32 || u.chain > 1 || u.qcond ||
+      P->K > 1024)
     return QEM_ERR_UNSUPPORTED;
   qem_status st = split_alloc(P);
   if (st != QEM_OK) return st;

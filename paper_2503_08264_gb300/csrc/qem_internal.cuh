@@ -44,6 +44,11 @@ struct LevelView {
   int nps;            // noise numbers per sample
   int level;          // index of this level
   int chain;          // days per region of a chain plate (1: plain plate)
+  int qcond;          // parent-conditioned proposal (copies drawn from permuted parent copies)
+  const int* perm;    // [n][K] qcond: parent copy of each sample
+  const float* pz;    // qcond: the parent level's samples [n_parent][K][pD]
+  int pD;             // qcond: the parent's dimension
+  float* cz;          // [n][K][D] qcond: joint-weighted parent sample per child sample (adjoint)
   const float* x;     // [n][n_obs][D]
   const float* y;     // [n][n_obs]
   const long long* parent;     // [n] (level > 0)
@@ -134,6 +139,8 @@ struct qem_plan_s {
   void* run = nullptr;         // cached device-loop graph of qem_run (qem_api.cu)
   qem::Tune tune;              // launch shapes (defaults, or chosen by qem_tune)
   qem::SplitWs* split = nullptr; // split-root workspace (qem_estep_split_root), allocated on first use
+  int* perm_own = nullptr;     // qcond: the plan's drawn permutations [n_1][K]
+  const int* perm_user = nullptr; // qcond: caller-supplied permutations (qem_set_perm)
   bool tuned = false;          // qem_tune has run (or a cached choice was applied)
 };
 
@@ -328,6 +335,7 @@ cudaError_t launch_root(const LevelView& v, int K, bool has_children, double* lo
                         double* trace, Ctl* ctl, cudaStream_t s);
 // Kc: sample count of the children (0: K).
 cudaError_t launch_compact(const LevelView& parent, int K, float rel, cudaStream_t s, int Kc = 0);
+// (levels with qcond also write cz, the joint-weighted parent sample per child sample)
 cudaError_t launch_adj_compact(const LevelView& v, const LevelView& parent, int K, int max_eff, cudaStream_t s,
                                bool split = false);
 cudaError_t launch_adj_small(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
@@ -350,6 +358,10 @@ cudaError_t launch_split_root_moments(const LevelView& root, int K, const float*
 cudaError_t launch_chain_forward(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
 cudaError_t launch_chain_adjoint(const LevelView& v, const LevelView& parent, int K, cudaStream_t s);
 cudaError_t configure_chain(int D, int K);
+// Parent-conditioned proposals (qem_simt.cu): the counter-based permutations
+// and the residual moments.
+cudaError_t launch_draw_perm(const LevelView& v, int K, int* perm, const Ctl* ctl, cudaStream_t s);
+cudaError_t launch_residual_moments(const LevelView& v, int K, const double* mom_parent, double* mom, cudaStream_t s);
 cudaError_t launch_predictive(const LevelView& v, int K, const float* xn, const float* yn, int nn, double* out,
                               cudaStream_t s);
 

@@ -41,7 +41,7 @@ extern "C" qem_status qem_estep_single_noalloc(const qem_level_desc* level, int 
   if (!level || !q_params || !moments || K < 1 || K > 4096) return QEM_ERR_INVALID_ARG;
   const qem_level_desc& d = *level;
   if (d.parent || d.n < 0 || d.dim < 1 || d.n_obs < 0 || d.chain < 0) return QEM_ERR_INVALID_ARG;
-  if (d.chain > 1) return QEM_ERR_UNSUPPORTED;
+  if (d.chain > 1 || d.qcond) return QEM_ERR_UNSUPPORTED;
   if (d.dim > kMaxDim || d.n_obs > 4096 || (size_t)d.n_obs * d.dim > 8192) return QEM_ERR_UNSUPPORTED;
   if (d.qfam < QEM_Q_GAUSS || d.qfam > QEM_Q_BETA || d.lik < QEM_LIK_NONE || d.lik > QEM_LIK_BERNOULLI_PROB)
     return QEM_ERR_INVALID_ARG;
@@ -97,6 +97,11 @@ extern "C" qem_status qem_estep_single_noalloc(const qem_level_desc* level, int 
   v.level = 0;
   v.chain = 1;
   v.beta = nullptr;
+  v.qcond = 0;
+  v.perm = nullptr;
+  v.pz = nullptr;
+  v.pD = 0;
+  v.cz = nullptr;
   v.x = d.x;
   v.y = d.y;
   v.cst = reinterpret_cast<double*>(take(sizeof(double) * (size_t)d.n));

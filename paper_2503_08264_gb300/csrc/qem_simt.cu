@@ -252,6 +252,15 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
             z[d] = fmaf(qs[D + d], ep, qs[d]);
           }
         }
+        if (v.qcond) {
+          // parent-conditioned proposal: copy k is centred on the parent's copy perm[k]
+          // (clamped: a supplied permutation is caller data)
+          const int pk = min(max(v.perm[e * K + k], 0), K - 1);
+          const float* zp = v.pz + (v.parent[e] * K + pk) * (long long)v.pD;
+#pragma unroll
+          for (int d = 0; d < MAXD; ++d)
+            if (d < D) z[d] += zp[d];
+        }
         lq = -0.5f * ss;
       } else {
         const unsigned long long sample = (unsigned long long)e * K + k;
@@ -887,6 +896,73 @@ cudaError_t launch_moments_rescale(const LevelView* lvs, int l, const double* lp
 // the last E-step's samples and marginal weights (the paper's diagnostic of
 // held-out data):  out[e] = log sum_k w_e[k] prod_n p(y_n | z_e^k, x_n).
 // One block per element; FP32 terms with a block-wide max shift.
+// ---------------------------------------------------------------------------
+// Parent-conditioned proposals (App. A.2, the permutation copy scheme).
+// Permutations: per element, the K keys are word (k mod 4) of Philox4x32-10
+// with counter (k div 4, e mod 2^32, (e div 2^32) | 2^30, iter) and key seed
+// (bit 30 of the third word keeps these counters apart from the noise
+// stream's); copies are ordered by (key, k): perm[rank of copy k] = k.  One
+// block per element, keys in shared memory, ranks by counting (K^2 / block).
+__global__ void k_draw_perm(LevelView v, int K, int* perm, const Ctl* ctl) {
+  extern __shared__ uint32_t keys[];
+  const long long e = blockIdx.x;
+  const unsigned long long seed = ctl->seed, iter = ctl->iter;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)(k >> 2), (uint32_t)e, (uint32_t)(e >> 32) | 0x40000000u,
+                                             (uint32_t)iter),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+    keys[k] = w[k & 3];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const uint32_t kk = keys[k];
+    int rank = 0;
+    for (int j = 0; j < K; ++j) {
+      const uint32_t kj = keys[j];
+      rank += (kj < kk || (kj == kk && j < k)) ? 1 : 0;
+    }
+    perm[e * K + rank] = k;
+  }
+}
+
+cudaError_t launch_draw_perm(const LevelView& v, int K, int* perm, const Ctl* ctl, cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  if (K > 4096) return cudaErrorInvalidValue;
+  k_draw_perm<<<(unsigned)v.n, 256, sizeof(uint32_t) * (size_t)K, s>>>(v, K, perm, ctl);
+  return cudaGetLastError();
+}
+
+// Residual moments of a qcond level (the Gaussian M-step's statistics of the
+// parent-conditioned proposal): with d = z - z_parent[0:D] under the joint
+// weights of (parent sample, child sample),
+//   E d   = E z - E z_parent,   E d^2 = E z^2 - 2 E[z z_parent] + E z_parent^2,
+// E[z z_parent] = sum_k z^k cz^k (cz from the adjoint).  mom holds the level's
+// (E z, E z^2) on entry and (E d, E d^2) on exit; FP64 sums.  One block per
+// element, one thread per dimension.
+__global__ void k_residual_moments(LevelView v, int K, const double* __restrict__ mom_parent, double* mom) {
+  const long long e = blockIdx.x;
+  const int D = v.D, d = threadIdx.x;
+  if (d >= D) return;
+  double cross = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const long long i = (e * K + k) * D + d;
+    cross += (double)v.z[i] * (double)v.cz[i];
+  }
+  const long long p = v.parent[e];
+  const double pm1 = mom_parent[(p * 2 + 0) * v.pD + d], pm2 = mom_parent[(p * 2 + 1) * v.pD + d];
+  const double m1 = mom[(e * 2 + 0) * D + d], m2 = mom[(e * 2 + 1) * D + d];
+  mom[(e * 2 + 0) * D + d] = m1 - pm1;
+  mom[(e * 2 + 1) * D + d] = m2 - 2.0 * cross + pm2;
+}
+
+cudaError_t launch_residual_moments(const LevelView& v, int K, const double* mom_parent, double* mom, cudaStream_t s) {
+  if (v.n == 0) return cudaSuccess;
+  const int thr = ((v.D + 31) / 32) * 32;
+  k_residual_moments<<<(unsigned)v.n, thr, 0, s>>>(v, K, mom_parent, mom);
+  return cudaGetLastError();
+}
+
 template <int MAXD>
 __global__ void __launch_bounds__(256) k_predictive(LevelView v, int K, const float* __restrict__ xn,
                                                   const float* __restrict__ yn, int nn, double* out) {

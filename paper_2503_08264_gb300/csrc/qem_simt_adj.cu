@@ -30,8 +30,10 @@ __device__ __forceinline__ void stage_samples(const LevelView& v, long long e, i
 // keeps more than max_eff samples are left to the tensor-core adjoint
 // (max_eff = 0: no limit).  SPLIT: the kept parent rows are pairs
 // kp = a K + b of a split parent (as in the forward); cidx, cw and lt hold
-// K^2 entries per element.
-template <int MAXD, bool SPLIT>
+// K^2 entries per element.  CROSS (parent-conditioned proposals): also
+// cz[e][k] = sum_kp w_p[kp] P(k | kp) z_p^kp[0:D], the child-prior mean of
+// each kept parent sample being that sample's first D coordinates.
+template <int MAXD, bool SPLIT, bool CROSS>
 __global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView par, int K, int n_rt, int max_eff) {
   constexpr int DP = MAXD / 2;       // dimension pairs
   __shared__ float4 pq[kChunk * DP];  // per kept parent sample and pair: (pm_d, pm_d+1, pp_d, pp_d+1)
@@ -53,6 +55,9 @@ __global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView
   for (int d = 0; d < MAXD; ++d) zr[d] = (act && d < D) ? zc[threadIdx.x * (D + 1) + d] : 0.f;
   const float hk = act ? v.htil[e * K + k] : 0.f;
   float acc = 0.f;
+  float accp[CROSS ? MAXD : 1];
+#pragma unroll
+  for (int d = 0; d < (CROSS ? MAXD : 1); ++d) accp[d] = 0.f;
   for (int j0 = 0; j0 < n_eff; j0 += kChunk) {
     const int nj = min(kChunk, n_eff - j0);
     __syncthreads();
@@ -99,10 +104,24 @@ __global__ void __launch_bounds__(kRowTile) k_adj_compact(LevelView v, LevelView
         mul2(q0, q1, t0, t1, t0, t1);
         fma2(a0, a1, t.z, t.w, q0, q1);
       }
-      acc += expf(a0 + a1);
+      const float term = expf(a0 + a1);
+      acc += term;
+      if (CROSS) {
+#pragma unroll
+        for (int dp = 0; dp < DP; ++dp) {
+          const float4 t = pq[j * DP + dp];
+          accp[2 * dp] = fmaf(term, t.x, accp[2 * dp]);
+          accp[2 * dp + 1] = fmaf(term, t.y, accp[2 * dp + 1]);
+        }
+      }
     }
   }
   if (act) v.w[e * K + k] = acc;
+  if (CROSS && act) {
+#pragma unroll
+    for (int d = 0; d < (CROSS ? MAXD : 1); ++d)
+      if (d < D) v.cz[(e * K + k) * D + d] = accp[d];
+  }
 }
 
 // Small-set adjoint with its own normaliser (used when the forward ran at a
@@ -248,13 +267,21 @@ cudaError_t configure_adj_small(int D, int K) {
   return adj_small_cfg<64>(sm);
 }
 
-template <int MAXD, bool SPLIT>
+template <int MAXD, bool SPLIT, bool CROSS = false>
 static cudaError_t adj_compact_dispatch(const LevelView& v, const LevelView& par, int K, int max_eff, cudaStream_t s) {
   const int thr = K >= kRowTile ? kRowTile : ((K + 31) / 32) * 32;
   const int n_rt = (K + thr - 1) / thr;
-  k_adj_compact<MAXD, SPLIT><<<(unsigned)(v.n * n_rt), thr, sizeof(float) * thr * (size_t)(v.D + 1), s>>>(
+  k_adj_compact<MAXD, SPLIT, CROSS><<<(unsigned)(v.n * n_rt), thr, sizeof(float) * thr * (size_t)(v.D + 1), s>>>(
       v, par, K, n_rt, max_eff);
   return cudaGetLastError();
+}
+
+static cudaError_t adj_compact_cross(const LevelView& v, const LevelView& par, int K, int max_eff, cudaStream_t s) {
+  if (v.D <= 4) return adj_compact_dispatch<4, false, true>(v, par, K, max_eff, s);
+  if (v.D <= 8) return adj_compact_dispatch<8, false, true>(v, par, K, max_eff, s);
+  if (v.D <= 20) return adj_compact_dispatch<20, false, true>(v, par, K, max_eff, s);
+  if (v.D <= 32) return adj_compact_dispatch<32, false, true>(v, par, K, max_eff, s);
+  return cudaErrorInvalidValue;
 }
 
 template <bool SPLIT>
@@ -270,6 +297,7 @@ static cudaError_t adj_compact_dims(const LevelView& v, const LevelView& par, in
 cudaError_t launch_adj_compact(const LevelView& v, const LevelView& par, int K, int max_eff, cudaStream_t s,
                                bool split) {
   if (v.n == 0) return cudaSuccess;
+  if (v.qcond) return split ? cudaErrorInvalidValue : adj_compact_cross(v, par, K, max_eff, s);
   return split ? adj_compact_dims<true>(v, par, K, max_eff, s) : adj_compact_dims<false>(v, par, K, max_eff, s);
 }
 

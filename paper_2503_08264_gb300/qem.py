@@ -126,6 +126,7 @@ class Plan:
             d.prior_a, d.prior_b = float(lv.prior_a), float(lv.prior_b)
             d.lik, d.lik_var, d.n_obs, d.qfam = lv.lik, float(lv.lik_var), lv.n_obs if lv.lik else 0, lv.qfam
             d.chain = int(getattr(lv, "chain", 1) or 1)
+            d.qcond = int(getattr(lv, "qcond", 0) or 0)
             if lv.parent is not None:
                 par = np.ascontiguousarray(lv.parent, np.int64)
                 self._keep.append(par)
@@ -194,6 +195,12 @@ class Plan:
             root_weights = torch.empty((self.n_inst, 2, self.K), dtype=torch.float32, device=self.device)
         qem_estep_split_root(self.h, q, eps, seed, it, moments, log_pmp, root_weights)
         return moments, log_pmp, root_weights
+
+    def set_perm(self, perm=None):
+        """Parent-copy permutations of the qcond level (device int32 [n_1, K]) for the
+        following E-steps, or None for the counter-based draw."""
+        self._perm = None if perm is None else torch.as_tensor(perm, dtype=torch.int32).to(self.device).contiguous()
+        L.check(L.load().qem_set_perm(self.h, _ptr(self._perm)), "qem_set_perm")
 
     def log_pmp_fresh(self, q, seed: int, it: int, log_pmp=None):
         """log P_MP of q from a fresh draw of the samples (device double [n_inst])."""

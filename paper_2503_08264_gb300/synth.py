@@ -73,6 +73,7 @@ class Level:
     x: np.ndarray | None = None        # float32 [n, n_obs, dim]
     y: np.ndarray | None = None        # float32 [n, n_obs]
     chain: int = 1                     # T > 1: elements form chains of T days (leaf level)
+    qcond: int = 0                     # 1: proposal centred on a permuted parent copy (leaf level)
 
     def noise_per_sample(self) -> int:
         """Number of N(0,1)/U(0,1) numbers one sample of this level consumes."""

@@ -125,3 +125,16 @@ def test_conditional_weights_sum_to_one():
     o = QC.estep(model, S.random_q(model, seed=22), K, S.noise(model, K, seed=23), _perms(model, K, 24))
     for l in range(2):
         np.testing.assert_allclose(o["w"][l].sum(1), 1.0, rtol=1e-12)
+
+
+def test_counter_based_permutations_are_uniform_permutations():
+    n, K = 2000, 8
+    perm = QC.draw_perm(seed=77, it=3, n=n, K=K)
+    assert np.all(np.sort(perm, axis=1) == np.arange(K))            # every row is a permutation
+    # the parent copy of child copy 0 is uniform over the K copies (chi-square, 7 dof, 0.1% level)
+    counts = np.bincount(perm[:, 0], minlength=K)
+    chi2 = ((counts - n / K) ** 2 / (n / K)).sum()
+    assert chi2 < 24.3, counts
+    # different iterations and elements give different permutations
+    other = QC.draw_perm(seed=77, it=4, n=n, K=K)
+    assert np.mean(np.all(other == perm, axis=1)) < 0.01
