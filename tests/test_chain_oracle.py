@@ -7,6 +7,9 @@ autoregressive timeseries, App. F), every (region, day) its own latent.
   observations, one- and two-dimensional latents, several instances;
 * special case: chains of length 1 are an ordinary two-level model, whose
   estimator the C oracle computes (shared noise);
+* closed form: on a linear-Gaussian chain (Gaussian days) the average of
+  P_MP / p(y) over independent draws is 1, p(y) from Gaussian conditioning,
+  and the moments approach the exact posterior marginals as K grows;
 * weights of every latent sum to one.
 """
 import copy
@@ -61,3 +64,52 @@ def test_chain_weights_sum_to_one():
     for l in range(2):
         np.testing.assert_allclose(o["w"][l].sum(1), 1.0, rtol=1e-12)
     assert np.all(np.isfinite(o["B"])) and np.all(np.isfinite(o["L"]))
+
+
+def _chain_gauss_exact(model):
+    """log p(y) and the posterior of (g, z) for the linear-Gaussian chain:
+    g ~ N(0, a0), z_{c,0} = g + N(0, a), z_{c,d} = z_{c,d-1} + N(0, b),
+    y_{c,d} = x z_{c,d} + N(0, v) (D = 1, one observation per day)."""
+    from scipy import stats
+    r, u = model.levels
+    T = u.chain
+    n = u.n
+    A = np.zeros((n + 1, n + 1))          # latent = A @ innovations (g first)
+    var = np.zeros(n + 1)
+    var[0] = r.prior_a
+    A[0, 0] = 1.0
+    for e in range(n):
+        prev = 0 if e % T == 0 else e        # index of the parent in the latent vector
+        A[e + 1] = A[prev]
+        A[e + 1, e + 1] = 1.0
+        var[e + 1] = u.prior_a if e % T == 0 else u.prior_b
+    C = A @ np.diag(var) @ A.T
+    P = np.zeros((n, n + 1))
+    P[np.arange(n), np.arange(n) + 1] = u.x[:, 0, 0].astype(np.float64)
+    Sy = P @ C @ P.T + u.lik_var * np.eye(n)
+    y = u.y[:, 0].astype(np.float64)
+    lpy = stats.multivariate_normal(np.zeros(n), Sy).logpdf(y)
+    G = C @ P.T @ np.linalg.inv(Sy)
+    return lpy, G @ y, C - G @ P @ C
+
+
+def test_chain_gaussian_unbiased_evidence_and_exact_marginals():
+    """E[P_MP] = p(y) (Sec. 3.2) with p(y) from Gaussian conditioning, and the
+    MPIW moments approach the exact posterior marginals as K grows (App. C)."""
+    import math
+    model = S.chain_poisson(n_inst=1, R=2, T=5, D=1, seed=41, lik=S.LIK_GAUSS, lik_var=0.3)
+    lpy, mean, cov = _chain_gauss_exact(model)
+    sd = np.sqrt(np.diag(cov))
+    q = [np.array([[[mean[0]], [1.3 * sd[0]]]]), np.stack([mean[1:], 1.3 * sd[1:]], 1)[:, :, None]]
+    K, R = 8, 300
+    ratios = np.array([math.exp(C.estep(model, q, K, S.noise(model, K, seed=500 + s))["log_pmp"][0] - lpy)
+                       for s in range(R)])
+    se = ratios.std(ddof=1) / math.sqrt(R)
+    assert abs(ratios.mean() - 1.0) < 4 * se + 1e-3, (ratios.mean(), se)
+    errs = []
+    q0 = S.initial_q(model)
+    for K in (16, 512):
+        o = C.estep(model, q0, K, S.noise(model, K, seed=7))
+        m1 = np.concatenate([o["mom"][0][:, 0, 0], o["mom"][1][:, 0, 0]])
+        errs.append(np.max(np.abs(m1 - mean) / sd))
+    assert errs[1] < 0.5 and errs[1] < errs[0], errs
