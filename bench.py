@@ -69,6 +69,8 @@ def parse(argv=None):
                    help="pairs: E-step throughput (default); time_to_tol: the warm-start study")
     p.add_argument("--root", choices=["grouped", "split"], default="grouped",
                    help="split: the root's mean and log-variance as separate latents (K^2 parent pairs)")
+    p.add_argument("--qcond", action="store_true",
+                   help="leaf level with the parent-conditioned proposal (permutation copies; two-level, FP32)")
     p.add_argument("--train-instances", type=int, default=2000)
     p.add_argument("--test-instances", type=int, default=16)
     return p.parse_args(argv)
@@ -222,7 +224,7 @@ def roofline_for(kind: str, precision: str, D: int, pairs: float, ms: float, sm_
 
 
 # --------------------------------------------------------------------------- CPU oracle baseline
-def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7):
+def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7, qcond: bool = False):
     """Time the FP64 oracle E-step on a bounded sample of the workload (all host cores).
 
     The sample keeps the workload's shapes (K, dimensions, observations per
@@ -247,7 +249,7 @@ def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7):
             n = count * T
             users = S.Level(n=n, dim=lv.dim, prior=lv.prior, prior_a=lv.prior_a, prior_b=lv.prior_b, lik=lv.lik,
                             lik_var=lv.lik_var, n_obs=lv.n_obs, qfam=lv.qfam,
-                            parent=np.zeros(n, np.int64), x=lv.x[:n], y=lv.y[:n], chain=T)
+                            parent=np.zeros(n, np.int64), x=lv.x[:n], y=lv.y[:n], chain=T, qcond=int(qcond))
             what = "regions" if T > 1 else "plate elements"
             return S.Model([full.levels[0], users]), f"{count} of {total} {what}"
         return S.batched_three_level(n_inst=count, seed=seed), f"{count} of {total} instances"
@@ -262,14 +264,23 @@ def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7):
             break
         count = min(total, count * min(50.0, target_s / max(t, 1e-3)))
     pairs = model.pairs(K)
-    cores = 1 if T > 1 else O.max_threads()
-    noise = "supplied noise" if T > 1 else "counter-based noise"
+    cores = 1 if (T > 1 or qcond) else O.max_threads()
+    noise = "supplied noise" if (T > 1 or qcond) else "counter-based noise"
     return {"value": pairs / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one FP64 E-step on {desc} of {workload} ({noise}), {t:.1f} s"}, model
 
 
 def oracle_estep_seconds(model, K: int, it: int) -> float:
-    """Seconds of one FP64 oracle E-step of `model` (the chain oracle for chain plates)."""
+    """Seconds of one FP64 oracle E-step of `model` (the chain oracle for chain plates,
+    the conditional-proposal oracle for qcond levels)."""
+    if len(model.levels) == 2 and int(getattr(model.levels[1], "qcond", 0) or 0):
+        from oracle import conditional as QC
+        eps = S.noise(model, K, seed=it)
+        rng = np.random.default_rng(it)
+        perm = np.stack([rng.permutation(K) for _ in range(model.levels[1].n)])
+        t0 = time.perf_counter()
+        QC.estep(model, S.initial_q(model), K, eps, perm)
+        return time.perf_counter() - t0
     if len(model.levels) == 2 and int(getattr(model.levels[1], "chain", 1) or 1) > 1:
         from oracle import chain as C
         eps = S.noise(model, K, seed=it)
@@ -292,7 +303,7 @@ def run_reference(args):
     builder, K, _ = WORKLOADS[args.workload]
     # size one step's sample so that warmup + steps fit in about three minutes
     per_step = max(0.2, args.ref_seconds / max(1, args.steps + args.warmup))
-    base, model = cpu_oracle_sample(args.workload, per_step)
+    base, model = cpu_oracle_sample(args.workload, per_step, qcond=args.qcond)
     times = []
     for i in range(args.warmup + args.steps):
         t = oracle_estep_seconds(model, K, i + 1)
@@ -303,7 +314,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "K": K, "sample": base["sample"]},
+            "config": {"workload": args.workload, "K": K, "sample": base["sample"],
+                       "proposal": "parent-conditioned, permutation copies" if args.qcond else "factorised"},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
@@ -498,6 +510,10 @@ def run_ours(args):
     builder, K, default_prec = WORKLOADS[args.workload]
     precision = args.precision or default_prec
     model = builder(1000 + rank)
+    if args.qcond:
+        if len(model.levels) != 2 or precision != "fp32":
+            raise SystemExit("--qcond needs a two-level workload and the fp32 path")
+        model.levels[1].qcond = 1
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         plan = qem.Plan(model, K, precision=precision, stream=stream, tile=L.QEM_TILE_AUTO)
@@ -615,7 +631,7 @@ def run_ours(args):
 
     cpu = None
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
-        cpu, _ = cpu_oracle_sample(args.workload, args.cpu_seconds)
+        cpu, _ = cpu_oracle_sample(args.workload, args.cpu_seconds, qcond=args.qcond)
 
     if rank == 0:
         ws_bytes = plan.workspace_bytes
@@ -629,7 +645,8 @@ def run_ours(args):
                            "step": "qem_estep + qem_mstep (one Alg. 1 iteration)",
                            "l2": f"working set {ws_bytes / 1e9:.2f} GB > 129 MB L2 (no flush)",
                            "parallelism": f"replicas x{ws} (independent instances)",
-                           "launch_shapes": plan.tuning()},
+                           "launch_shapes": plan.tuning(),
+                           "proposal": "parent-conditioned, permutation copies" if args.qcond else "factorised"},
                 "graph_loop": graph_loop,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clk, "kernels_ms": {k: round(v[0], 4) for k, v in prof.items()},
