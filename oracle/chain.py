@@ -1,7 +1,7 @@
 """FP64 reference of the E-step of a two-level model whose leaf plate is a chain.
 
 TEST INFRASTRUCTURE ONLY: the test-suite and the benchmark's CPU-baseline
-leg are the only callers.  Nothing here imports the CUDA package.
+and reference legs are the only callers.  Nothing here imports the CUDA package.
 
 The chain plate follows the autoregressive timeseries of App. F's Covid
 model: every region c of an instance has T daily latents z_{c,0..T-1}; the

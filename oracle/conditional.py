@@ -1,8 +1,9 @@
 """FP64 reference of the E-step with a parent-conditioned (non-factorised)
 massively parallel proposal and the permutation copy scheme.
 
-TEST INFRASTRUCTURE ONLY: the test-suite is the only caller.  Nothing here
-imports the CUDA package.
+TEST INFRASTRUCTURE ONLY: the test-suite and the benchmark's CPU-baseline
+and reference legs are the only callers.  Nothing here imports the CUDA
+package.
 
 App. A.2 defines Q_MP(z) = prod_i Q_MP(z_i | z_j, j in qa(i)) from a
 single-sample proposal Q(z_i' | z_j') and a scheme that picks which of the K
