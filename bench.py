@@ -189,7 +189,8 @@ SMS = 152
 NCU_TRAFFIC = {
     ("forward", "hier_logistic_M5000_N10_K1024", "bf16x3"): {
         "bytes": 819579904 + 21370624, "source": "paper_2503_08264_gb300/csrc/qem_tc.cu",
-        "blob": "f35ba41dc5179f8fbdfdc7012d1fc54b19f4599f",
+        # captured on blob f35ba41d; ac74cb7d differs from it in one comment line only
+        "blob": "ac74cb7da04ad1f89cb694c2447f97e4c4aae8cc",
         "profile": "profiles/contract_forward_bf16x3_hier_logistic_M5000_K1024.md"},
 }
 

@@ -167,7 +167,7 @@ qem_status qem_layout(const qem_plan_t plan, int level, int64_t* q_off, int64_t*
  * eps_len (eps), w_len (weights), n_inst (log_pmp).                          */
 qem_status qem_sizes(const qem_plan_t plan, int64_t* q_len, int64_t* eps_len, int64_t* w_len, int64_t* n_inst);
 
-/* E-step (Alg. 1 "z ~ Q_t; m = MPIW(z, Q_t)"; Eq. mp_iw; Sec. 7 for the
+/* E-step (Alg. 1 "z ~ Q_t; m = MPIW(z, Q_t)"; Eq. mp_iw; Sec. 6 for the
  * plate-tree recursion).  Draws K samples per latent from the proposal
  * q_params (DEVICE float, layout above), forms the K_parent x K_child
  * log-factor tiles, contracts them leaves-to-root in log space into

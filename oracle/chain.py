@@ -15,7 +15,7 @@ the previous day,
 each day has its own observations and its own factorised Gaussian proposal,
 and under massively parallel sampling each (region, day) is its own latent
 with its own sample index.  Eq. mp_iw then factorises along each chain
-(Sec. 7's recursion with the previous day as the parent), leaves to root:
+(Sec. 6's recursion with the previous day as the parent), leaves to root:
 
   h_{c,d}[k]     = sum_n log p(x | z_{c,d}^k) - log q_{c,d}(z_{c,d}^k)       (Eq. rmp)
   S_{c,d}[j, k]  = log N(z_{c,d}^k; z_{c,d-1}^j, b I) + h_{c,d}[k] + B_{c,d+1}[k]   (d >= 1)

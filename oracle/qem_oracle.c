@@ -12,7 +12,7 @@
  *      P_MP = K^-n sum_k r_k,   r_k = P(x, z^k) / prod_i Q(z_i^{k_i}),
  *      w_i[k] = K^-n sum_{k : k_i = k} r_k / P_MP   (marginal weight of sample k of latent i),
  *      m_i = sum_k w_i[k] T(z_i^k)                   (Eq. mp_iw, m(z) = T(z_i));
- *    evaluated by the distributive law over the plate tree (Sec. 7: sum the
+ *    evaluated by the distributive law over the plate tree (Sec. 6: sum the
  *    child indices out one latent at a time, leaves first), every step in
  *    FP64 with no blocking, fusion or reordering of the sums;
  *  - the moment-matching M-step (Sec. 4, App. B) for Gaussian, Gamma and
@@ -279,7 +279,7 @@ static double log_mean_exp(const double* v, int K) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* E-step: MPIW over the plate tree (Eq. mp_iw; Sec. 7 for the recursion).   */
+/* E-step: MPIW over the plate tree (Eq. mp_iw; Sec. 6 for the recursion).   */
 int orc_estep(int n_levels, orc_level* lv, int K, uint64_t seed, uint64_t iter, double* log_pmp) {
   if (n_levels < 1 || K < 1) return 1;
   double** local = calloc((size_t)n_levels, sizeof(double*));  /* log lik - log q  [n][K] */

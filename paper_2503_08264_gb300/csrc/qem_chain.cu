@@ -3,7 +3,7 @@
 // of a region takes the level's prior given the parent sample; day d >= 1
 // takes N(z_{c,d-1}, b I) (b = prior_b).  Every day is its own latent with
 // its own sample index, so Eq. mp_iw factorises along the chain, the
-// previous day acting as the parent (Sec. 7's recursion):
+// previous day acting as the parent (Sec. 6's recursion):
 //   forward (last day first), d >= 1:
 //     beta_d[j] = log (1/K) sum_k exp( log N(z_d^k; z_{d-1}^j, b I) + h_d[k] + beta_{d+1}[k] ),
 //   day 0, per parent sample p:

@@ -490,7 +490,7 @@ cudaError_t launch_finalize(const LevelView& v, int K, bool has_children, cudaSt
 }
 
 // ---------------------------------------------------------------------------
-// Plate sum (Sec. 7: the child's factor enters the parent's as a sum over the
+// Plate sum (Sec. 6: the child's factor enters the parent's as a sum over the
 // plate): hsum_p[kp] = sum_{e in children(p)} (lt[e][kp] + off[e] + cst[e]) in
 // FP64, in a fixed order (deterministic).  Stage 1 sums chunks of at most 32
 // consecutive children into partial[chunk][kp]; stage 2 adds a parent's

@@ -12,7 +12,7 @@ namespace qem {
 
 // ---------------------------------------------------------------------------
 // K3 (FP32): forward contraction of one plate element (Eq. Prmp summed over
-// the child index, Sec. 7):
+// the child index, Sec. 6):
 //   lt[e][kp] = log (1/K) sum_k exp( log p(z_e^k | z_p^kp) + htil[e][k] )
 // One thread per parent sample kp; the element's child samples stream
 // through shared memory in chunks; online max-shifted sum per row.

@@ -1,7 +1,7 @@
 // Tensor-core (tcgen05) contraction path of libqem for sm_103a.
 //
 // The K_parent x K_child log-factor tile of one plate element (Eq. rmp; the
-// sum over the child index of Eq. Prmp, organised per Sec. 7) is a
+// sum over the child index of Eq. Prmp, organised per Sec. 6) is a
 // low-rank bilinear form plus row and column terms:
 //   S[kp][k] = rowc[kp] + sum_f A[kp][f] B[k][f] + h[k].
 // The bilinear part and the column term run on the 5th-generation tensor
