@@ -13,7 +13,7 @@ parent (parent indices non-decreasing), which makes every plate a contiguous
 CSR segment.
 
 The workloads follow the model definitions of App. F (MovieLens, Eq. in
-App. F.2) and the conjugate hierarchies used to pin the estimator:
+App. F.3) and the conjugate hierarchies used to pin the estimator:
 
 * ``conjugate_gaussian``  mu~N(0,1), z_m~N(mu,1), x_mn~N(z_m,0.5^2)
 * ``hier_logistic``       mu,psi~N(0,I_18), z_m~N(mu,diag e^psi), y~Bern(sigmoid(z.x))
@@ -121,7 +121,7 @@ def conjugate_gaussian(M: int = 8, N: int = 16, seed: int = 0, obs_var: float = 
 
 
 def hier_logistic(M: int = 300, N: int = 5, D: int = 18, seed: int = 0, p_feat: float = 0.3) -> Model:
-    """MovieLens-shaped hierarchical logistic regression (App. F.2).
+    """MovieLens-shaped hierarchical logistic regression (App. F.3).
 
     Root = the grouped (mu, psi) pair as one 2D-dimensional latent; users
     z_m ~ N(mu, diag exp(psi)); binary genre features per (user, item).
