@@ -14,7 +14,10 @@ the M-step.
   log ratio significantly above 0, which no unbiased estimator can have
   (Jensen), so the pin tells the two readings of Eq. rmp apart;
 * residual moments: E d = E z_i - E z_p and E d^2 = E z_i^2 - 2 E[z_i z_p] +
-  E z_p^2 equal the moments of d = z_i - z_p under the enumerated joint weights.
+  E z_p^2 equal the moments of d = z_i - z_p under the enumerated joint weights,
+  and approach the exact posterior of d on the conjugate hierarchy as K grows;
+* the counter-based permutations are permutations, uniform, and change with
+  the iteration.
 """
 import math
 
@@ -138,3 +141,22 @@ def test_counter_based_permutations_are_uniform_permutations():
     # different iterations and elements give different permutations
     other = QC.draw_perm(seed=77, it=4, n=n, K=K)
     assert np.mean(np.all(other == perm, axis=1)) < 0.01
+
+
+def test_conditional_residual_moments_approach_exact_posterior():
+    """On the conjugate hierarchy the residual d_m = z_m - mu has an exact
+    Gaussian posterior (mean and variance from Gaussian conditioning); the
+    residual moments the M-step consumes approach them as K grows (App. C)."""
+    model = S.conjugate_gaussian(M=6, N=8, seed=31)
+    model.levels[1].qcond = 1
+    _, mean, cov = _conj_exact(model)
+    d_mean = mean[1:] - mean[0]
+    d_var = np.diag(cov)[1:] + cov[0, 0] - 2 * cov[0, 1:]
+    q = [np.array([[[0.0], [1.0]]]), np.stack([np.zeros(6), np.ones(6)], 1)[:, :, None]]
+    errs = []
+    for K in (32, 1024):
+        o = QC.estep(model, q, K, S.noise(model, K, seed=32), _perms(model, K, 33))
+        m1, m2 = o["mom"][1][:, 0, 0], o["mom"][1][:, 1, 0]
+        v = m2 - m1 ** 2
+        errs.append(max(np.max(np.abs(m1 - d_mean) / np.sqrt(d_var)), np.max(np.abs(v / d_var - 1.0))))
+    assert errs[1] < 0.3 and errs[1] < errs[0], errs
