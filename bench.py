@@ -225,7 +225,7 @@ def roofline_for(kind: str, precision: str, D: int, pairs: float, ms: float, sm_
 
 
 # --------------------------------------------------------------------------- CPU oracle baseline
-def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7, qcond: bool = False):
+def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7, qcond: bool = False, split: bool = False):
     """Time the FP64 oracle E-step on a bounded sample of the workload (all host cores).
 
     The sample keeps the workload's shapes (K, dimensions, observations per
@@ -260,20 +260,26 @@ def cpu_oracle_sample(workload: str, target_s: float, seed: int = 7, qcond: bool
     count = 4 if two_level else 1
     for _ in range(5):
         model, desc = sub(count)
-        t = oracle_estep_seconds(model, K, 1)
+        t = oracle_estep_seconds(model, K, 1, split)
         if t >= 0.6 * target_s or count >= total:
             break
         count = min(total, count * min(50.0, target_s / max(t, 1e-3)))
-    pairs = model.pairs(K)
-    cores = 1 if (T > 1 or qcond) else O.max_threads()
-    noise = "supplied noise" if (T > 1 or qcond) else "counter-based noise"
+    pairs = model.pairs(K) * (K if split else 1)
+    cores = 1 if (T > 1 or qcond or split) else O.max_threads()
+    noise = "supplied noise" if (T > 1 or qcond or split) else "counter-based noise"
     return {"value": pairs / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one FP64 E-step on {desc} of {workload} ({noise}), {t:.1f} s"}, model
 
 
-def oracle_estep_seconds(model, K: int, it: int) -> float:
+def oracle_estep_seconds(model, K: int, it: int, split: bool = False) -> float:
     """Seconds of one FP64 oracle E-step of `model` (the chain oracle for chain plates,
-    the conditional-proposal oracle for qcond levels)."""
+    the conditional-proposal oracle for qcond levels, the split-root oracle with split)."""
+    if split:
+        from oracle import split_root as R
+        eps = S.noise(model, K, seed=it)
+        t0 = time.perf_counter()
+        R.estep(model, S.initial_q(model), K, eps)
+        return time.perf_counter() - t0
     if len(model.levels) == 2 and int(getattr(model.levels[1], "qcond", 0) or 0):
         from oracle import conditional as QC
         eps = S.noise(model, K, seed=it)
@@ -304,19 +310,21 @@ def run_reference(args):
     builder, K, _ = WORKLOADS[args.workload]
     # size one step's sample so that warmup + steps fit in about three minutes
     per_step = max(0.2, args.ref_seconds / max(1, args.steps + args.warmup))
-    base, model = cpu_oracle_sample(args.workload, per_step, qcond=args.qcond)
+    split = args.root == "split"
+    base, model = cpu_oracle_sample(args.workload, per_step, qcond=args.qcond, split=split)
     times = []
     for i in range(args.warmup + args.steps):
-        t = oracle_estep_seconds(model, K, i + 1)
+        t = oracle_estep_seconds(model, K, i + 1, split)
         if i >= args.warmup:
             times.append(t)
-    pairs = model.pairs(K)
+    pairs = model.pairs(K) * (K if split else 1)
     value = pairs * len(times) / sum(times)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "K": K, "sample": base["sample"],
-                       "proposal": "parent-conditioned, permutation copies" if args.qcond else "factorised"},
+                       "proposal": "parent-conditioned, permutation copies" if args.qcond else "factorised",
+                       "root": "split (mean and log-variance as separate latents)" if split else "grouped"},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
