@@ -105,9 +105,10 @@ typedef struct {
                          * are n / T regions of T consecutive days, element c*T + d, each day
                          * its own latent; the T elements of a region share its parent; day 0
                          * takes the level's prior given the parent, day d >= 1 the prior
-                         * N(z_{c,d-1}, prior_b I).  Only as level 1 of a two-level model,
-                         * with a FP32 plan, a Gaussian proposal, dim <= 8 and K <= 1024
-                         * (QEM_ERR_UNSUPPORTED otherwise).                                    */
+                         * N(z_{c,d-1}, prior_b I).  n a multiple of T, prior_b > 0 and one
+                         * parent per region (QEM_ERR_INVALID_ARG otherwise).  Only as level 1
+                         * of a two-level model, with a FP32 plan, a Gaussian proposal,
+                         * dim <= 8 and K <= 1024 (QEM_ERR_UNSUPPORTED otherwise).             */
   int qcond;            /* 0: factorised proposal.  1: parent-conditioned proposal (App. A.2's
                          * non-factorised Q_MP with the permutation copy scheme): copy k is
                          * drawn from N(z_parent^{s(k)}[0:D] + loc, diag scale^2), s a uniformly
