@@ -50,3 +50,31 @@ def test_roofline_arithmetic():
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
     f = bench.roofline_for("forward", "fp32", 18, pairs=1e12, ms=100.0, sm_max_mhz=2000.0)
     assert abs(f["peak"] - 152 * 128 * 2e9 / (3 * 18 + 4) / 1e9) < 1e-6
+
+
+def _reference_line(argv):
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        rc = bench.main(["--impl", "reference", "--steps", "1", "--warmup", "1", "--ref-seconds", "1"] + argv)
+    assert rc == 0
+    lines = [ln for ln in buf.getvalue().splitlines() if ln.strip()]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def test_reference_arm_of_the_other_paths():
+    """The split root, the parent-conditioned proposal and the chain plate time
+    their own oracles (their pairs per step and proposal labelled in config)."""
+    d = _reference_line(["--workload", "hier_logistic_M300_N5_K128", "--root", "split"])
+    assert d["config"]["root"].startswith("split") and d["value"] > 0
+    d = _reference_line(["--workload", "hier_logistic_M300_N5_K128", "--qcond"])
+    assert d["config"]["proposal"].startswith("parent-conditioned") and d["value"] > 0
+    d = _reference_line(["--workload", "chain_poisson_R92_T109_K128"])
+    assert "regions" in d["cpu_baseline"]["sample"] and d["cpu_baseline"]["cores"] == 1
+
+
+def test_traffic_gate_follows_the_source_hash():
+    e = bench.NCU_TRAFFIC[("forward", "hier_logistic_M5000_N10_K1024", "bf16x3")]
+    same = bench.git_blob_hash(e["source"]) == e["blob"]
+    assert (bench.ncu_traffic("forward", "hier_logistic_M5000_N10_K1024", "bf16x3") is not None) == same
+    assert bench.ncu_traffic("forward", "hier_logistic_M300_N5_K128", "fp32") is None
