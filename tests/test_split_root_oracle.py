@@ -11,6 +11,8 @@ log-variance psi, are separate latents with their own sample indices.
   permuting the psi samples alone leaves log P_MP, the mu weights and every
   user's weights unchanged and permutes the psi weights (the grouped
   estimator, which pairs k_mu = k_psi, changes);
+* unbiasedness: with Gaussian users, E[P_MP] = p(x), p(x) by one-dimensional
+  Gauss-Hermite quadrature over psi of a closed-form Gaussian density;
 * weights of every latent sum to one.
 """
 import copy
@@ -103,3 +105,37 @@ def test_split_root_weights_sum_to_one():
     np.testing.assert_allclose(o["w_psi"].sum(1), 1.0, rtol=1e-12)
     np.testing.assert_allclose(o["w"].sum(1), 1.0, rtol=1e-12)
     assert np.all(np.isfinite(o["logL"]))
+
+
+def test_split_root_estimator_is_unbiased():
+    """E[P_MP] = p(x) (Sec. 3.2) for the split estimator.  Users with Gaussian
+    observations, D = 1, x = 1: given psi the data are Gaussian with covariance
+    1 (mu) + e^psi (user) + v I (noise), so p(x) = E_psi N(x; 0, Sigma(psi)),
+    one Gauss-Hermite quadrature over psi ~ N(0, 1)."""
+    import math
+    from scipy import stats
+    model = S.hier_logistic(M=2, N=3, D=1, seed=61)
+    u = model.levels[1]
+    v = 0.5
+    rng = np.random.default_rng(62)
+    u.lik, u.lik_var = S.LIK_GAUSS, v
+    u.x = np.ones_like(u.x)
+    u.y = (0.7 + rng.standard_normal(u.y.shape)).astype(np.float32)
+    y = u.y.astype(np.float64).reshape(-1)
+    M, N = u.y.shape
+    blk = np.kron(np.eye(M), np.ones((N, N)))
+
+    def lpx_given(psi):
+        return stats.multivariate_normal(np.zeros(M * N), np.ones((M * N, M * N)) + math.exp(psi) * blk
+                                         + v * np.eye(M * N)).logpdf(y)
+
+    xs, ws = np.polynomial.hermite_e.hermegauss(60)            # nodes for the weight exp(-x^2 / 2)
+    lpx = np.log(np.sum(ws / math.sqrt(2 * math.pi) * np.exp([lpx_given(t) for t in xs])))
+    q = S.random_q(model, seed=63, loc_scale=0.0, sd_lo=0.8, sd_hi=0.8)
+    q[0][0, 0, 0] = 0.7                                           # mu near the data mean
+    K, reps = 8, 400
+    ratios = np.array([math.exp(R.estep(model, q, K, S.noise(model, K, seed=900 + s))["log_pmp"][0] - lpx)
+                       for s in range(reps)])
+    se = ratios.std(ddof=1) / math.sqrt(reps)
+    assert abs(ratios.mean() - 1.0) < 4 * se + 1e-3, (ratios.mean(), se)
+    assert np.log(ratios).mean() < 0
