@@ -4,7 +4,8 @@ autoregressive timeseries, App. F), every (region, day) its own latent.
 
 * brute force: literal enumeration of every index vector over the root and
   all days (oracle/brute.py, scipy densities) for Poisson-log and Gaussian
-  observations, one- and two-dimensional latents, several instances;
+  observations, one- and two-dimensional latents, several instances, and a
+  first day under a (mean, log-variance) root;
 * special case: chains of length 1 are an ordinary two-level model, whose
   estimator the C oracle computes (shared noise);
 * closed form: on a linear-Gaussian chain (Gaussian days) the average of
@@ -23,8 +24,17 @@ from oracle import oracle as O
 from paper_2503_08264_gb300 import synth as S
 
 
+def _mean_logvar_first_day(model):
+    """The same chain with a (mean, log-variance) root and day 0 ~ N(mean, diag exp logvar)."""
+    m = copy.deepcopy(model)
+    m.levels[0].dim = 2 * m.levels[1].dim
+    m.levels[1].prior = S.PRIOR_NORMAL_MEAN_LOGVAR
+    return m
+
+
 def _cases():
     yield "poisson_R1_T3_K3", S.chain_poisson(n_inst=1, R=1, T=3, D=1, seed=1), 3
+    yield "mean_logvar_day0_R2_T2_K3", _mean_logvar_first_day(S.chain_poisson(n_inst=1, R=2, T=2, D=1, seed=9)), 3
     yield "poisson_R2_T2_K3", S.chain_poisson(n_inst=1, R=2, T=2, D=1, seed=2), 3
     yield "gauss_D2_R1_T3_K3", S.chain_poisson(n_inst=1, R=1, T=3, D=2, seed=3, lik=S.LIK_GAUSS, n_obs=2), 3
     yield "poisson_R1_T4_K2", S.chain_poisson(n_inst=1, R=1, T=4, D=1, seed=4, n_obs=3), 2
