@@ -142,8 +142,10 @@ typedef struct qem_plan_s* qem_plan_t;
 /* Human-readable name of a status code (static storage). */
 const char* qem_status_string(qem_status s);
 
-/* Build a plan: validate the model (parents non-decreasing and in range, prior
- * and dimension compatible with the parent level), copy its plate structure
+/* Build a plan for the E-step of Eq. mp_iw over the model's plate tree (the
+ * plated Bayes net of Sec. 3.1, summed leaves to root as in Sec. 6) and the
+ * M-step of Alg. 1: validate the model (parents non-decreasing and in range,
+ * prior and dimension compatible with the parent level), copy its plate structure
  * to the device and allocate the workspace, the plan's only device-memory
  * allocation: qem_estep, qem_mstep and qem_log_pmp_fresh allocate nothing
  * (graph-capturable), except that a plan made with tile = QEM_TILE_AUTO tunes
@@ -259,7 +261,11 @@ qem_status qem_predictive(qem_plan_t plan, int level, const float* x_new, const 
  * lambda is the weight of the new estimate; with sched_p in (0,1) it is
  * replaced by t^-sched_p (the schedule of Thm. 1, 1-lambda(t) in its
  * notation); t >= 1 is the iteration number.  moments may be NULL to only set
- * q_params from mean_params (Alg. 1's initial M-step).                       */
+ * q_params from mean_params (Alg. 1's initial M-step).  Gamma and Beta
+ * statistics that no member of the family has (non-finite; E log z >= log E z
+ * for the Gamma; e^{E log z} + e^{E log(1-z)} >= 1 for the Beta, which
+ * rounding can produce when the weights collapse) keep that element's
+ * previous q_params and raise QEM_ERR_NUMERIC at the next qem_log_pmp.      */
 qem_status qem_mstep(qem_plan_t plan, const double* moments, double* mean_params, float* q_params,
                      double lambda, double sched_p, int64_t t);
 
@@ -267,9 +273,13 @@ qem_status qem_mstep(qem_plan_t plan, const double* moments, double* mean_params
  *   q_params DEVICE float [q_len] in, mean_params DEVICE double [q_len] out.  */
 qem_status qem_mean_params(qem_plan_t plan, const float* q_params, double* mean_params);
 
-/* Copy log P_MP of the last E-step to HOST double [n_inst].  Synchronises the
- * plan's stream; returns QEM_ERR_NUMERIC if any value is not finite, and
- * QEM_ERR_TIMEOUT if a device wait of that E-step expired.                  */
+/* Copy log P_MP of the last E-step (Eq. Prmp: the log of the massively
+ * parallel importance-weighted estimate of the evidence P(x), the quantity
+ * Sec. 5 reports as the ELBO of each method) to HOST double [n_inst].
+ * Synchronises the plan's stream; returns QEM_ERR_NUMERIC if any value is not
+ * finite or a Gamma/Beta M-step met statistics outside its family's domain,
+ * and QEM_ERR_TIMEOUT if a device wait of that E-step expired.  Error states
+ * are sticky for the plan's life.                                           */
 qem_status qem_log_pmp(qem_plan_t plan, double* host_out);
 
 /* Copy the marginal weights of the last E-step (the per-sample posterior
@@ -410,23 +420,28 @@ const char* qem_profile_name(int kind);
 qem_status qem_diag_tc_gemm(const void* A, const void* B, int fk, int n, float* out, void* stream);
 
 /* Allocation-free E-step for single-level models (every instance has one
- * latent, no plate below it: the global importance weighting of App. A.1 as
- * the n = 1 case of MPIW).  The paper has no counterpart of this entry point;
- * it exists for callers that cannot allocate device memory when they run an
- * E-step (inside a CUDA-graph capture they do not own, under a memory pool
- * that forbids outside allocations, or in a latency-bound loop), and it
- * allocates nothing, on the device or the host.
+ * latent, no plate below it).  The paper has no counterpart of this entry
+ * point.  It is for callers that cannot allocate device memory at the moment
+ * they need an E-step: a runtime whose memory pool forbids allocations from
+ * outside it, or a real-time loop that cannot afford an allocation's latency
+ * and implicit device synchronisation.  It allocates nothing, on the device
+ * or the host.
  *   level      HOST descriptor of the single level (parent must be NULL; x, y DEVICE)
  *   q_params   DEVICE float [n][2][D]; eps DEVICE float [n][K][nps] or NULL
  *   moments    DEVICE double [n][2][D] out; log_pmp DEVICE double [n] out (nullable)
  *   stream     cudaStream_t (NULL: legacy default stream), asynchronous
  * Scratch lives in one library-wide device array of 32 MiB, held by every GPU
  * that loads the library until the process exits: requests needing more
- * (about n*K*(D+2)*4 bytes) return QEM_ERR_UNSUPPORTED.  Calls whose GPU work
- * overlaps race on that array.  The first call on a device looks the array's
- * address up (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Results equal qem_estep's on the same
- * single-level model and inputs.                                            */
+ * (about n*K*(D+2)*4 bytes) return QEM_ERR_UNSUPPORTED.  Every call shares
+ * that array and it keeps the last call's contents (each call writes what it
+ * reads first); calls whose GPU work overlaps (other streams, other host
+ * threads) race on it.  The first call on a device looks the array's address
+ * up (cudaGetSymbolAddress) with that device current and keeps it for the
+ * process; make that first call before any stream capture, and make no call
+ * after a cudaDeviceReset (the kept address then names released memory).
+ * The call is asynchronous and cannot report a non-finite log P_MP: pass
+ * log_pmp and check its values.  Moments and log P_MP equal qem_estep's on
+ * the same single-level model and inputs.                                   */
 qem_status qem_estep_single_noalloc(const qem_level_desc* level, int K, const float* q_params, const float* eps,
                                     uint64_t seed, uint64_t iter, double* moments, double* log_pmp, void* stream);
 

@@ -138,6 +138,7 @@ void orc_draw_noise_at(uint64_t seed, uint64_t iter, int level, const int64_t* i
 /* digamma: psi(x+1) = psi(x) + 1/x to shift x >= 10, then the asymptotic
  * series  ln x - 1/(2x) - sum_n B_2n / (2n x^2n)  (Bernoulli numbers).      */
 double orc_digamma(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return NAN;  /* defined here for finite x > 0 only */
   double acc = 0.0;
   while (x < 10.0) { acc -= 1.0 / x; x += 1.0; }
   double f = 1.0 / (x * x);
@@ -148,6 +149,7 @@ double orc_digamma(double x) {
 /* trigamma: psi'(x) = psi'(x+1) + 1/x^2, then
  *  1/x + 1/(2x^2) + sum_n B_2n / x^(2n+1).                                   */
 double orc_trigamma(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return NAN;
   double acc = 0.0;
   while (x < 10.0) { acc += 1.0 / (x * x); x += 1.0; }
   double f = 1.0 / (x * x);
@@ -400,6 +402,8 @@ void orc_mstep_gauss(const double* m, int64_t n, int D, double var_floor, double
 /* Gamma(shape a, rate b) from (E z, E log z): log a - psi(a) = log E z - E log z,
  * b = a / E z.  Newton from Minka's (2002) closed-form start.                */
 static double gamma_shape(double s) {
+  /* Jensen: E log z < log E z for every non-degenerate Gamma, so s > 0 */
+  if (!(s > 0.0) || !isfinite(s)) return NAN;
   double a = (3.0 - s + sqrt((s - 3.0) * (s - 3.0) + 24.0 * s)) / (12.0 * s);
   for (int it = 0; it < 100; ++it) {
     double f = log(a) - orc_digamma(a) - s;
@@ -424,12 +428,20 @@ void orc_mstep_gamma(const double* m, int64_t n, int D, double* q_out) {
 
 /* Beta(a, b) from (E log z, E log(1-z)):
  *   psi(a) - psi(a+b) = E log z,  psi(b) - psi(a+b) = E log(1-z).
- * Start from psi(x) ~ log(x - 1/2), then 2-D Newton (Minka 2000).           */
+ * Start from psi(x) ~ log(x - 1/2), then 2-D Newton (Minka 2000).
+ * Jensen gives e^{E log z} + e^{E log(1-z)} < E z + E(1-z) = 1 for every
+ * Beta; statistics outside that domain (or non-finite) have no solution and
+ * give NaN parameters, as does a Newton run that cannot stay positive.      */
 void orc_mstep_beta(const double* m, int64_t n, int D, double* q_out) {
   for (int64_t e = 0; e < n; ++e)
     for (int d = 0; d < D; ++d) {
       double la = m[(e * 2) * D + d], lb = m[(e * 2 + 1) * D + d];
       double A = exp(la), B = exp(lb);
+      if (!isfinite(la) || !isfinite(lb) || !(A + B < 1.0)) {
+        q_out[(e * 2) * D + d] = NAN;
+        q_out[(e * 2 + 1) * D + d] = NAN;
+        continue;
+      }
       double t = 0.5 / (1.0 - A - B);
       double a = 0.5 + A * t, b = 0.5 + B * t;
       for (int it = 0; it < 200; ++it) {
@@ -439,7 +451,9 @@ void orc_mstep_beta(const double* m, int64_t n, int D, double* q_out) {
         double det = j11 * j22 - j12 * j12;
         double da = (j22 * g1 - j12 * g2) / det, db = (j11 * g2 - j12 * g1) / det;
         double an = a - da, bn = b - db;
-        while (an <= 0.0 || bn <= 0.0) { da *= 0.5; db *= 0.5; an = a - da; bn = b - db; }
+        int halvings = 0;
+        while ((an <= 0.0 || bn <= 0.0) && halvings < 64) { da *= 0.5; db *= 0.5; an = a - da; bn = b - db; ++halvings; }
+        if (!(an > 0.0 && bn > 0.0) || !isfinite(an) || !isfinite(bn)) { a = b = NAN; break; }
         double ch = fabs(an - a) / a + fabs(bn - b) / b;
         a = an; b = bn;
         if (ch < 1e-15) break;

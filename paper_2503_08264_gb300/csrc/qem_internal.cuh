@@ -342,7 +342,7 @@ cudaError_t launch_adj_small(const LevelView& v, const LevelView& parent, int K,
 cudaError_t configure_adj_small(int D, int K);
 cudaError_t launch_moments(const LevelView& v, int K, int threads, double* mom, cudaStream_t s);
 cudaError_t launch_mstep(const LevelView& v, const double* mom, double* m, float* q, double lambda,
-                         double sched_p, double var_floor, long long t_host, const Ctl* ctl, cudaStream_t s);
+                         double sched_p, double var_floor, long long t_host, Ctl* ctl, cudaStream_t s);
 size_t sample_local_smem(const LevelView& v, int K, int threads);
 constexpr int kSampleThreadsLimit = 256;   // largest sampler block the tuner tries
 cudaError_t configure_sample_local(size_t smem);

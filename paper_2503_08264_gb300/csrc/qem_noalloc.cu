@@ -1,9 +1,8 @@
 // Allocation-free E-step for single-level models (one latent per instance).
 //
 // Some callers cannot call cudaMalloc at the point where they need an
-// E-step: code running inside a CUDA-graph-captured region they do not own,
-// memory-pool-managed runtimes that forbid allocations outside their pool,
-// or real-time loops where an allocation's latency and implicit
+// E-step: memory-pool-managed runtimes that forbid allocations outside their
+// pool, or real-time loops where an allocation's latency and implicit
 // synchronisation are not acceptable.  For them this entry point keeps its
 // scratch (samples, local factors, weights, per-instance constants and the
 // control block) in one file-scope device array instead of a plan workspace,
@@ -28,6 +27,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of the scratch array, looked up once per device with that
 // device current (host code must not use the symbol itself as an address).
+// A cudaDeviceReset releases the module that holds the array, so a kept
+// address is not valid after one (documented in the header).
 void* g_scratch_addr[kMaxDevices] = {};
 
 inline size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }

@@ -744,7 +744,10 @@ cudaError_t launch_moments(const LevelView& v, int K, int threads, double* mom, 
 // Special functions for the Gamma/Beta M-steps: digamma and trigamma from
 // their recurrences (psi(x) = psi(x+1) - 1/x, psi'(x) = psi'(x+1) + 1/x^2)
 // and asymptotic expansions in 1/x^2 with Bernoulli-number coefficients.
+// Both are defined here for finite x > 0 only and return NaN otherwise (the
+// recurrence would not terminate for x = -inf or x below -2^53).
 __device__ double dev_digamma(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return nan("");
   double r = 0.0;
   for (; x < 8.0; x += 1.0) r -= 1.0 / x;
   const double x2 = 1.0 / (x * x);
@@ -754,6 +757,7 @@ __device__ double dev_digamma(double x) {
 }
 
 __device__ double dev_trigamma(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return nan("");
   double r = 0.0;
   for (; x < 8.0; x += 1.0) r += 1.0 / (x * x);
   const double x2 = 1.0 / (x * x);
@@ -766,9 +770,14 @@ __device__ double dev_trigamma(double x) {
 // Eq. ema, App. B): Gaussian mean/variance from (E z, E z^2) with a floor;
 // Gamma shape from log a - psi(a) = log E z - E log z (Newton from Minka's
 // closed-form start), rate = a / E z; Beta from psi(a) - psi(a+b) = E log z,
-// psi(b) - psi(a+b) = E log(1-z) (2-D Newton).
+// psi(b) - psi(a+b) = E log(1-z) (2-D Newton).  Statistics that no Gamma or
+// Beta matches (non-finite; E log z >= log E z for the Gamma; e^{E log z} +
+// e^{E log(1-z)} >= 1 for the Beta, reachable through rounding when the
+// weights collapse) and a Newton run that fails to reach a finite positive
+// solution keep the element's previous parameters and raise ERR_NUMERIC;
+// every loop is bounded.
 __global__ void k_mstep(LevelView v, const double* __restrict__ mom, double* m, float* q, double lambda,
-                        double sched_p, double var_floor, long long t_host, const Ctl* ctl) {
+                        double sched_p, double var_floor, long long t_host, Ctl* ctl) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int D = v.D;
   if (i >= v.n * D) return;
@@ -793,6 +802,10 @@ __global__ void k_mstep(LevelView v, const double* __restrict__ mom, double* m, 
     qb = sqrt(var);
   } else if (v.qfam == QEM_Q_GAMMA) {
     const double s = log(m0) - m1;
+    if (!(m0 > 0.0) || !isfinite(m0) || !isfinite(m1) || !(s > 0.0) || !isfinite(s)) {
+      atomicOr(&ctl->err, ERR_NUMERIC);
+      return;
+    }
     double a = (3.0 - s + sqrt((s - 3.0) * (s - 3.0) + 24.0 * s)) / (12.0 * s);
     for (int it = 0; it < 64; ++it) {
       const double step = (log(a) - dev_digamma(a) - s) / (1.0 / a - dev_trigamma(a));
@@ -802,26 +815,49 @@ __global__ void k_mstep(LevelView v, const double* __restrict__ mom, double* m, 
       a = an;
       if (done) break;
     }
+    if (!(a > 0.0) || !isfinite(a)) {
+      atomicOr(&ctl->err, ERR_NUMERIC);
+      return;
+    }
     qa = a;
     qb = a / m0;
   } else {
     const double A = exp(m0), B = exp(m1);
+    if (!isfinite(m0) || !isfinite(m1) || !(A + B < 1.0)) {
+      atomicOr(&ctl->err, ERR_NUMERIC);
+      return;
+    }
     const double h = 0.5 / (1.0 - A - B);
     double a = 0.5 + A * h, b = 0.5 + B * h;
-    for (int it = 0; it < 128; ++it) {
+    bool bad = !(a > 0.0 && b > 0.0 && isfinite(a) && isfinite(b));
+    for (int it = 0; it < 128 && !bad; ++it) {
       const double ps = dev_digamma(a + b), ts = dev_trigamma(a + b);
       const double g1 = dev_digamma(a) - ps - m0, g2 = dev_digamma(b) - ps - m1;
       const double h11 = dev_trigamma(a) - ts, h22 = dev_trigamma(b) - ts, h12 = -ts;
       const double det = h11 * h22 - h12 * h12;
       double da = (h22 * g1 - h12 * g2) / det, db = (h11 * g2 - h12 * g1) / det;
-      while (a - da <= 0.0 || b - db <= 0.0) {
+      if (!isfinite(da) || !isfinite(db)) {
+        bad = true;
+        break;
+      }
+      int halvings = 0;
+      while ((a - da <= 0.0 || b - db <= 0.0) && halvings < 64) {
         da *= 0.5;
         db *= 0.5;
+        ++halvings;
+      }
+      if (a - da <= 0.0 || b - db <= 0.0) {
+        bad = true;
+        break;
       }
       const double rel = fabs(da) / a + fabs(db) / b;
       a -= da;
       b -= db;
       if (rel < 1e-15) break;
+    }
+    if (bad || !(a > 0.0 && b > 0.0) || !isfinite(a) || !isfinite(b)) {
+      atomicOr(&ctl->err, ERR_NUMERIC);
+      return;
     }
     qa = a;
     qb = b;
@@ -831,7 +867,7 @@ __global__ void k_mstep(LevelView v, const double* __restrict__ mom, double* m, 
 }
 
 cudaError_t launch_mstep(const LevelView& v, const double* mom, double* m, float* q, double lambda, double sched_p,
-                         double var_floor, long long t_host, const Ctl* ctl, cudaStream_t s) {
+                         double var_floor, long long t_host, Ctl* ctl, cudaStream_t s) {
   const long long tot = v.n * v.D;
   if (tot == 0) return cudaSuccess;
   k_mstep<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(v, mom, m, q, lambda, sched_p, var_floor, t_host, ctl);

@@ -245,6 +245,28 @@ def test_mstep_round_trips():
     np.testing.assert_allclose(q[:, 1], b, rtol=1e-10)
 
 
+@pytest.mark.timeout(60)
+def test_mstep_outside_the_family_domain_gives_nan():
+    """Statistics no Gamma or Beta has (Jensen: E log z < log E z, and
+    e^{E log z} + e^{E log(1-z)} < 1) give NaN parameters, promptly; the
+    special functions are NaN outside x > 0 (their recurrences would not end
+    at x = -inf)."""
+    for x in (0.0, -1.0, -np.inf, -1e300, np.nan):
+        assert np.isnan(O.digamma(x)) and np.isnan(O.trigamma(x))
+    la = np.log(0.6)
+    m = np.array([[[la, la + 1e-3, la, np.nan, -0.9]], [[np.log(0.4) + 1e-12, np.log(0.4) - 1e-3, -np.inf, la, -0.7]]])
+    m = np.moveaxis(m, 0, 1)                       # [n=1][2][D=5]
+    q = O.mstep(O.Q_BETA, m)
+    assert np.all(np.isnan(q[0, :, :4]))           # A + B >= 1, -inf, NaN
+    assert np.all(np.isfinite(q[0, :, 4])) and np.all(q[0, :, 4] > 0)
+    a, b = q[0, 0, 4], q[0, 1, 4]
+    np.testing.assert_allclose([special.digamma(a) - special.digamma(a + b),
+                                special.digamma(b) - special.digamma(a + b)], [-0.9, -0.7], rtol=1e-10)
+    g = np.array([[[2.0, 2.0, -1.0], [np.log(2.0), np.log(2.0) + 0.1, 0.0]]])  # s = 0, s < 0, E z < 0
+    qg = O.mstep(O.Q_GAMMA, g)
+    assert np.all(np.isnan(qg))
+
+
 def test_gauss_mstep_variance_floor():
     m = np.array([[[2.0], [4.0]]])   # var 0: the single-dominant-sample pathology (Sec. 4)
     q = O.mstep(O.Q_GAUSS, m, var_floor=1e-6)

@@ -205,6 +205,38 @@ def test_mstep_matches_oracle():
         plan.close()
 
 
+def test_mstep_outside_the_family_domain_raises_numeric():
+    """Beta statistics with e^{E log z} + e^{E log(1-z)} just above 1 (reachable
+    through rounding when the weights collapse) have no solution: the M-step
+    keeps that element's previous parameters, fits the others, and the next
+    qem_log_pmp reports QEM_ERR_NUMERIC."""
+    from scipy import special
+    from paper_2503_08264_gb300 import _lib as L
+    model = S.beta_bernoulli(n_inst=4, N=3, seed=1)
+    plan = _plan(model, 8)
+    q0 = [np.full((4, 2, 1), 2.0)]
+    q_d = plan.flat(q0)
+    plan.estep(q_d, None, seed=1, it=1)
+    assert np.all(np.isfinite(plan.log_pmp()))
+    a = np.array([[1.5], [3.0], [0.7], [9.0]])
+    b = np.array([[2.5], [0.8], [4.0], [2.0]])
+    m = np.stack([special.digamma(a) - special.digamma(a + b), special.digamma(b) - special.digamma(a + b)], 1)
+    m[2, 0, 0] = np.log(0.5) + 1e-9
+    m[2, 1, 0] = np.log(0.5) + 1e-9          # A + B = 1 + 2e-9
+    m_d = plan.flat([m], torch.float64)
+    plan.mstep(None, m_d, q_d, 1.0)
+    torch.cuda.synchronize()
+    got = plan.split_q(q_d)[0]
+    np.testing.assert_array_equal(got[2], q0[0][2])
+    keep = [0, 1, 3]
+    np.testing.assert_allclose(got[keep, 0], a[keep], rtol=1e-6)
+    np.testing.assert_allclose(got[keep, 1], b[keep], rtol=1e-6)
+    with pytest.raises(L.QemError) as ei:
+        plan.log_pmp()
+    assert ei.value.code == L.QEM_ERR_NUMERIC
+    plan.close()
+
+
 def test_ema_schedule_theorem_1():
     """sched_p replaces lambda by t^-p (Thm. 1's schedule)."""
     model = S.gamma_poisson(n_inst=2, N=2)

@@ -1,7 +1,7 @@
 """GPU test of the allocation-free single-level E-step.
 
 Callers that cannot allocate device memory at the moment they need an
-E-step (a graph capture they do not own, a pool-managed runtime, a
+E-step (a runtime whose memory pool forbids outside allocations, a
 latency-bound loop) use qem_estep_single_noalloc, whose scratch is a
 library-wide device array.  It must give the same moments and log P_MP as the
 planned E-step on the same single-level model and inputs, on consecutive
