@@ -50,6 +50,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "hier_logistic_M5000_N10_K1024"
 EMA_LAMBDA = 0.5
+CONVERGE_ITERS = 100   # Alg. 1 iterations run before the timed region (EM steady state)
 
 
 def parse(argv=None):
@@ -59,7 +60,7 @@ def parse(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    p.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"])
+    p.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3", "tf32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -112,23 +113,88 @@ def aggregate(local_ms: float, local_units: float, ws: int, device=None):
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled every 5 ms during the
+    timed region, read through NVML (libnvidia-ml, the library nvidia-smi
+    reports from; read-only queries), with `nvidia-smi -lms 50` as the fallback.
+    The GPU is found by its PCI address, so the sample follows the CUDA device
+    under any CUDA_VISIBLE_DEVICES."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # clock-event reason bits of nvmlDeviceGetCurrentClocksEventReasons
+    REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                   0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    PERIOD_S = 0.005
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, cuda_device: int):
+        self.dev = cuda_device
         self.proc = None
         self.path = None
+        self.thread = None
+        self.samples = []
+        self.nvml = None
+        self.handle = None
+
+    def _nvml_open(self):
+        import ctypes as C
+        try:
+            nv = C.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return False
+        if nv.nvmlInit_v2() != 0:
+            return False
+        h = C.c_void_p()
+        ok = False
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.dev)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+            ok = nv.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(bus), C.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok:
+            ok = nv.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.dev), C.byref(h)) == 0
+        if not ok:
+            return False
+        self.nvml, self.handle = nv, h
+        return True
+
+    def _nvml_read(self):
+        import ctypes as C
+        sm, smax, pw, rs = C.c_uint(), C.c_uint(), C.c_uint(), C.c_ulonglong()
+        nv, h = self.nvml, self.handle
+        if nv.nvmlDeviceGetClockInfo(h, 1, C.byref(sm)) != 0:          # NVML_CLOCK_SM
+            return None
+        nv.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(smax))
+        nv.nvmlDeviceGetPowerUsage(h, C.byref(pw))
+        f = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        f(h, C.byref(rs))
+        return float(sm.value), float(smax.value), pw.value / 1000.0, int(rs.value)
+
+    def _loop(self):
+        while not self.stop_evt.is_set():
+            r = self._nvml_read()
+            if r is not None:
+                self.samples.append(r)
+            self.stop_evt.wait(self.PERIOD_S)
 
     def start(self):
+        import threading
+        if self._nvml_open() and self._nvml_read() is not None:
+            self.stop_evt = threading.Event()
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+            t0 = time.perf_counter()
+            while not self.samples and time.perf_counter() - t0 < 2.0:
+                time.sleep(0.001)
+            return
         try:
             fd, self.path = tempfile.mkstemp(prefix="qem_clocks_", suffix=".csv")
             os.close(fd)
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
             # the timed region starts once the sampler is producing samples
@@ -139,6 +205,15 @@ class ClockSampler:
             self.proc = None
 
     def stop(self) -> dict:
+        if self.thread is not None:
+            self.stop_evt.set()
+            self.thread.join(timeout=2.0)
+            sm = [x[0] for x in self.samples]
+            smax = [x[1] for x in self.samples]
+            reasons = sorted({nm for x in self.samples for bit, nm in self.REASON_BITS.items() if x[3] & bit})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                    "reasons": reasons, "samples": len(sm), "source": "NVML, 5 ms period",
+                    "power_w_max": max(x[2] for x in self.samples) if self.samples else None}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         self.proc.terminate()
@@ -164,7 +239,7 @@ class ClockSampler:
                         reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 50 ms period"}
 
 
 # --------------------------------------------------------------------------- roofline
@@ -180,6 +255,8 @@ def measured_peaks():
 # launch): FP32 CUDA-core path = FP32 pipe (128 lanes/clk/SM), tensor-core
 # path = MUFU ex2 (1 exponential per pair; 32 per clk per SM on GB300).
 SMS = 152
+# where the per-SM unit rates come from (probe method, cycle counts, clocks)
+PEAK_SOURCE = "profiles/mufu_fp32_peaks.md"
 
 
 # DRAM bytes per launch of a dominant kernel from one ncu capture
@@ -221,7 +298,8 @@ def roofline_for(kind: str, precision: str, D: int, pairs: float, ms: float, sm_
         model = f"MUFU ex2: 1/pair, 32/clk/SM x {SMS} SMs x {clk / 1e6:.0f} MHz"
     achieved = pairs / (ms * 1e-3)
     return {"bound": "alu", "kernel": kind, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-            "frac": achieved / peak, "traffic": None, "model": model + " (derived from unit counts and max clock)"}
+            "frac": achieved / peak, "traffic": None, "model": model + " (derived from unit counts and max clock)",
+            "peak_source": PEAK_SOURCE}
 
 
 # --------------------------------------------------------------------------- CPU oracle baseline
@@ -538,23 +616,26 @@ def run_ours(args):
         plan.estep(q_d, None, seed=seed, it=t, moments=mom_d, log_pmp=lp_d)
         plan.mstep(mom_d, m_d, q_d, EMA_LAMBDA, t=t)
 
-    t_iter = 1
+    with torch.cuda.stream(stream):
+        # EM steady state before anything is timed: a fixed number of Alg. 1
+        # iterations from q_0 as one graph launch (the first call autotunes the
+        # launch shapes), whatever --warmup and --steps are; the adjoint's work
+        # grows with the root samples that keep weight as the proposal converges
+        plan.run(CONVERGE_ITERS, EMA_LAMBDA, m_d, q_d, moments=mom_d, seed=seed)
+    t_iter = CONVERGE_ITERS + 1
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step(t_iter)   # the first call autotunes the launch shapes
+            step(t_iter)
             t_iter += 1
-        # build the single-launch loop graph (timed separately below) from a copy
-        m_g, q_g = m_d.clone(), q_d.clone()
-        plan.run(1, EMA_LAMBDA, m_g, q_g, moments=mom_d, seed=seed)
     stream.synchronize()
     per_iter, per_call = plan.run_kernels()
     plan.log_pmp()  # raises on a non-finite estimate or a device error
+    m_g, q_g = m_d.clone(), q_d.clone()  # the single-launch loop (timed below) continues from a copy
     barrier(ws)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
     clocks.start()
-    plan.profile(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         ev0.record(stream)
@@ -567,11 +648,24 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     local_ms = ev0.elapsed_time(ev1)
-    prof = plan.profile_read()
-    plan.profile(False)
     lp_host = plan.log_pmp()
     max_ms, tot_pairs = aggregate(local_ms, pairs * args.steps, ws, device="cuda")
     value = tot_pairs / (max_ms * 1e-3)
+
+    # per-kernel device times from a second pass of as many steps (every kernel
+    # bracketed by CUDA events on the plan's stream; not the headline pass)
+    plan.profile(True)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        pe0.record(stream)
+        for _ in range(args.steps):
+            step(t_iter)
+            t_iter += 1
+        pe1.record(stream)
+    stream.synchronize()
+    prof = plan.profile_read()
+    prof_ms = pe0.elapsed_time(pe1)
+    plan.profile(False)
 
     # the same iterations as one graph launch (device-side loop, no host
     # round trip between iterations)
@@ -586,24 +680,32 @@ def run_ours(args):
     graph_loop = {"ms_per_step": g_ms / args.steps, "value": g_pairs / (g_ms * 1e-3),
                   "launches": int(per_iter * args.steps + per_call)}
 
-    # dominant kernel and its roofline (CUDA events on the plan's stream)
-    kind = max(prof, key=lambda k: prof[k][0])
-    k_ms, k_n = prof[kind]
-    # kernels of one iteration, counted in the loop graph (the host loop launches
-    # the same ones, its control set-up in place of the loop control)
+    # rooflines of the two contraction kernels (CUDA events on the plan's
+    # stream); the headline one is the kernel with the larger share of the step.
+    # Work per step: the forward evaluates every pair (K_parent x K_child per
+    # element); the adjoint only the pairs of kept parent samples (its
+    # compaction), counted from the last E-step's kept lists.
+    kept_tc, kept_all = plan.adjoint_pairs()
+    adj_pairs = kept_all if precision == "fp32" else kept_tc
     gpu_launches = int(per_iter * args.steps)
     sm_max = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
     D_child = model.levels[-1].dim
-    pairs_per_launch = pairs / max(1, (len(model.levels) - 1))
-    if kind in ("forward", "adjoint"):
-        roof = roofline_for(kind, precision, D_child, pairs_per_launch * k_n, k_ms, sm_max)
-        roof["traffic"] = ncu_traffic(kind, args.workload, precision)
-        if roof["traffic"] is not None:
-            roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
-    else:
-        roof = {"bound": "hbm", "kernel": kind, "achieved": None, "peak": measured_peaks().get("hbm_gbs"),
-                "unit": "GB/s", "frac": None, "traffic": None}
-    roof["share_of_step"] = k_ms / local_ms if local_ms else None
+    rooflines = {}
+    for kind, work in (("forward", pairs), ("adjoint", adj_pairs)):
+        k_ms, k_n = prof.get(kind, (0.0, 0))
+        if k_ms <= 0 or work <= 0:
+            continue
+        r = roofline_for(kind, precision, D_child, work * args.steps, k_ms, sm_max)
+        r["pairs_per_step"] = work
+        r["launches"] = k_n
+        r["ms_per_launch"] = k_ms / k_n
+        r["traffic"] = ncu_traffic(kind, args.workload, precision)
+        if r["traffic"] is not None:
+            r["traffic_unit"] = "bytes per launch (ncu dram read + write)"
+        r["share_of_step"] = k_ms / prof_ms if prof_ms else None
+        rooflines[kind] = r
+    kind = max(rooflines, key=lambda k: rooflines[k]["share_of_step"] or 0.0)
+    roof = rooflines[kind]
 
     # end to end through the C ABI with host buffers: the step's inputs are
     # copied from pinned host memory each step and its results read back
@@ -647,17 +749,20 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16",
-                                                                   "bf16x3": "bf16x3"}[precision],
+                                                                   "bf16x3": "bf16x3", "tf32": "tf32"}[precision],
                 "data": "synthetic",
                 "config": {"workload": args.workload, "K": K, "pairs_per_step_per_gpu": pairs,
                            "precision": precision, "noise": "in-kernel Philox4x32-10",
                            "step": "qem_estep + qem_mstep (one Alg. 1 iteration)",
+                           "state": f"EM steady state: {CONVERGE_ITERS} iterations from q_0 before the "
+                                    f"{args.warmup} warm-up and {args.steps} timed steps",
                            "l2": f"working set {ws_bytes / 1e9:.2f} GB > 129 MB L2 (no flush)",
                            "parallelism": f"replicas x{ws} (independent instances)",
                            "launch_shapes": plan.tuning(),
                            "proposal": "parent-conditioned, permutation copies" if args.qcond else "factorised"},
                 "graph_loop": graph_loop,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": gpu_launches,
                 "clocks": clk, "kernels_ms": {k: round(v[0], 4) for k, v in prof.items()},
                 "log_pmp_last": float(lp_host[0])}
         print(json.dumps(line))

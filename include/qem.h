@@ -85,7 +85,10 @@ enum { QEM_Q_GAUSS = 0, QEM_Q_GAMMA = 1, QEM_Q_BETA = 2 };
 enum {
   QEM_PREC_FP32 = 0,    /* FP32 CUDA-core contraction                                   */
   QEM_PREC_BF16 = 1,    /* tcgen05 BF16 operands, FP32 accumulation                      */
-  QEM_PREC_BF16X3 = 2   /* tcgen05 split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+  QEM_PREC_BF16X3 = 2,  /* tcgen05 split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+  QEM_PREC_TF32 = 3     /* tcgen05 kind::tf32, operands rounded to TF32 (10-bit mantissa),
+                         * one product per k-step, FP32 accumulation; the local factor h
+                         * enters as three TF32 parts, so only the bilinear terms round  */
 };
 
 typedef struct {
@@ -307,7 +310,8 @@ qem_status qem_run(qem_plan_t plan, int64_t T, double lambda, double sched_p, ui
                    double* mean_params, float* q_params, double* moments, double* log_pmp_trace);
 
 /* Autotuning of the launch shapes (sampler and moments block sizes; FP32
- * contraction rows per block and staged child samples): a coordinate search
+ * contraction rows per block and staged child samples; the tensor-core
+ * schedules of the forward and the adjoint): a coordinate search
  * timing whole E-steps on q_params (DEVICE float [q_len]) on the plan's
  * stream, keeping a candidate only when it is at least 3% faster; results do
  * not depend on the choice beyond rounding order of the FP32 contraction.
@@ -320,9 +324,20 @@ qem_status qem_run(qem_plan_t plan, int64_t T, double lambda, double sched_p, ui
  * capture.  No counterpart in the paper (launch configuration only).        */
 qem_status qem_tune(qem_plan_t plan, const float* q_params, int flags);
 
-/* The plan's launch shapes: HOST int [4] = sampler threads per block, moments
+/* Apply launch shapes without timing (HOST int [5], the layout qem_tune_get
+ * returns; every value one of the tuner's candidates, QEM_ERR_INVALID_ARG
+ * otherwise): results depend on the choice only through the rounding order
+ * of the FP32 contraction.  Synchronises the plan's stream; drops qem_run's
+ * cached graph.  No counterpart in the paper (launch configuration only).   */
+qem_status qem_tune_set(qem_plan_t plan, const int* params);
+
+/* The plan's launch shapes: HOST int [5] = sampler threads per block, moments
  * threads per block, FP32 contraction rows per block, FP32 staged child
- * samples.                                                                    */
+ * samples, tensor-core schedules (bit 0: the forward keeps a whole element's
+ * operand rows in shared memory while the parent's row blocks stream; bit 1:
+ * the adjoint keeps the element's rows, four row blocks per pass, while the
+ * parent's kept rows stream; each used when its operands fit; a clear bit:
+ * one row block per CTA, the other operand streamed).  Default 1.           */
 qem_status qem_tune_get(qem_plan_t plan, int* params);
 
 /* ------------------------------------------------------------------------
@@ -379,6 +394,16 @@ qem_status qem_mlp_to_q(const float* out, int64_t n, float* q_params, void* stre
  * kernels each qem_run call launches outside the loop.                        */
 qem_status qem_run_kernels(qem_plan_t plan, int64_t* per_iteration, int64_t* per_call);
 
+/* Work of the last E-step's adjoint (tracing support, not part of the
+ * method): the (kept parent sample, child sample) pairs over every element
+ * below the root, where a parent keeps the samples whose weight is at least
+ * 2^-40 (FP32 plans) or 2^-24 (mixed-precision plans) of its largest (the
+ * adjoint's compaction); kept_tc counts those of parents keeping more than
+ * four samples on a mixed-precision plan (the tensor-core adjoint's share).
+ * Chain plates are not counted.  HOST doubles, either may be NULL;
+ * synchronises the plan's stream.                                          */
+qem_status qem_adjoint_pairs(qem_plan_t plan, double* kept_tc, double* kept_all);
+
 /* Kernel classes of the per-kernel profiler. */
 enum {
   QEM_K_SAMPLE = 0,      /* sampling and local factors                 */
@@ -391,7 +416,8 @@ enum {
   QEM_K_MOMENTS = 7,     /* moments                                    */
   QEM_K_MSTEP = 8,       /* EMA + M-step                               */
   QEM_K_OPERANDS = 9,    /* tensor-core operand features / compaction  */
-  QEM_K_COUNT = 10
+  QEM_K_ADJ_SMALL = 10,  /* adjoint of parents keeping few samples (CUDA cores, mixed-precision plans) */
+  QEM_K_COUNT = 11
 };
 
 /* Per-kernel timing (tracing support, not part of the method): while enabled,

@@ -16,7 +16,7 @@ QEM_MAX_LEVELS = 4
 QEM_GAMMA_TRIES = 8
 
 QEM_OK, QEM_ERR_INVALID_ARG, QEM_ERR_UNSUPPORTED, QEM_ERR_OOM, QEM_ERR_CUDA, QEM_ERR_NUMERIC, QEM_ERR_TIMEOUT = range(7)
-QEM_PREC_FP32, QEM_PREC_BF16, QEM_PREC_BF16X3 = 0, 1, 2
+QEM_PREC_FP32, QEM_PREC_BF16, QEM_PREC_BF16X3, QEM_PREC_TF32 = 0, 1, 2, 3
 QEM_TILE_AUTO, QEM_TUNE_FORCE = -1, 1
 QEM_MLP_DIM, QEM_MLP_HIDDEN, QEM_MLP_PARAMS = 18, 128, 26020
 
@@ -71,6 +71,8 @@ SIGNATURES = {
     "qem_run_kernels": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "qem_tune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "qem_tune_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "qem_tune_set": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "qem_adjoint_pairs": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "qem_mlp_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "qem_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "qem_mlp_workspace_size": (C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
@@ -84,7 +86,7 @@ SIGNATURES = {
 }
 
 QEM_K_NAMES = ["sample_local", "parent_params", "finalize", "forward", "plate_sum", "root", "adjoint", "moments",
-               "mstep", "operands"]
+               "mstep", "operands", "adjoint_small"]
 
 _lib = None
 

@@ -43,7 +43,7 @@ qem_status validate(const qem_model_desc* desc, const qem_plan_opts* o) {
   if (!desc || !o) return QEM_ERR_INVALID_ARG;
   if (desc->n_levels < 1 || desc->n_levels > QEM_MAX_LEVELS) return QEM_ERR_INVALID_ARG;
   if (o->K < 1 || o->K > 4096) return QEM_ERR_INVALID_ARG;
-  if (o->precision < QEM_PREC_FP32 || o->precision > QEM_PREC_BF16X3) return QEM_ERR_INVALID_ARG;
+  if (o->precision < QEM_PREC_FP32 || o->precision > QEM_PREC_TF32) return QEM_ERR_INVALID_ARG;
   if (o->var_floor < 0 || o->timeout_s < 0) return QEM_ERR_INVALID_ARG;
   if (o->tile != 0 && o->tile != QEM_TILE_AUTO) return QEM_ERR_INVALID_ARG;
   const int L = desc->n_levels;
@@ -218,7 +218,7 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
     if (P->precision == QEM_PREC_FP32) {
       QEM_LAUNCH(P, QEM_K_ADJOINT, launch_adj_compact(P->lv[l], P->lv[l - 1], K, 0, s));
     } else {
-      QEM_LAUNCH(P, QEM_K_ADJOINT, launch_adj_small(P->lv[l], P->lv[l - 1], K, s));
+      QEM_LAUNCH(P, QEM_K_ADJ_SMALL, launch_adj_small(P->lv[l], P->lv[l - 1], K, s));
       QEM_LAUNCH(P, QEM_K_OPERANDS, tc_adjoint_prep(P, l));
       QEM_LAUNCH(P, QEM_K_ADJOINT, tc_adjoint(P, l));
     }
@@ -257,6 +257,7 @@ const int kSampleCand[] = {64, 128, 256};
 const int kMomCand[] = {128, 256, 512};
 const int kRowsCand[] = {64, 128, 256};
 const int kChunkCand[] = {16, 32, 64};
+const int kSchedCand[] = {1, 3, 0, 2};
 
 template <size_t N>
 bool one_of(int v, const int (&c)[N]) {
@@ -266,7 +267,7 @@ bool one_of(int v, const int (&c)[N]) {
 }
 bool tune_valid(const Tune& t) {
   return one_of(t.sample_threads, kSampleCand) && one_of(t.mom_threads, kMomCand) && one_of(t.fwd_rows, kRowsCand) &&
-         one_of(t.fwd_chunk, kChunkCand);
+         one_of(t.fwd_chunk, kChunkCand) && one_of(t.tc_sched, kSchedCand);
 }
 
 std::string tune_signature(const qem_plan_s* P) {
@@ -300,7 +301,8 @@ void tune_read_file_locked() {
     if (!bar) continue;
     *bar = 0;
     Tune t;
-    if (std::sscanf(bar + 1, "%d %d %d %d", &t.sample_threads, &t.mom_threads, &t.fwd_rows, &t.fwd_chunk) == 4 &&
+    if (std::sscanf(bar + 1, "%d %d %d %d %d", &t.sample_threads, &t.mom_threads, &t.fwd_rows, &t.fwd_chunk,
+                    &t.tc_sched) == 5 &&
         tune_valid(t))
       g_tune_cache[line] = t;
   }
@@ -312,7 +314,8 @@ void tune_store_locked(const std::string& sig, const Tune& t) {
   const char* path = tune_file();
   FILE* f = path ? std::fopen(path, "a") : nullptr;
   if (!f) return;
-  std::fprintf(f, "%s|%d %d %d %d\n", sig.c_str(), t.sample_threads, t.mom_threads, t.fwd_rows, t.fwd_chunk);
+  std::fprintf(f, "%s|%d %d %d %d %d\n", sig.c_str(), t.sample_threads, t.mom_threads, t.fwd_rows, t.fwd_chunk,
+               t.tc_sched);
   std::fclose(f);
 }
 
@@ -383,7 +386,10 @@ extern "C" qem_status qem_tune(qem_plan_t P, const float* q_params, int flags) {
     try_knob(&Tune::fwd_rows, kRowsCand, 3);
     try_knob(&Tune::fwd_chunk, kChunkCand, 3);
   }
+  if (P->precision != QEM_PREC_FP32 && P->L > 1) try_knob(&Tune::tc_sched, kSchedCand, 4);
   P->tune = best;
+  delete static_cast<RunGraph*>(P->run);  // a loop graph built before holds the old launch shapes
+  P->run = nullptr;
   if (mom) {
     if (cudaStreamSynchronize(P->stream) != cudaSuccess && st == QEM_OK) st = QEM_ERR_CUDA;
     cudaFree(mom);
@@ -398,12 +404,30 @@ extern "C" qem_status qem_tune(qem_plan_t P, const float* q_params, int flags) {
   return st;
 }
 
+extern "C" qem_status qem_tune_set(qem_plan_t P, const int* params) {
+  if (!P || !params) return QEM_ERR_INVALID_ARG;
+  Tune t;
+  t.sample_threads = params[0];
+  t.mom_threads = params[1];
+  t.fwd_rows = params[2];
+  t.fwd_chunk = params[3];
+  t.tc_sched = params[4];
+  if (!tune_valid(t)) return QEM_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEM_ERR_CUDA;
+  P->tune = t;
+  P->tuned = true;
+  delete static_cast<RunGraph*>(P->run);  // the loop graph holds the old launch shapes
+  P->run = nullptr;
+  return QEM_OK;
+}
+
 extern "C" qem_status qem_tune_get(qem_plan_t P, int* params) {
   if (!P || !params) return QEM_ERR_INVALID_ARG;
   params[0] = P->tune.sample_threads;
   params[1] = P->tune.mom_threads;
   params[2] = P->tune.fwd_rows;
   params[3] = P->tune.fwd_chunk;
+  params[4] = P->tune.tc_sched;
   return QEM_OK;
 }
 
@@ -938,6 +962,29 @@ qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint6
   return st;
 }
 
+qem_status qem_adjoint_pairs(qem_plan_t P, double* kept_tc, double* kept_all) {
+  if (!P) return QEM_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEM_ERR_CUDA;
+  double tc = 0.0, all = 0.0;
+  for (int l = 1; l < P->L; ++l) {
+    const LevelView& pa = P->lv[l - 1];
+    if (pa.n == 0 || P->lv[l].chain > 1) continue;
+    std::vector<int> cnt((size_t)pa.n);
+    std::vector<long long> co((size_t)pa.n + 1);
+    if (cudaMemcpy(cnt.data(), pa.ccnt, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(co.data(), pa.child_off, sizeof(long long) * co.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return QEM_ERR_CUDA;
+    for (long long p = 0; p < pa.n; ++p) {
+      const double pairs = (double)cnt[(size_t)p] * (double)(co[(size_t)p + 1] - co[(size_t)p]) * P->K;
+      all += pairs;
+      if (P->precision != QEM_PREC_FP32 && cnt[(size_t)p] > kSmallKept) tc += pairs;
+    }
+  }
+  if (kept_tc) *kept_tc = tc;
+  if (kept_all) *kept_all = all;
+  return QEM_OK;
+}
+
 qem_status qem_run_kernels(qem_plan_t P, int64_t* per_iteration, int64_t* per_call) {
   if (!P || !per_iteration || !per_call) return QEM_ERR_INVALID_ARG;
   RunGraph* R = run_of(P);
@@ -959,7 +1006,7 @@ qem_status qem_run_kernels(qem_plan_t P, int64_t* per_iteration, int64_t* per_ca
 
 static const char* kKindNames[QEM_K_COUNT] = {"sample_local", "parent_params", "finalize", "forward",
                                               "plate_sum",    "root",          "adjoint",  "moments",
-                                              "mstep",        "operands"};
+                                              "mstep",        "operands",      "adjoint_small"};
 
 const char* qem_profile_name(int kind) { return kind >= 0 && kind < QEM_K_COUNT ? kKindNames[kind] : nullptr; }
 

@@ -27,255 +27,11 @@
 #include <new>
 
 #include "qem_tc.cuh"
+#include "qem_tc_ptx.cuh"
 
 namespace qem {
 
-// Column layout of the operand rows of one level (bf16 columns, canonical
-// K-major core-matrix layout).  Parent rows (A of the forward):
-//   [Ah | 1 1 1 | .. | Ah at a_ah2 | .. | Al at a_al | 0..]   (split 3)
-// child rows (B of the forward):
-//   [Bh | h1 h2 h3 | .. | Bl at b_bl | (Bh at b_bh2) | 0..]
-// and a table of MMA k-steps pairing parent columns ka[i]..+16 with child
-// columns kb[i]..+16.  When it saves child bytes, the lo*hi product re-reads
-// the first Bh block instead of storing Bh twice (b_bh2 = -1), with the
-// ragged tail of that product packed into the padding (tail, a_alt, b_bht).
-struct Layout {
-  int nb = 0, split = 1;
-  int fka = 0, fkb = 0;
-  int a_ah2 = -1, a_al = -1, b_bl = -1, b_bh2 = -1;
-  // compact form: the last `tail` features of the lo*hi product sit in the
-  // padding after the Ah/Bl block (parent Al at a_alt, child Bh copy at
-  // b_bht); the Al block at a_al then holds only the first nb - tail.
-  int tail = 0, a_alt = -1, b_bht = -1;
-  int nks = 0;
-  int ka[16] = {}, kb[16] = {};
-};
-
-struct TcBuffers {
-  Layout lay[QEM_MAX_LEVELS];
-  int nb[QEM_MAX_LEVELS] = {};   // bilinear features of child level l
-  int split = 3;
-  __nv_bfloat16* bfeat[QEM_MAX_LEVELS] = {};   // child level l:   [n_l][K rows][fkb] canonical
-  __nv_bfloat16* afeat[QEM_MAX_LEVELS] = {};   // parent of l:     [n_{l-1}][K rows][fka]
-  __nv_bfloat16* cfeat[QEM_MAX_LEVELS] = {};   // compacted parent rows, same layout
-  float* rowc[QEM_MAX_LEVELS] = {};            // [n_{l-1}][K] row constants (nats)
-  float* center[QEM_MAX_LEVELS] = {};          // [n_{l-1}][D_l]
-  float* dcol[QEM_MAX_LEVELS] = {};            // [n_l][K] adjoint column shifts (log2 units)
-};
-
 namespace tc {
-
-constexpr int kRows = 128;        // MMA M: rows of one work unit
-constexpr int kMaxN = 256;        // MMA N of one column chunk
-constexpr int kEpiWarps = 16;    // 4 per TMEM lane quarter, each owning a quarter of a chunk's columns
-constexpr int kBStagesMax = 4;   // column-operand ring depth limit (one producer warp per stage)
-constexpr int kProdWarps = 1 + kBStagesMax;      // warp 0: row operand, warps 1..4: one column stage each
-constexpr int kMmaWarp = kProdWarps;             // warp 5: MMA issuer, TMEM owner
-constexpr int kEpiWarp0 = kProdWarps + 1;        // warps 6..21: epilogue
-constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
-constexpr int kMaxFK = 128;
-constexpr float kLog2e = 1.4426950408889634f;
-constexpr float kLn2 = 0.6931471805599453f;
-constexpr float kNegBig = -1.0e30f;
-
-// ---------------------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on a barrier phase: false (and the CTA abort flag set) when the
-// wait exceeds `limit` cycles or another role of the CTA has aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit, volatile int* abort_flag) {
-  if (mbar_try_wait(b, parity)) return true;
-  const long long t0 = clock64();
-  for (;;) {
-    if (mbar_try_wait(b, parity)) return true;
-    if (*abort_flag) return false;
-    if (clock64() - t0 > limit) {
-      *abort_flag = 1;
-      return false;
-    }
-  }
-}
-// Non-suspending variant for the single MMA-issuing thread: polls with
-// test_wait so it reacts to a completed phase at once.
-__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_spin(uint64_t* b, uint32_t parity, long long limit, volatile int* abort_flag) {
-  const long long t0 = clock64();
-  for (int i = 0;; ++i) {
-    if (mbar_test(b, parity)) return true;
-    if ((i & 63) == 63) {
-      if (*abort_flag) return false;
-      if (clock64() - t0 > limit) {
-        *abort_flag = 1;
-        return false;
-      }
-    }
-  }
-}
-__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 in, FP32 accumulate), one elected thread.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// Shared-memory matrix descriptor: canonical K-major layout without swizzle.
-// start address, leading-dimension byte offset (between core matrices along
-// K), stride byte offset (between 8-row groups), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
-  const uint32_t a = smem_u32(p);
-  return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-// Instruction descriptor: BF16 A and B (K-major), FP32 D, M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
-}
-
-// TMEM -> registers (load and wait in one block, so the outputs are valid after it).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
-  uint32_t r[64];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
-  uint32_t r[4];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Split TMEM load: issue (outputs valid only after tmem_wait on the same
-// registers; the in-out operands of the wait order every use after it).
-__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-               : "r"(taddr)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) : : "memory");
-}
-
-__device__ __forceinline__ float ex2f(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Element (row, col) of a canonical tile with fk columns: bf16 index.
-__host__ __device__ __forceinline__ long long canon(long long row, int col, int fk) {
-  return ((row >> 3) * (fk >> 3) + (col >> 3)) * 64 + (row & 7) * 8 + (col & 7);
-}
-
-__device__ __forceinline__ void split2(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn(x);
-  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-}
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-  if (!(x > kNegBig)) {  // -inf / very negative / NaN-safe: a large finite negative
-    a = __float2bfloat16_rn(isnan(x) ? x : kNegBig);
-    b = c = __float2bfloat16_rn(0.f);
-    return;
-  }
-  a = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(a);
-  b = __float2bfloat16_rn(r1);
-  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
-}
 
 // ---------------------------------------------------------------------------- feature builders
 // Parent side (A rows of the forward tile, B columns of the adjoint): for each
@@ -496,6 +252,130 @@ __global__ void __launch_bounds__(128) k_child_features_t(LevelView ch, float pp
   }
 }
 
+// ---------------------------------------------------------------------------- TF32 operand rows
+// TF32 mode: one product per k-step, every operand value an FP32 word rounded
+// to TF32 (cvt.rna; the tensor core reads the upper 19 bits), rows of nb + 3
+// values padded to a multiple of 8 (one kind::tf32 k-step), in the same
+// canonical byte layout (a 16-byte granule holds 4 values; widths and column
+// offsets are given in 16-bit units, 2 per value):
+//   parent rows  [A (nb) | 1 1 1 | 0..]        child rows  [B (nb) | h1 h2 h3 | 0..]
+// with h = h1 + h2 + h3 its three-part TF32 split (33 significant bits).
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void split3_tf32(float x, float& a, float& b, float& c) {
+  if (!(x > kNegBig)) {  // -inf / very negative / NaN-safe, as split3
+    a = isnan(x) ? x : kNegBig;
+    b = c = 0.f;
+    return;
+  }
+  a = tf32_rna(x);
+  const float r1 = x - a;
+  b = tf32_rna(r1);
+  c = tf32_rna(r1 - b);
+}
+
+__global__ void k_parent_features_tf32(LevelView par, int Dc, int mean_logvar, int K, int fk, int nb,
+                                       __nv_bfloat16* afeat, float* rowc, float* center) {
+  const long long p = blockIdx.x;
+  __shared__ float cen[kMaxDim];
+  __shared__ float red[8][kMaxDim];
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = 0; d < Dc; ++d) {
+      float acc = 0.f;
+      for (int kp = threadIdx.x; kp < K; kp += blockDim.x) acc += par.pm[(p * K + kp) * Dc + d];
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) red[warp][d] = acc;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < Dc; d += blockDim.x) {
+      float t = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][d];
+      cen[d] = t / K;
+      center[p * Dc + d] = cen[d];
+    }
+    __syncthreads();
+  }
+  for (int kp = blockIdx.y * blockDim.x + threadIdx.x; kp < K; kp += gridDim.y * blockDim.x) {
+    const float* pm = par.pm + (p * K + kp) * Dc;
+    const float* pp = par.pp + (p * K + kp) * Dc;
+    double rc = par.pc[p * K + kp];
+    for (int d = 0; d < Dc; ++d) {
+      const float dm = pm[d] - cen[d];
+      rc += (double)pp[d] * dm * dm;
+    }
+    if (blockIdx.z == 0) rowc[p * K + kp] = (float)rc;
+    __nv_bfloat16* row = afeat + p * (long long)K * fk;
+    for (int c0 = 0; c0 < fk / 2; c0 += 4) {
+      float g[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int f = c0 + j;
+        if (f < nb) {
+          const float v = mean_logvar ? (f < Dc ? pp[f] : -2.f * pp[f - Dc] * (pm[f - Dc] - cen[f - Dc]))
+                                      : -2.f * pp[f] * (pm[f] - cen[f]);
+          g[j] = tf32_rna(v * kLog2e);
+        } else {
+          g[j] = f < nb + 3 ? 1.f : 0.f;
+        }
+      }
+      *reinterpret_cast<float4*>(row + canon(kp, 2 * c0, fk)) = make_float4(g[0], g[1], g[2], g[3]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_child_features_tf32(LevelView ch, int mean_logvar, float pp_fixed, int K,
+                                                             int fk, int nb, const float* center,
+                                                             __nv_bfloat16* bfeat) {
+  extern __shared__ float csm[];
+  const long long e = blockIdx.x;
+  const int D = ch.D, zst = D + 1, bst = nb + 4;
+  const long long p = ch.parent[e];
+  float* cen = csm;                      // [D]
+  float* zc = cen + D;                   // [128][D+1]
+  float* bf = zc + 128 * zst;            // [128][nb+4] row values (features, then h1 h2 h3)
+  for (int d = threadIdx.x; d < D; d += blockDim.x) cen[d] = center[p * D + d];
+  __nv_bfloat16* out = bfeat + e * (long long)K * fk;
+  const int nv = nb + 3, gran = fk >> 3;  // values per row; 16-byte granules per row
+  for (int k0 = 0; k0 < K; k0 += blockDim.x) {
+    const int nk = min((int)blockDim.x, K - k0);
+    __syncthreads();
+    stage_rows<0>(ch.z + (e * K + k0) * (long long)D, nk * D, D, zc);
+    __syncthreads();
+    if ((int)threadIdx.x < nk) {
+      const int r = threadIdx.x;
+      float ss = 0.f;
+      for (int d = 0; d < D; ++d) {
+        const float zp = zc[r * zst + d] - cen[d];
+        ss = fmaf(zp, zp, ss);
+        if (mean_logvar) {
+          bf[r * bst + d] = tf32_rna(zp * zp);
+          bf[r * bst + D + d] = tf32_rna(zp);
+        } else {
+          bf[r * bst + d] = tf32_rna(zp);
+        }
+      }
+      float h = ch.htil[e * K + k0 + r];
+      if (!mean_logvar) h = fmaf(pp_fixed, ss, h);
+      split3_tf32(h * kLog2e, bf[r * bst + nb], bf[r * bst + nb + 1], bf[r * bst + nb + 2]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nk * gran; i += blockDim.x) {
+      const int r = i % nk, g = i / nk;
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = 4 * g + j;
+        v[j] = c < nv ? bf[r * bst + c] : 0.f;
+      }
+      *reinterpret_cast<float4*>(out + canon(k0 + r, g * 8, fk)) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  }
+}
+
 // Adjoint operands of the parents whose compacted weight list is longer than
 // `small` (the others are handled on the CUDA cores): the kept rows of the
 // parent features, gathered in order (padding rows repeat row 0 and carry a
@@ -533,66 +413,6 @@ __global__ void k_dcol(LevelView ch, LevelView par, int K, int small, const floa
   }
 }
 
-
-// Online log-sum-exp of one row over the group of 32 values at TMEM address
-// taddr (log2 units): shift by the running maximum m (set from the first
-// group), all 32 subtractions, then all 32 exponentials, then a pairwise sum,
-// in place; a partial sum above 2^32 (a group far above the shift) is redone
-// from TMEM at the group's exact maximum, so the running sum never overflows.
-// Called by all 32 lanes of a warp together (it issues warp-collective loads).
-// Packed FP32 pair arithmetic (two lanes of work per instruction).
-__device__ __forceinline__ void sub2(float& a0, float& a1, float b) {
-  asm("{\n .reg .b64 x, y, r;\n mov.b64 x, {%0, %1};\n mov.b64 y, {%2, %2};\n"
-      " sub.rn.ftz.f32x2 r, x, y;\n mov.b64 {%0, %1}, r;\n}\n"
-      : "+f"(a0), "+f"(a1)
-      : "f"(b));
-}
-__device__ __forceinline__ void add2(float& a0, float& a1, float b0, float b1) {
-  asm("{\n .reg .b64 x, y, r;\n mov.b64 x, {%0, %1};\n mov.b64 y, {%2, %3};\n"
-      " add.rn.ftz.f32x2 r, x, y;\n mov.b64 {%0, %1}, r;\n}\n"
-      : "+f"(a0), "+f"(a1)
-      : "f"(b0), "f"(b1));
-}
-
-__device__ __forceinline__ void lse_group32(uint32_t taddr, float& m, float& sacc) {
-  float v[32];
-  tmem_ld32(taddr, v);
-  if (m == -INFINITY) {
-    float mx = v[0];
-#pragma unroll
-    for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
-    m = mx;
-  }
-#pragma unroll
-  for (int j = 0; j < 32; j += 2) sub2(v[j], v[j + 1], m);
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = ex2f(v[j]);
-  // pairwise tree on pairs: (v[2i], v[2i+1]) += (v[2i+w], v[2i+w+1])
-#pragma unroll
-  for (int w = 16; w >= 2; w >>= 1)
-#pragma unroll
-    for (int j = 0; j < w; j += 2) add2(v[j], v[j + 1], v[j + w], v[j + w + 1]);
-  float pt = v[0] + v[1];
-  const bool redo = !(pt <= 4294967296.0f);
-  // tcgen05.ld is warp-collective: the reload runs on the whole warp whenever
-  // any lane needs it, and only those lanes use it.
-  if (__any_sync(0xffffffffu, redo)) {
-    tmem_ld32(taddr, v);
-    if (redo) {
-      float mx = v[0];
-#pragma unroll
-      for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
-      if (mx > m) {
-        sacc *= ex2f(m - mx);
-        m = mx;
-      }
-      pt = 0.f;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) pt += ex2f(v[j] - m);
-    }
-  }
-  sacc += pt;
-}
 
 // ---------------------------------------------------------------------------- the contraction kernel
 // One work unit = 128 rows of one plate element.  Columns stream in chunks
@@ -649,7 +469,6 @@ __host__ __device__ inline size_t contract_smem_bytes(int frow, int fcol, bool a
   tot += 32 * 8 + 16 + kRows * 4 * sizeof(float2);
   return tot;
 }
-constexpr size_t kSmemLimit = 227 * 1024;
 // Shared-memory budget: a double-buffered row operand first (a new row block
 // per unit when parents change from unit to unit), then the deepest column
 // ring that fits (a chunk's MMAs are known complete only well after they
@@ -761,7 +580,7 @@ struct Walker {
   }
 };
 
-template <bool ADJ>
+template <bool ADJ, bool TF32>
 __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
   extern __shared__ uint8_t smem_raw[];
   Smem s = carve(smem_raw, a.frow, a.fcol, ADJ, a.a_slots, a.nst);
@@ -913,14 +732,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
           ok = mbar_spin(&s.b_full[bs], bph, lim, s.abort_flag) && mbar_spin(&s.t_empty[ts], tph ^ 1, lim, s.abort_flag);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t idesc = idesc_bf16(nc);
+          const uint32_t idesc = idesc_fmt(nc, TF32 ? 2u : 1u);
           const uint64_t bd = bdesc0 + (uint64_t)(bs * b_step);
           for (int r = 0; r < RT; ++r) {
             const uint32_t d_tmem = tmem + (uint32_t)(ts * 256 + r * kNB);
             const uint64_t ad = adesc0 + (uint64_t)(as * a_step + r * t_step);
 #pragma unroll
             for (int ks = 0; ks < 16; ++ks)
-              if (ks < nks) mma_bf16(d_tmem, ad + kro[ks], bd + kco[ks], idesc, ks > 0 ? 1u : 0u);
+              if (ks < nks) mma_kind<TF32>(d_tmem, ad + kro[ks], bd + kco[ks], idesc, ks > 0 ? 1u : 0u);
           }
           mma_commit(&s.b_empty[bs]);
           mma_commit(&s.t_full[ts]);
@@ -1127,10 +946,18 @@ static int up16(int x) { return (x + 15) & ~15; }
 static int up8(int x) { return (x + 7) & ~7; }
 
 // Operand layout of a level with nb bilinear features (see Layout).
+// split 0: TF32 rows [X (nb) | 1 1 1 or h1 h2 h3 | 0..], nb + 3 values padded
+// to a multiple of 8 (one kind::tf32 k-step of 32 bytes = 16 units).
 static Layout make_layout(int nb, int split) {
   Layout L;
   L.nb = nb;
   L.split = split;
+  if (split == 0) {
+    L.fka = L.fkb = 2 * up8(nb + 3);
+    L.nks = L.fka / 16;
+    for (int i = 0; i < L.nks; ++i) L.ka[i] = L.kb[i] = 16 * i;
+    return L;
+  }
   if (split == 1) {
     L.fka = L.fkb = up16(nb + 3);
     L.nks = L.fka / 16;
@@ -1175,9 +1002,10 @@ qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base,
   if (P->precision == QEM_PREC_FP32) return QEM_OK;
   const int K = P->K;
   if (K % kRows != 0) return QEM_ERR_UNSUPPORTED;
-  const int split = P->precision == QEM_PREC_BF16X3 ? 3 : 1;
+  const int split = P->precision == QEM_PREC_BF16X3 ? 3 : (P->precision == QEM_PREC_TF32 ? 0 : 1);
   TcBuffers tb;
   tb.split = split;
+  tb.tf32 = split == 0;
   size_t off = 0;
   auto take = [&](size_t b) -> char* {
     char* p = base ? base + off : nullptr;
@@ -1209,6 +1037,7 @@ qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base,
 
 qem_status tc_plan_init(qem_plan_t P, const qem_model_desc*) {
   if (P->precision == QEM_PREC_FP32) return QEM_OK;
+  const bool tf32 = P->tc->tf32;
   size_t sf = 0, sa = 0;
   for (int l = 1; l < P->L; ++l) {
     const Layout& L = P->tc->lay[l];
@@ -1217,11 +1046,18 @@ qem_status tc_plan_init(qem_plan_t P, const qem_model_desc*) {
     sf = std::max(sf, contract_smem_bytes(L.fka, L.fkb, false, na, ns));
     if (!contract_config(L.fkb, L.fka, true, na, ns)) return QEM_ERR_UNSUPPORTED;
     sa = std::max(sa, contract_smem_bytes(L.fkb, L.fka, true, na, ns));
+    const qem_status rs = tc_res_init(L.fka, L.fkb, P->K, tf32);
+    if (rs != QEM_OK) return rs;
   }
-  if (cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf) != cudaSuccess ||
-      cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess)
-    return QEM_ERR_CUDA;
-  return QEM_OK;
+  cudaError_t e1, e2;
+  if (tf32) {
+    e1 = cudaFuncSetAttribute(k_contract<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+    e2 = cudaFuncSetAttribute(k_contract<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+  } else {
+    e1 = cudaFuncSetAttribute(k_contract<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+    e2 = cudaFuncSetAttribute(k_contract<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+  }
+  return e1 == cudaSuccess && e2 == cudaSuccess ? QEM_OK : QEM_ERR_CUDA;
 }
 
 void tc_plan_release(qem_plan_t P) {
@@ -1238,6 +1074,19 @@ cudaError_t tc_features(qem_plan_t P, int l) {
   const Layout& L = T.lay[l];
   const int K = P->K, nb = T.nb[l];
   const int mlv = ch.prior == QEM_PRIOR_NORMAL_MEAN_LOGVAR ? 1 : 0;
+  if (T.tf32) {
+    if (pa.n > 0) {
+      const dim3 grid((unsigned)pa.n, (unsigned)std::max(1, std::min(16, (int)(2 * P->num_sms / std::max(1LL, pa.n)))));
+      k_parent_features_tf32<<<grid, 256, 0, P->stream>>>(pa, ch.D, mlv, K, L.fka, nb, T.afeat[l], T.rowc[l],
+                                                          T.center[l]);
+    }
+    if (ch.n > 0) {
+      const size_t sm = sizeof(float) * (size_t)(ch.D + 128 * (ch.D + 1) + 128 * (nb + 4));
+      k_child_features_tf32<<<(unsigned)ch.n, 128, sm, P->stream>>>(ch, mlv, -0.5f / ch.prior_a, K, L.fkb, nb,
+                                                                    T.center[l], T.bfeat[l]);
+    }
+    return cudaGetLastError();
+  }
   if (pa.n > 0) {
     const dim3 grid((unsigned)pa.n, (unsigned)std::max(1, std::min(16, (int)(2 * P->num_sms / std::max(1LL, pa.n)))));
     k_parent_features<<<grid, 256, 0, P->stream>>>(pa, ch.D, mlv, K, L.fka, nb, T.split, L.a_ah2, L.a_al, L.a_alt,
@@ -1303,14 +1152,27 @@ static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
   const long long work = adj ? a.n_elts : a.n_units;
   const long long grid = work < P->num_sms ? work : P->num_sms;
   const size_t smem = contract_smem_bytes(a.frow, a.fcol, adj, a.a_slots, a.nst);
-  if (adj)
-    k_contract<true><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
-  else
-    k_contract<false><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
+  if (T.tf32) {
+    if (adj)
+      k_contract<true, true><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
+    else
+      k_contract<false, true><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
+  } else {
+    if (adj)
+      k_contract<true, false><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
+    else
+      k_contract<false, false><<<(unsigned)grid, kThreads, smem, P->stream>>>(a);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t tc_forward(qem_plan_t P, int l) { return launch_contract(P, l, false); }
+// The element-resident schedule when the plan's launch shapes select it (bit
+// 0 of tc_sched) and the level's operands fit it, otherwise the streaming one.
+cudaError_t tc_forward(qem_plan_t P, int l) {
+  const Layout& L = P->tc->lay[l];
+  if ((P->tune.tc_sched & 1) && tc_res_fits(L.fka, L.fkb, P->K)) return tc_forward_res(P, l, P->tc->tf32);
+  return launch_contract(P, l, false);
+}
 
 cudaError_t tc_adjoint_prep(qem_plan_t P, int l) {
   TcBuffers& T = *P->tc;
@@ -1322,7 +1184,11 @@ cudaError_t tc_adjoint_prep(qem_plan_t P, int l) {
   return cudaGetLastError();
 }
 
-cudaError_t tc_adjoint(qem_plan_t P, int l) { return launch_contract(P, l, true); }
+cudaError_t tc_adjoint(qem_plan_t P, int l) {
+  const Layout& L = P->tc->lay[l];
+  if ((P->tune.tc_sched & 2) && tc_adj_res_fits(L.fkb, L.fka, P->K)) return tc_adjoint_res(P, l, P->tc->tf32);
+  return launch_contract(P, l, true);
+}
 
 }  // namespace qem
 

@@ -1,0 +1,858 @@
+// Element-resident schedules of the tensor-core contractions (sm_103a): the
+// forward (k_fwd_res) and the adjoint (k_adj_res).
+//
+// Forward tile of plate element e (Eq. Prmp, organised per Sec. 6):
+//   S_e[kp][k] = rowc[kp] + sum_f A_p[kp][f] B_e[k][f] + h_e[k]   (log2 units),
+//   lt[e][kp]  = rowc[kp] + ln 2 * log2 sum_k 2^(S_e - rowc)[kp][k] - ln K,
+// with A_p the parent's operand rows (shared by every child of the parent)
+// and B_e the element's own rows.  Adjoint tile (Eq. mmp with the indicator
+// moment; Sec. 3.2's source-term weights in closed form) over the parent
+// samples the parent keeps (its compacted list of n_eff samples):
+//   w[e][k] = sum_j 2^(B_e[k] . A_p[j] + h_e[k] + d_e[j]),
+//   d_e[j]  = log2 e (rowc[kp_j] + ln w_p[kp_j] - ln K - lt_e[kp_j]).
+//
+// The streaming schedule in qem_tc.cu gives each CTA one 128-row block of one
+// element and streams the other operand through shared memory chunk by
+// chunk, 1.25 B of L2 traffic per pair for the forward's 80-column
+// split-BF16 rows.  Here one CTA takes whole elements and keeps one operand
+// of the element in shared memory:
+//  * forward: B_e (all K rows, 160 KB at K = 1024) stays while the parent's
+//    K / 128 row blocks stream through a two-slot ring (0.37 B per pair);
+//  * adjoint: the element's rows are taken in passes of four row blocks
+//    while the parent's kept rows stream once per pass in chunks of 256
+//    (0.55 B per pair at K = 1024).
+// Tiles are 128 x 256 (the MMA's full rate; a narrower N is bound by the MMA
+// issue rate) in two TMEM slots of 256 columns.  Roles (640 threads, one CTA
+// per SM): warp 0 loads the row side, warp 1 the column side (and the
+// adjoint's column shifts), warp 2 issues the MMAs (one thread) and owns
+// TMEM, warp 3 is idle, warps 4..19 are the epilogue: warp w reads TMEM lanes
+// 32 (w % 4) .. +31 (the rule of tcgen05.ld) and a quarter of every tile's
+// columns, all 64 of its values into registers before it hands the slot
+// back, so the next tile's MMAs run while it exponentiates; four warps per
+// SM sub-partition cover one another's load and hand-off latencies.  The
+// four quarters of a row are merged through shared memory once per row
+// block (forward) or once per pass (adjoint).
+//
+// Every wait is bounded; an expired wait sets the CTA's abort flag, every
+// role stops at its next wait, the producers wait (bounded, ignoring the
+// flag) for their own copies and the MMA issuer for its MMAs before TMEM is
+// freed, and the plan's control block gets ERR_TIMEOUT.
+#include "qem_tc.cuh"
+#include "qem_tc_ptx.cuh"
+
+namespace qem {
+namespace tc {
+
+constexpr int kResMaxChunks = kBStagesMax;  // forward: one producer warp per resident chunk, K <= 1024
+
+__host__ __device__ inline int imin(int x, int y) { return x < y ? x : y; }
+
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// ---------------------------------------------------------------------------- forward, columns resident
+struct ResArgs {
+  int K, R, C;                      // samples, row blocks (K / 128), column chunks (K / 256 rounded up)
+  int frow, fcol, ksteps;           // operand row widths (16-bit units) and MMA k-steps
+  int koff_row[16], koff_col[16];   // per k-step: 16-bit column offset in the row / column operand
+  long long n_elts;
+  const long long* parent;
+  const __nv_bfloat16* rows_feat;   // A: parent operand rows [n_parent][K][frow]
+  const __nv_bfloat16* cols_feat;   // B: element operand rows [n][K][fcol]
+  const float* rowc;                // [n_parent][K] row constants (nats)
+  float* lt;                        // [n][K] output
+  Ctl* ctl;
+  long long timeout_cycles;
+};
+
+struct ResSmem {
+  uint8_t* a0;       // two row blocks, a_stride apart
+  uint8_t* b0;       // C column chunks of 256 rows, b_stride apart
+  uint32_t a_stride, b_stride;
+  uint64_t* a_full;
+  uint64_t* a_empty;
+  uint64_t* b_full;
+  uint64_t* b_empty;
+  uint64_t* t_full;   // [2]
+  uint64_t* t_empty;  // [2]
+  uint64_t* done;
+  uint32_t* tmem_base;
+  volatile int* abort_flag;
+  volatile int* stop_flag;
+  float2* merge;     // [kRows][4] partial (max, sum) of every row
+};
+
+__host__ __device__ inline size_t res_smem_bytes(int frow, int fcol, int K) {
+  const size_t a = (size_t)kRows * frow * 2, b = (size_t)imin(K, kMaxN) * fcol * 2;
+  const int C = (K + kMaxN - 1) / kMaxN;
+  return 1024 + 2 * a + (size_t)C * b + 32 * 8 + 16 + kRows * 4 * sizeof(float2);
+}
+
+__device__ __forceinline__ ResSmem res_carve(uint8_t* raw, int frow, int fcol, int K) {
+  ResSmem s;
+  uint8_t* p = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+  const int C = (K + kMaxN - 1) / kMaxN;
+  s.a_stride = (uint32_t)kRows * frow * 2;
+  s.b_stride = (uint32_t)imin(K, kMaxN) * fcol * 2;
+  s.a0 = p;
+  p += 2 * (size_t)s.a_stride;
+  s.b0 = p;
+  p += (size_t)C * s.b_stride;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(p);
+  s.a_full = bars + 0;
+  s.a_empty = bars + 2;
+  s.b_full = bars + 4;
+  s.b_empty = bars + 4 + kResMaxChunks;
+  s.t_full = bars + 4 + 2 * kResMaxChunks;
+  s.t_empty = s.t_full + 2;
+  s.done = s.t_empty + 2;
+  p += 32 * 8;
+  s.tmem_base = reinterpret_cast<uint32_t*>(p);
+  s.abort_flag = reinterpret_cast<volatile int*>(p + 4);
+  s.stop_flag = reinterpret_cast<volatile int*>(p + 8);
+  p += 16;
+  s.merge = reinterpret_cast<float2*>(p);
+  return s;
+}
+
+// Roles of the forward: warp 0 loads the parent's row blocks, warp 1 the
+// element's column chunks, warp 2 issues the MMAs and owns TMEM, warp 3 is
+// idle, warps 4..19 are the epilogue (640 threads: up to 96 registers per
+// thread, room for a warp to hold its 64 values of a tile at once).
+constexpr int kFwdThreads = 640;
+constexpr int kFwdMmaWarp = 2, kFwdEpiWarp0 = 4;
+
+// The 64 values of one row in one warp's part of a tile, already in
+// registers, folded into the row's online log-sum-exp: shift by the running
+// maximum (set from the tile's first group when still -inf), 2^, summed as
+// they are produced; a partial sum above 2^32 (values far above the shift)
+// is redone from the registers at the exact maximum.
+__device__ __forceinline__ void lse_regs64(const uint32_t (&va)[32], const uint32_t (&vb)[32], float& m, float& sacc) {
+  if (m == -INFINITY) {
+    float mx = __uint_as_float(va[0]);
+#pragma unroll
+    for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(va[j]));
+    m = mx;
+  }
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    float x0 = __uint_as_float(va[j]), x1 = __uint_as_float(va[j + 1]);
+    float x2 = __uint_as_float(va[j + 2]), x3 = __uint_as_float(va[j + 3]);
+    sub2(x0, x1, m);
+    sub2(x2, x3, m);
+    const float e0 = ex2f(x0), e1 = ex2f(x1), e2 = ex2f(x2), e3 = ex2f(x3);
+    add2(p0, p1, e0, e1);
+    add2(p2, p3, e2, e3);
+  }
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    float x0 = __uint_as_float(vb[j]), x1 = __uint_as_float(vb[j + 1]);
+    float x2 = __uint_as_float(vb[j + 2]), x3 = __uint_as_float(vb[j + 3]);
+    sub2(x0, x1, m);
+    sub2(x2, x3, m);
+    const float e0 = ex2f(x0), e1 = ex2f(x1), e2 = ex2f(x2), e3 = ex2f(x3);
+    add2(p0, p1, e0, e1);
+    add2(p2, p3, e2, e3);
+  }
+  add2(p0, p1, p2, p3);
+  float pt = p0 + p1;
+  if (!(pt <= 4294967296.0f)) {  // per thread: the values are in its own registers
+    float mx = m;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fmaxf(__uint_as_float(va[j]), __uint_as_float(vb[j])));
+    sacc *= ex2f(m - mx);
+    m = mx;
+    pt = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) pt += ex2f(__uint_as_float(va[j]) - m) + ex2f(__uint_as_float(vb[j]) - m);
+  }
+  sacc += pt;
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_res(ResArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  ResSmem s = res_carve(smem_raw, a.frow, a.fcol, a.K);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int K = a.K, R = a.R, C = a.C, frow = a.frow, fcol = a.fcol;
+  const uint32_t sbo_a = (uint32_t)(frow >> 3) * 128u, sbo_b = (uint32_t)(fcol >> 3) * 128u;
+  const uint32_t a_bytes = (uint32_t)kRows * frow * 2;
+  const long long lim = a.timeout_cycles;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&s.a_full[i], 1);
+      mbar_init(&s.a_empty[i], 1);
+      mbar_init(&s.t_full[i], 1);
+      mbar_init(&s.t_empty[i], kEpiWarps);
+    }
+    for (int c = 0; c < C; ++c) {
+      mbar_init(&s.b_full[c], 1);
+      mbar_init(&s.b_empty[c], 1);
+    }
+    mbar_init(s.done, 1);
+    *s.abort_flag = 0;
+    *s.stop_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == kFwdMmaWarp) {
+    tmem_alloc(s.tmem_base, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s.tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ row blocks of the parent
+    if (lane == 0) {
+      int as = 0;
+      uint32_t aph = 0, armed = 0, last = 0;
+      bool ok = true;
+      for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x) {
+        const long long p = a.parent[e];
+        for (int rb = 0; rb < R; ++rb) {
+          ok = mbar_wait(&s.a_empty[as], aph ^ 1, lim, s.abort_flag);
+          if (!ok) break;
+          mbar_expect_tx(&s.a_full[as], a_bytes);
+          bulk_g2s(s.a0 + as * s.a_stride, a.rows_feat + (p * K + (long long)rb * kRows) * frow, a_bytes,
+                   &s.a_full[as]);
+          armed |= 1u << as;
+          last = (last & ~(1u << as)) | (aph << as);
+          if (++as == 2) {
+            as = 0;
+            aph ^= 1;
+          }
+        }
+      }
+      // no copy of this CTA may still be landing when it exits (bounded, ignores abort)
+      volatile int never = 0;
+      for (int i = 0; i < 2; ++i)
+        if (armed & (1u << i)) mbar_wait(&s.a_full[i], (last >> i) & 1u, lim, &never);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ the element's column chunks
+    // Chunk c of the next element is loaded once the last MMAs on chunk c of
+    // this one have completed; the releases come in chunk order.
+    if (lane == 0) {
+      uint32_t armed = 0, last = 0;
+      bool ok = true;
+      int i = 0;
+      for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x, ++i) {
+        const uint32_t ph = (uint32_t)i & 1u;
+        for (int c = 0; c < C; ++c) {
+          const int c0 = c * kMaxN;
+          const uint32_t bytes = (uint32_t)imin(kMaxN, K - c0) * fcol * 2;
+          ok = mbar_wait(&s.b_empty[c], ph ^ 1u, lim, s.abort_flag);
+          if (!ok) break;
+          mbar_expect_tx(&s.b_full[c], bytes);
+          bulk_g2s(s.b0 + c * s.b_stride, a.cols_feat + (e * K + c0) * fcol, bytes, &s.b_full[c]);
+          armed |= 1u << c;
+          last = (last & ~(1u << c)) | (ph << c);
+        }
+        const long long en = e + gridDim.x;  // the CTA's next element: warm L2 while this one is contracted
+        if (ok && en < a.n_elts)
+          for (int c = 0; c < C; ++c)
+            bulk_prefetch_l2(a.cols_feat + (en * K + (long long)c * kMaxN) * fcol,
+                             (uint32_t)imin(kMaxN, K - c * kMaxN) * fcol * 2);
+      }
+      volatile int never = 0;
+      for (int c = 0; c < C; ++c)
+        if (armed & (1u << c)) mbar_wait(&s.b_full[c], (last >> c) & 1u, lim, &never);
+    }
+  } else if (warp == kFwdMmaWarp) {
+    // ------------------------------------------------------------ MMA issuer (one thread)
+    if (lane == 0) {
+      const int nks = a.ksteps;
+      const uint64_t adesc0 = smem_desc(s.a0, 128, sbo_a), bdesc0 = smem_desc(s.b0, 128, sbo_b);
+      const uint32_t a_step = s.a_stride >> 4, b_step = s.b_stride >> 4;
+      const uint32_t fmt = TF32 ? 2u : 1u;
+      int as = 0, ts = 0, i = 0;
+      uint32_t aph = 0, tph = 0;
+      bool ok = true;
+      for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x, ++i) {
+        const uint32_t bph = (uint32_t)i & 1u;
+        for (int rb = 0; rb < R && ok; ++rb) {
+          ok = mbar_spin(&s.a_full[as], aph, lim, s.abort_flag);
+          if (!ok) break;
+          for (int c = 0; c < C; ++c) {
+            const int nc = imin(kMaxN, K - c * kMaxN);
+            if (rb == 0) ok = mbar_spin(&s.b_full[c], bph, lim, s.abort_flag);
+            if (ok) ok = mbar_spin(&s.t_empty[ts], tph ^ 1u, lim, s.abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t idesc = idesc_fmt(nc, fmt);
+            const uint32_t d_tmem = tmem + (uint32_t)(ts * kMaxN);
+            const uint64_t ad = adesc0 + (uint64_t)(as * a_step), bd = bdesc0 + (uint64_t)(c * b_step);
+#pragma unroll
+            for (int ks = 0; ks < 16; ++ks)
+              if (ks < nks)  // k-step offsets read from the kernel parameters (constant bank)
+                mma_kind<TF32>(d_tmem, ad + (uint32_t)a.koff_row[ks], bd + (uint32_t)a.koff_col[ks], idesc,
+                               ks > 0 ? 1u : 0u);
+            mma_commit(&s.t_full[ts]);
+            if (rb == R - 1) mma_commit(&s.b_empty[c]);  // the element's last use of chunk c
+            ts ^= 1;
+            if (ts == 0) tph ^= 1u;
+          }
+          if (!ok) break;
+          mma_commit(&s.a_empty[as]);
+          if (++as == 2) {
+            as = 0;
+            aph ^= 1u;
+          }
+        }
+      }
+      // every issued MMA has completed before the teardown (bounded, ignores abort)
+      mma_commit(s.done);
+      volatile int never = 0;
+      mbar_wait(s.done, 0, lim, &never);
+    }
+    __syncwarp();
+  } else if (warp >= kFwdEpiWarp0) {
+    // ------------------------------------------------------------ epilogue (16 warps)
+    // Warp w reads TMEM lanes 32 (w % 4) .. +31 (tcgen05.ld's lane-quarter
+    // rule) and a quarter of each tile's columns, all of them into registers
+    // before it hands the slot back, so the next tile's MMAs start while it
+    // exponentiates.  The four quarters of a row are merged through shared
+    // memory between two named barriers that every epilogue warp executes
+    // for every row block it enters, and the decision to stop is read from a
+    // flag written between them.
+    const int quarter = warp & 3;
+    const int part = (warp - kFwdEpiWarp0) >> 2;
+    const int row = quarter * 32 + lane;
+    const float lnK = logf((float)K);
+    int ts = 0;
+    uint32_t tph = 0;
+    bool stop = false;
+    for (long long e = blockIdx.x; e < a.n_elts && !stop; e += gridDim.x) {
+      const long long p = a.parent[e];
+      for (int rb = 0; rb < R; ++rb) {
+        float m = -INFINITY, sacc = 0.f;
+        bool ok = true;
+        const long long k = (long long)rb * kRows + row;
+        // the row constant, read now so that its latency is spent under this row block's tiles
+        const float rc = part == 0 ? a.rowc[p * K + k] : 0.f;
+        for (int c = 0; c < C && ok; ++c) {
+          const int nc = imin(kMaxN, K - c * kMaxN);
+          ok = mbar_wait(&s.t_full[ts], tph, lim, s.abort_flag);
+          ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ts * kMaxN + part * (nc >> 2));
+          if (nc == kMaxN) {
+            uint32_t va[32], vb[32];
+            tmem_ld32_issue(tbase, va);
+            tmem_ld32_issue(tbase + 32u, vb);
+            tmem_wait32(va);
+            tmem_wait32(vb);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s.t_empty[ts]);
+            lse_regs64(va, vb, m, sacc);
+          } else {  // a 128-column last chunk: 32 columns per warp
+            lse_group32(tbase, m, sacc);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s.t_empty[ts]);
+          }
+          ts ^= 1;
+          if (ts == 0) tph ^= 1u;
+        }
+        s.merge[row * 4 + part] = make_float2(m, sacc);
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        if (threadIdx.x == 32 * kFwdEpiWarp0) *s.stop_flag = *s.abort_flag;
+        if (part == 0 && ok) {
+          float M = -INFINITY;
+          for (int j = 0; j < 4; ++j) M = fmaxf(M, s.merge[row * 4 + j].x);
+          float S = 0.f;
+          for (int j = 0; j < 4; ++j) {
+            const float2 o = s.merge[row * 4 + j];
+            if (o.x != -INFINITY) S += o.y * ex2f(o.x - M);
+          }
+          a.lt[e * K + k] = rc + (M + log2f(S)) * kLn2 - lnK;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        if (*s.stop_flag) {
+          stop = true;
+          break;
+        }
+      }
+    }
+  }
+
+  if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kFwdMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------------------- adjoint, rows resident
+// The element's K operand rows are taken in passes of up to four 128-row
+// blocks (80 KB of split-BF16 rows in shared memory); in each pass the
+// parent's kept rows stream once, in chunks of 256 (the MMA's full rate),
+// through a two-deep ring with their column shifts, and every chunk meets
+// the pass's row blocks in turn (tile = row block x chunk, 128 x 256, two
+// TMEM slots).  Each epilogue thread keeps one partial sum per row block of
+// the pass; at the pass's end the four column quarters of every row are
+// added through shared memory.  Operand traffic: the element's rows once and
+// the parent's kept rows once per pass, (2 * 224 + 160) B per kept parent
+// sample and child sample pair / K at K = 1024 (0.55 B per pair).
+constexpr int kAdjPassRows = 4;   // row blocks per pass
+
+struct AdjResArgs {
+  int K, R, frow, fcol, ksteps, nst;  // nst: depth of the chunk ring
+  int koff_row[16], koff_col[16];
+  long long n_elts;
+  const long long* parent;
+  const int* ccnt;                    // kept samples per parent
+  int small;                          // parents keeping <= small are skipped (CUDA-core adjoint)
+  const __nv_bfloat16* rows_feat;     // element operand rows [n][K][frow]
+  const __nv_bfloat16* cols_feat;     // compacted parent rows [n_parent][K][fcol]
+  const float* dcol;                  // [n][K] column shifts (log2 units)
+  float* w_out;                       // [n][K]
+  Ctl* ctl;
+  long long timeout_cycles;
+};
+
+struct AdjSmem {
+  uint8_t* a0;       // kAdjPassRows row blocks, a_stride apart
+  uint8_t* b0;       // nst column chunks of 256 rows, b_stride apart
+  float* d0;         // nst column-shift rows of 256 floats
+  float* merge;      // [kAdjPassRows][kRows][4] partial row sums of a pass
+  uint32_t a_stride, b_stride;
+  uint64_t* a_full;   // [kAdjPassRows]
+  uint64_t* a_empty;  // [kAdjPassRows]
+  uint64_t* b_full;   // [nst]
+  uint64_t* b_empty;  // [nst]
+  uint64_t* d_full;   // [nst]
+  uint64_t* d_empty;  // [nst]
+  uint64_t* t_full;   // [2]
+  uint64_t* t_empty;  // [2]
+  uint64_t* done;
+  uint32_t* tmem_base;
+  volatile int* abort_flag;
+  volatile int* stop_flag;
+};
+
+__host__ __device__ inline size_t adj_res_smem_bytes(int frow, int fcol, int nst) {
+  return 1024 + (size_t)kAdjPassRows * kRows * frow * 2 + (size_t)nst * kMaxN * fcol * 2 + (size_t)nst * kMaxN * 4 +
+         (size_t)kAdjPassRows * kRows * 4 * 4 + 32 * 8 + 16;
+}
+
+__device__ __forceinline__ AdjSmem adj_carve(uint8_t* raw, int frow, int fcol, int nst) {
+  AdjSmem s;
+  uint8_t* p = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+  s.a_stride = (uint32_t)kRows * frow * 2;
+  s.b_stride = (uint32_t)kMaxN * fcol * 2;
+  s.a0 = p;
+  p += (size_t)kAdjPassRows * s.a_stride;
+  s.b0 = p;
+  p += (size_t)nst * s.b_stride;
+  s.d0 = reinterpret_cast<float*>(p);
+  p += (size_t)nst * kMaxN * 4;
+  s.merge = reinterpret_cast<float*>(p);
+  p += (size_t)kAdjPassRows * kRows * 4 * 4;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(p);
+  s.a_full = bars;
+  s.a_empty = bars + kAdjPassRows;
+  s.b_full = bars + 2 * kAdjPassRows;
+  s.b_empty = s.b_full + 4;
+  s.d_full = s.b_empty + 4;
+  s.d_empty = s.d_full + 4;
+  s.t_full = s.d_empty + 4;
+  s.t_empty = s.t_full + 2;
+  s.done = s.t_empty + 2;
+  p += 32 * 8;
+  s.tmem_base = reinterpret_cast<uint32_t*>(p);
+  s.abort_flag = reinterpret_cast<volatile int*>(p + 4);
+  s.stop_flag = reinterpret_cast<volatile int*>(p + 8);
+  return s;
+}
+
+// Sum of 2^(v + d) over 32 values already in registers, shifts d from
+// shared memory (the same addresses across the warp).
+__device__ __forceinline__ float adj_sum_f32(const float (&v)[32], const float* d) {
+  const float4* d4 = reinterpret_cast<const float4*>(d);
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    const float4 dv = d4[j >> 2];
+    float x0 = v[j], x1 = v[j + 1], x2 = v[j + 2], x3 = v[j + 3];
+    add2(x0, x1, dv.x, dv.y);
+    add2(x2, x3, dv.z, dv.w);
+    const float e0 = ex2f(x0), e1 = ex2f(x1), e2 = ex2f(x2), e3 = ex2f(x3);
+    add2(p0, p1, e0, e1);
+    add2(p2, p3, e2, e3);
+  }
+  add2(p0, p1, p2, p3);
+  return p0 + p1;
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(kFwdThreads, 1) k_adj_res(AdjResArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  const int NS = a.nst;
+  AdjSmem s = adj_carve(smem_raw, a.frow, a.fcol, NS);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int K = a.K, R = a.R, frow = a.frow, fcol = a.fcol;
+  const int passes = (R + kAdjPassRows - 1) / kAdjPassRows;
+  const uint32_t sbo_a = (uint32_t)(frow >> 3) * 128u, sbo_b = (uint32_t)(fcol >> 3) * 128u;
+  const uint32_t a_bytes = (uint32_t)kRows * frow * 2;
+  const long long lim = a.timeout_cycles;
+
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < kAdjPassRows; ++j) {
+      mbar_init(&s.a_full[j], 1);
+      mbar_init(&s.a_empty[j], 1);
+    }
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&s.b_full[i], 1);
+      mbar_init(&s.b_empty[i], 1);
+      mbar_init(&s.d_full[i], 1);
+      mbar_init(&s.d_empty[i], kEpiWarps);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&s.t_full[i], 1);
+      mbar_init(&s.t_empty[i], kEpiWarps);
+    }
+    mbar_init(s.done, 1);
+    *s.abort_flag = 0;
+    *s.stop_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == kFwdMmaWarp) {
+    tmem_alloc(s.tmem_base, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s.tmem_base;
+
+  // the elements of this CTA whose parent keeps more than `small` samples,
+  // the same sequence in every role
+  auto kept_of = [&](long long e) { return a.ccnt[a.parent[e]]; };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ row blocks of the element, pass by pass
+    if (lane == 0) {
+      uint32_t uses = 0, armed = 0, last = 0;  // uses: 4 bits per slot (use count parity in bit 0 of each nibble)
+      bool ok = true;
+      for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x) {
+        if (kept_of(e) <= a.small) continue;
+        for (int h = 0; h < passes && ok; ++h) {
+          const int nrb = imin(kAdjPassRows, R - h * kAdjPassRows);
+          for (int j = 0; j < nrb; ++j) {
+            const uint32_t ph = (uses >> j) & 1u;
+            ok = mbar_wait(&s.a_empty[j], ph ^ 1u, lim, s.abort_flag);
+            if (!ok) break;
+            mbar_expect_tx(&s.a_full[j], a_bytes);
+            bulk_g2s(s.a0 + j * s.a_stride, a.rows_feat + (e * K + (long long)(h * kAdjPassRows + j) * kRows) * frow,
+                     a_bytes, &s.a_full[j]);
+            armed |= 1u << j;
+            last = (last & ~(1u << j)) | (ph << j);
+            uses ^= 1u << j;
+          }
+        }
+      }
+      volatile int never = 0;
+      for (int j = 0; j < kAdjPassRows; ++j)
+        if (armed & (1u << j)) mbar_wait(&s.a_full[j], (last >> j) & 1u, lim, &never);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ parent chunks and column shifts, once per pass
+    if (lane == 0) {
+      uint32_t armed_b = 0, armed_d = 0, last_b = 0, last_d = 0;
+      bool ok = true;
+      long long g = 0;
+      for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x) {
+        const long long p = a.parent[e];
+        const int n_eff = a.ccnt[p];
+        if (n_eff <= a.small) continue;
+        const int npad = imin(K, (n_eff + 15) & ~15);
+        for (int h = 0; h < passes && ok; ++h)
+          for (int c0 = 0; c0 < npad; c0 += kMaxN, ++g) {
+            const int st = (int)(g % NS);
+            const uint32_t ph = (uint32_t)((g / NS) & 1);
+            const int nc = imin(kMaxN, npad - c0);
+            ok = mbar_wait(&s.b_empty[st], ph ^ 1u, lim, s.abort_flag);
+            if (!ok) break;
+            mbar_expect_tx(&s.b_full[st], (uint32_t)nc * fcol * 2);
+            bulk_g2s(s.b0 + st * s.b_stride, a.cols_feat + (p * K + c0) * fcol, (uint32_t)nc * fcol * 2,
+                     &s.b_full[st]);
+            armed_b |= 1u << st;
+            last_b = (last_b & ~(1u << st)) | (ph << st);
+            ok = mbar_wait(&s.d_empty[st], ph ^ 1u, lim, s.abort_flag);
+            if (!ok) break;
+            mbar_expect_tx(&s.d_full[st], (uint32_t)nc * 4u);
+            bulk_g2s(s.d0 + st * kMaxN, a.dcol + e * K + c0, (uint32_t)nc * 4u, &s.d_full[st]);
+            armed_d |= 1u << st;
+            last_d = (last_d & ~(1u << st)) | (ph << st);
+          }
+      }
+      volatile int never = 0;
+      for (int st = 0; st < NS; ++st) {
+        if (armed_b & (1u << st)) mbar_wait(&s.b_full[st], (last_b >> st) & 1u, lim, &never);
+        if (armed_d & (1u << st)) mbar_wait(&s.d_full[st], (last_d >> st) & 1u, lim, &never);
+      }
+    }
+  } else if (warp == kFwdMmaWarp) {
+    // ------------------------------------------------------------ MMA issuer (one thread)
+    if (lane == 0) {
+      const int nks = a.ksteps;
+      const uint64_t adesc0 = smem_desc(s.a0, 128, sbo_a), bdesc0 = smem_desc(s.b0, 128, sbo_b);
+      const uint32_t a_step = s.a_stride >> 4, b_step = s.b_stride >> 4;
+      const uint32_t fmt = TF32 ? 2u : 1u;
+      uint32_t uses = 0;  // bit j: use parity of row-block slot j
+      int ts = 0;
+      uint32_t tph = 0;
+      bool ok = true;
+      long long g = 0;
+      for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x) {
+        const int n_eff = kept_of(e);
+        if (n_eff <= a.small) continue;
+        const int npad = imin(K, (n_eff + 15) & ~15);
+        for (int h = 0; h < passes && ok; ++h) {
+          const int nrb = imin(kAdjPassRows, R - h * kAdjPassRows);
+          for (int c0 = 0; c0 < npad && ok; c0 += kMaxN, ++g) {
+            const int st = (int)(g % NS);
+            const uint32_t bph = (uint32_t)((g / NS) & 1);
+            const int nc = imin(kMaxN, npad - c0);
+            const bool last_chunk = c0 + kMaxN >= npad;
+            ok = mbar_spin(&s.b_full[st], bph, lim, s.abort_flag);
+            if (!ok) break;
+            const uint32_t idesc = idesc_fmt(nc, fmt);
+            const uint64_t bd = bdesc0 + (uint64_t)(st * b_step);
+            for (int j = 0; j < nrb; ++j) {
+              if (c0 == 0) ok = mbar_spin(&s.a_full[j], (uses >> j) & 1u, lim, s.abort_flag);
+              if (ok) ok = mbar_spin(&s.t_empty[ts], tph ^ 1u, lim, s.abort_flag);
+              if (!ok) break;
+              tc_fence_after();
+              const uint32_t d_tmem = tmem + (uint32_t)(ts * kMaxN);
+              const uint64_t ad = adesc0 + (uint64_t)(j * a_step);
+#pragma unroll
+              for (int ks = 0; ks < 16; ++ks)
+                if (ks < nks)
+                  mma_kind<TF32>(d_tmem, ad + (uint32_t)a.koff_row[ks], bd + (uint32_t)a.koff_col[ks], idesc,
+                                 ks > 0 ? 1u : 0u);
+              mma_commit(&s.t_full[ts]);
+              ts ^= 1;
+              if (ts == 0) tph ^= 1u;
+              if (last_chunk) {
+                mma_commit(&s.a_empty[j]);
+                uses ^= 1u << j;
+              }
+            }
+            if (ok) mma_commit(&s.b_empty[st]);
+          }
+        }
+      }
+      mma_commit(s.done);
+      volatile int never = 0;
+      mbar_wait(s.done, 0, lim, &never);
+    }
+    __syncwarp();
+  } else if (warp >= kFwdEpiWarp0) {
+    // ------------------------------------------------------------ epilogue (16 warps)
+    // Warp w takes TMEM lanes 32 (w % 4) .. +31 and column quarter `part` of
+    // every tile (loaded into registers before the slot is handed back) and
+    // keeps one partial sum per row block of the pass; at the pass's end the
+    // four quarters of every row are added through shared memory between two
+    // named barriers that every epilogue warp executes, and the decision to
+    // stop is read from a flag written between them.
+    const int quarter = warp & 3;
+    const int part = (warp - kFwdEpiWarp0) >> 2;
+    const int row = quarter * 32 + lane;
+    int ts = 0;
+    uint32_t tph = 0;
+    long long g = 0;
+    bool stop = false;
+    for (long long e = blockIdx.x; e < a.n_elts && !stop; e += gridDim.x) {
+      const int n_eff = kept_of(e);
+      if (n_eff <= a.small) continue;
+      const int npad = imin(K, (n_eff + 15) & ~15);
+      for (int h = 0; h < passes && !stop; ++h) {
+        const int nrb = imin(kAdjPassRows, R - h * kAdjPassRows);
+        float acc[kAdjPassRows] = {0.f, 0.f, 0.f, 0.f};
+        bool ok = true;
+        for (int c0 = 0; c0 < npad && ok; c0 += kMaxN, ++g) {
+          const int st = (int)(g % NS);
+          const uint32_t dph = (uint32_t)((g / NS) & 1);
+          const int nc = imin(kMaxN, npad - c0);
+          const int ncp = imin(64, nc - part * 64);  // this warp's columns of the chunk (a multiple of 16; <= 0: none)
+          ok = mbar_wait(&s.d_full[st], dph, lim, s.abort_flag);
+          const float* dsm = s.d0 + st * kMaxN + part * 64;
+#pragma unroll
+          for (int j = 0; j < kAdjPassRows; ++j) {
+            if (j >= nrb || !ok) break;
+            ok = mbar_wait(&s.t_full[ts], tph, lim, s.abort_flag);
+            ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ts * kMaxN + part * 64);
+            if (ncp == 64) {
+              // each load completes inside its own asm block (this kernel spills a
+              // few registers; no spill may fall between a load and its wait)
+              float va[32], vb[32];
+              tmem_ld32(tb, va);
+              tmem_ld32(tb + 32u, vb);
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&s.t_empty[ts]);
+              acc[j] += adj_sum_f32(va, dsm) + adj_sum_f32(vb, dsm + 32);
+            } else {
+              float sum = 0.f;
+              for (int c = 0; c < ncp; c += 16) {
+                float v[16];
+                tmem_ld16(tb + (uint32_t)c, v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) sum += ex2f(v[q] + dsm[c + q]);
+              }
+              acc[j] += sum;
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&s.t_empty[ts]);
+            }
+            ts ^= 1;
+            if (ts == 0) tph ^= 1u;
+          }
+          __syncwarp();
+          if (lane == 0 && ok) mbar_arrive(&s.d_empty[st]);
+        }
+        // add the four column quarters of every row of the pass's row blocks
+#pragma unroll
+        for (int j = 0; j < kAdjPassRows; ++j) s.merge[(j * kRows + row) * 4 + part] = acc[j];
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        if (threadIdx.x == 32 * kFwdEpiWarp0) *s.stop_flag = *s.abort_flag;
+        if (ok && part < nrb) {  // warp part p writes row block p of the pass
+          const float* mr = s.merge + (part * kRows + row) * 4;
+          a.w_out[e * K + (long long)(h * kAdjPassRows + part) * kRows + row] = (mr[0] + mr[1]) + (mr[2] + mr[3]);
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        if (*s.stop_flag) stop = true;
+      }
+    }
+  }
+
+  if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kFwdMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+bool tc_res_fits(int frow, int fcol, int K) {
+  return K % kRows == 0 && K <= kResMaxChunks * kMaxN && res_smem_bytes(frow, fcol, K) <= kSmemLimit;
+}
+
+// Deepest chunk ring of the resident adjoint that fits (0: it does not fit).
+static int tc_adj_res_stages(int frow, int fcol, int K) {
+  if (K % kRows != 0) return 0;
+  for (int nst = 4; nst >= 2; --nst)
+    if (adj_res_smem_bytes(frow, fcol, nst) <= kSmemLimit) return nst;
+  return 0;
+}
+
+bool tc_adj_res_fits(int frow, int fcol, int K) { return tc_adj_res_stages(frow, fcol, K) > 0; }
+
+qem_status tc_res_init(int frow, int fcol, int K, bool tf32) {
+  cudaError_t e = cudaSuccess;
+  if (tc_res_fits(frow, fcol, K)) {
+    const int bytes = (int)res_smem_bytes(frow, fcol, K);
+    e = tf32 ? cudaFuncSetAttribute(k_fwd_res<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+             : cudaFuncSetAttribute(k_fwd_res<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
+  // the adjoint's rows are the child operand (fcol wide), its columns the parent's (frow wide)
+  const int nst = tc_adj_res_stages(fcol, frow, K);
+  if (e == cudaSuccess && nst > 0) {
+    const int bytes = (int)adj_res_smem_bytes(fcol, frow, nst);
+    e = tf32 ? cudaFuncSetAttribute(k_adj_res<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+             : cudaFuncSetAttribute(k_adj_res<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
+  return e == cudaSuccess ? QEM_OK : QEM_ERR_CUDA;
+}
+
+static long long res_timeout_cycles(qem_plan_t P) { return (long long)(P->timeout_s * (double)P->clock_khz * 1e3); }
+
+cudaError_t tc_forward_res(qem_plan_t P, int l, bool tf32) {
+  TcBuffers& T = *P->tc;
+  const LevelView& ch = P->lv[l];
+  const Layout& L = T.lay[l];
+  if (ch.n == 0) return cudaSuccess;
+  ResArgs a{};
+  a.K = P->K;
+  a.R = P->K / kRows;
+  a.C = (P->K + kMaxN - 1) / kMaxN;
+  a.frow = L.fka;
+  a.fcol = L.fkb;
+  a.ksteps = L.nks;
+  for (int i = 0; i < L.nks; ++i) {
+    a.koff_row[i] = L.ka[i];
+    a.koff_col[i] = L.kb[i];
+  }
+  a.n_elts = ch.n;
+  a.parent = ch.parent;
+  a.rows_feat = T.afeat[l];
+  a.cols_feat = T.bfeat[l];
+  a.rowc = T.rowc[l];
+  a.lt = ch.lt;
+  a.ctl = P->ctl;
+  a.timeout_cycles = res_timeout_cycles(P);
+  const long long grid = ch.n < P->num_sms ? ch.n : P->num_sms;
+  const size_t smem = res_smem_bytes(a.frow, a.fcol, a.K);
+  if (tf32)
+    k_fwd_res<true><<<(unsigned)grid, kFwdThreads, smem, P->stream>>>(a);
+  else
+    k_fwd_res<false><<<(unsigned)grid, kFwdThreads, smem, P->stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_adjoint_res(qem_plan_t P, int l, bool tf32) {
+  TcBuffers& T = *P->tc;
+  const LevelView& ch = P->lv[l];
+  const Layout& L = T.lay[l];
+  if (ch.n == 0) return cudaSuccess;
+  AdjResArgs a{};
+  a.K = P->K;
+  a.R = P->K / kRows;
+  a.frow = L.fkb;
+  a.fcol = L.fka;
+  a.nst = tc_adj_res_stages(a.frow, a.fcol, a.K);
+  if (a.nst == 0) return cudaErrorInvalidValue;
+  a.ksteps = L.nks;
+  for (int i = 0; i < L.nks; ++i) {
+    a.koff_row[i] = L.kb[i];
+    a.koff_col[i] = L.ka[i];
+  }
+  a.n_elts = ch.n;
+  a.parent = ch.parent;
+  a.ccnt = P->lv[l - 1].ccnt;
+  a.small = kSmallKept;
+  a.rows_feat = T.bfeat[l];
+  a.cols_feat = T.cfeat[l];
+  a.dcol = T.dcol[l];
+  a.w_out = ch.w;
+  a.ctl = P->ctl;
+  a.timeout_cycles = res_timeout_cycles(P);
+  const long long grid = ch.n < P->num_sms ? ch.n : P->num_sms;
+  const size_t smem = adj_res_smem_bytes(a.frow, a.fcol, a.nst);
+  if (tf32)
+    k_adj_res<true><<<(unsigned)grid, kFwdThreads, smem, P->stream>>>(a);
+  else
+    k_adj_res<false><<<(unsigned)grid, kFwdThreads, smem, P->stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace qem

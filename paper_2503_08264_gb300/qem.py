@@ -15,7 +15,7 @@ import torch
 from . import _lib as L
 from . import synth as S
 
-PREC = {"fp32": L.QEM_PREC_FP32, "bf16": L.QEM_PREC_BF16, "bf16x3": L.QEM_PREC_BF16X3}
+PREC = {"fp32": L.QEM_PREC_FP32, "bf16": L.QEM_PREC_BF16, "bf16x3": L.QEM_PREC_BF16X3, "tf32": L.QEM_PREC_TF32}
 
 
 def _ptr(t):
@@ -80,9 +80,9 @@ def qem_tune(h, q_params, flags: int = 0) -> None:
 
 
 def qem_tune_get(h) -> dict:
-    a = (C.c_int * 4)()
+    a = (C.c_int * 5)()
     L.check(L.load().qem_tune_get(h, a), "qem_tune_get")
-    return {"sample_threads": a[0], "mom_threads": a[1], "fwd_rows": a[2], "fwd_chunk": a[3]}
+    return {"sample_threads": a[0], "mom_threads": a[1], "fwd_rows": a[2], "fwd_chunk": a[3], "tc_sched": a[4]}
 
 
 def qem_run(h, T: int, lam: float, sched_p: float, seed: int, mean_params, q_params, moments, trace=None) -> None:
@@ -263,6 +263,21 @@ class Plan:
 
     def tuning(self) -> dict:
         return qem_tune_get(self.h)
+
+    def set_tuning(self, **kw) -> dict:
+        """Apply launch shapes (keys of tuning()); unspecified ones keep their value."""
+        cur = qem_tune_get(self.h)
+        cur.update(kw)
+        keys = ["sample_threads", "mom_threads", "fwd_rows", "fwd_chunk", "tc_sched"]
+        a = (C.c_int * 5)(*[int(cur[k]) for k in keys])
+        L.check(L.load().qem_tune_set(self.h, a), "qem_tune_set")
+        return qem_tune_get(self.h)
+
+    def adjoint_pairs(self) -> tuple:
+        """(kept pairs on the tensor-core adjoint, all kept pairs) of the last E-step."""
+        a, b = C.c_double(), C.c_double()
+        L.check(L.load().qem_adjoint_pairs(self.h, C.byref(a), C.byref(b)), "qem_adjoint_pairs")
+        return a.value, b.value
 
     def profile(self, on: bool = True) -> None:
         qem_profile_enable(self.h, on)

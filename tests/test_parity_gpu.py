@@ -52,8 +52,10 @@ def moment_errors(model, q, got, ref):
     return out
 
 
-def run_pair(model, K, q, eps=None, seed=0, it=0, precision="fp32"):
+def run_pair(model, K, q, eps=None, seed=0, it=0, precision="fp32", tuning=None):
     plan = _plan(model, K, precision)
+    if tuning:
+        plan.set_tuning(**tuning)
     qd = plan.flat(q)
     ed = plan.flat(eps) if eps is not None else None
     mom, _ = plan.estep(qd, ed, seed=seed, it=it)

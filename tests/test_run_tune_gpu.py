@@ -68,14 +68,17 @@ def test_qem_run_single_launch_matches_host_loop():
     plan.close()
 
 
-def test_autotuned_plan_matches_oracle_and_caches():
+@pytest.mark.parametrize("precision,K,tol", [("fp32", 128, 1e-5), ("bf16x3", 256, 1e-3)])
+def test_autotuned_plan_matches_oracle_and_caches(precision, K, tol):
+    """The tuner's choice (FP32 tiles, or the tensor-core schedules of a
+    split-BF16 plan) gives results within the path's tolerance, and the
+    cached choice is reapplied without timing."""
     from paper_2503_08264_gb300 import _lib as L
     from paper_2503_08264_gb300 import qem
     model = S.hier_logistic(M=300, N=5, seed=71)
-    K = 128
     q = S.random_q(model, seed=72, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
     eps = S.noise(model, K, seed=73)
-    plan = qem.Plan(model, K, precision="fp32", tile=L.QEM_TILE_AUTO)
+    plan = qem.Plan(model, K, precision=precision, tile=L.QEM_TILE_AUTO)
     qd = plan.flat(q)
     mom, _ = plan.estep(qd, plan.flat(eps))   # tunes first (outside any capture)
     choice = plan.tuning()
@@ -83,14 +86,15 @@ def test_autotuned_plan_matches_oracle_and_caches():
     assert choice["sample_threads"] in (64, 128, 256)
     assert choice["mom_threads"] in (128, 256, 512)
     assert choice["fwd_rows"] in (64, 128, 256) and choice["fwd_chunk"] in (16, 32, 64)
+    assert choice["tc_sched"] in (0, 1, 2, 3)
     got = {"log_pmp": plan.log_pmp(), "mom": plan.split_q(mom), "w": plan.split_w(plan.weights())}
     ref = O.estep(model, q, K, eps=eps)
-    assert_parity(model, q, got, ref, 1e-5, 1e-5, 1e-5)
-    # every candidate of every knob is a valid launch: force each FP32 tile
+    assert_parity(model, q, got, ref, tol, tol, tol)
+    # every candidate of every knob is a valid launch: force each one
     forced = plan.tune(qd, force=True)
     assert forced == plan.tuning()
     plan.close()
     # same shapes: the cached choice is applied without timing
-    plan2 = qem.Plan(model, K, precision="fp32")
+    plan2 = qem.Plan(model, K, precision=precision)
     assert plan2.tune(plan2.flat(q)) == forced
     plan2.close()

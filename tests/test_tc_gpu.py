@@ -5,8 +5,11 @@
 * the E-step with split-BF16 operands (BF16X3) against the FP64 oracle at the
   mixed-precision tolerance (1e-3 relative: log P_MP, moments relative to
   max(|m|, sd_q) or sd_q^2, weights absolute);
-* plain BF16 reports its error (it is kept for the precision study, not held
-  to the tolerance).
+* plain BF16 and TF32 report their errors (kept for the precision study: the
+  parent's operand rows are shared by all of its children, so their rounding
+  adds up over the plate sum instead of averaging out);
+* the element-resident and streaming schedules agree to FP32 summation
+  order (the same MMAs; each row's exponentials are added in another order).
 """
 import ctypes as C
 
@@ -106,3 +109,101 @@ def test_dense_parent_weights(precision, tol):
     print("min kept parent samples per level", kept)
     assert min(kept) > 16
     assert_parity(model, q, got, ref, tol, tol, tol)
+
+
+def _estep_with(model, K, q, eps, precision, **tuning):
+    from paper_2503_08264_gb300 import qem
+    plan = qem.Plan(model, K, precision=precision)
+    if tuning:
+        plan.set_tuning(**tuning)
+    mom, _ = plan.estep(plan.flat(q), plan.flat(eps))
+    out = {"log_pmp": plan.log_pmp(), "mom": mom.cpu().numpy(), "w": plan.weights().cpu().numpy(),
+           "tuning": plan.tuning()}
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("M,K", [(300, 128), (200, 256), (40, 384), (3, 640), (13, 1024)])
+def test_schedules_agree(precision, M, K):
+    """Both element-resident kernels (tc_sched 3) against the streaming ones:
+    K = 128 (one 128-column chunk), 256, 384 and 640 (a ragged last chunk),
+    1024 (four resident chunks, two adjoint passes); M > 152 wraps elements
+    around the CTAs."""
+    model = S.hier_logistic(M=M, N=5, seed=61)
+    q = S.random_q(model, seed=62, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    eps = S.noise(model, K, seed=63)
+    res = _estep_with(model, K, q, eps, precision, tc_sched=3)
+    stream = _estep_with(model, K, q, eps, precision, tc_sched=0)
+    assert res["tuning"]["tc_sched"] == 3 and stream["tuning"]["tc_sched"] == 0
+    np.testing.assert_allclose(res["log_pmp"], stream["log_pmp"], rtol=1e-7)
+    np.testing.assert_allclose(res["w"], stream["w"], rtol=1e-5, atol=1e-9)
+    # moments relative to max(|m|, sd_q) (the parity tests' measure): near-zero
+    # means are sums of +-1e-3 terms whose FP32 summation order shows at 1e-7
+    plan_q = [np.asarray(x, np.float64) for x in q]
+    off, split_r, split_s = 0, [], []
+    for lv in model.levels:
+        n = lv.n * 2 * lv.dim
+        split_r.append(res["mom"][off:off + n].reshape(lv.n, 2, lv.dim))
+        split_s.append(stream["mom"][off:off + n].reshape(lv.n, 2, lv.dim))
+        off += n
+    assert max(moment_errors(model, plan_q, split_r, split_s)) < 1e-5
+
+
+@pytest.mark.parametrize("K", [512, 1024])
+def test_resident_adjoint_dense_root_weights(K):
+    """Flat root weights (the root's proposal equal to its prior, few users):
+    the root keeps most of its K samples, so every element's resident adjoint
+    (tc_sched 3) runs over full chunks of 256 and a ragged last one; against
+    the oracle at the mixed-precision tolerance."""
+    model = S.hier_logistic(M=3, N=2, seed=65)
+    q = S.random_q(model, seed=66, loc_scale=0.1, sd_lo=0.9, sd_hi=1.1)
+    q[0][:, 0, :] = 0.0
+    q[0][:, 1, :] = 1.0
+    eps = S.noise(model, K, seed=67)
+    got, ref = run_pair(model, K, q, eps, precision="bf16x3", tuning={"tc_sched": 3})
+    kept = (ref["w"][0] > 2.0 ** -24 * ref["w"][0].max(1, keepdims=True)).sum(1).min()
+    print("kept root samples", kept)
+    assert kept > K // 2
+    assert_parity(model, q, got, ref, 1e-3, 1e-3, 1e-3)
+
+
+def test_tune_set_rejects_values_outside_the_candidates():
+    from paper_2503_08264_gb300 import _lib as L
+    from paper_2503_08264_gb300 import qem
+    plan = qem.Plan(S.hier_logistic(M=4, N=2, seed=0), 128, precision="bf16x3")
+    with pytest.raises(L.QemError) as ei:
+        plan.set_tuning(tc_sched=4)
+    assert ei.value.code == L.QEM_ERR_INVALID_ARG
+    with pytest.raises(L.QemError):
+        plan.set_tuning(sample_threads=96)
+    plan.close()
+
+
+@pytest.mark.parametrize("M,K", [(300, 128), (40, 256), (13, 1024)])
+def test_tf32_reports_error(M, K):
+    """kind::tf32 with one product per k-step: errors reported (like plain
+    BF16, not held to the mixed-precision tolerance)."""
+    model = S.hier_logistic(M=M, N=5, seed=11)
+    q = S.random_q(model, seed=12, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    eps = S.noise(model, K, seed=13)
+    got, ref = run_pair(model, K, q, eps, precision="tf32")
+    lp = np.max(np.abs(got["log_pmp"] - ref["log_pmp"]) / np.abs(ref["log_pmp"]))
+    w = [np.max(np.abs(got["w"][l] - ref["w"][l])) for l in range(2)]
+    print(f"tf32 M={M} K={K}: log_pmp rel {lp:.2e}, moments",
+          ["%.2e" % e for e in moment_errors(model, q, got["mom"], ref["mom"])], "weights", ["%.2e" % e for e in w])
+    assert lp < 1e-2
+    for l in range(2):
+        np.testing.assert_allclose(got["w"][l].sum(1), 1.0, atol=1e-5)
+
+
+def test_tf32_three_level_reports_error():
+    model = S.batched_three_level(n_inst=6, D=8, seed=21, groups=(0, 5), units=(0, 12))
+    K = 256
+    q = S.random_q(model, seed=22, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    eps = S.noise(model, K, seed=23)
+    got, ref = run_pair(model, K, q, eps, precision="tf32")
+    lp = np.max(np.abs(got["log_pmp"] - ref["log_pmp"]) / np.abs(ref["log_pmp"]))
+    print(f"tf32 three-level: log_pmp rel {lp:.2e}, moments",
+          ["%.2e" % e for e in moment_errors(model, q, got["mom"], ref["mom"])])
+    assert lp < 1e-2
