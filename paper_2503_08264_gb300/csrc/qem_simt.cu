@@ -109,21 +109,51 @@ __device__ double gamma_variate(double a, const NoiseSrc& ns, int base) {
 // of FP32) dominated the kernel.
 constexpr int kSampleThreadsMax = 256;
 
-// Poisson-log reference point of a count: s0 = log max(y, 1) and e^s0, both
-// in FP32 and identical wherever they are evaluated (the sampler, the count
-// table and the per-element constants use this one function).
+// e^x - 1 - x without cancellation: for |x| < 1/2 the series
+// x^2 (1/2! + x/3! + ... + x^7/9!) (truncation below 3e-9 relative), beyond
+// it expm1(x) - x (no cancellation there: |expm1(x) - x| > 0.1 |x|).
+__device__ __forceinline__ float expm1mx(float x) {
+  if (fabsf(x) < 0.5f) {
+    float p = 1.f / 362880.f;
+    p = fmaf(p, x, 1.f / 40320.f);
+    p = fmaf(p, x, 1.f / 5040.f);
+    p = fmaf(p, x, 1.f / 720.f);
+    p = fmaf(p, x, 1.f / 120.f);
+    p = fmaf(p, x, 1.f / 24.f);
+    p = fmaf(p, x, 1.f / 6.f);
+    p = fmaf(p, x, 0.5f);
+    return x * x * p;
+  }
+  return expm1f(x) - x;
+}
+
+// Poisson-log reference point s0 of an observation: the per-sample part of
+// y s - e^s is then (y - e^s0)(s - s0) - e^s0 (e^(s-s0) - 1 - (s-s0)), and
+// y s0 - e^s0 - lgamma(y + 1) joins the element's FP64 constant.  Its
+// derivative y - e^s multiplies every rounding of s - s0, so s0 sits where
+// the samples are: for Gaussian proposals the centre loc . x of the
+// observation (FP64, capped so that e^s0 stays finite); otherwise (parent-
+// conditioned or Gamma/Beta proposals) log max(y, 1) in FP32.  e^s0 is
+// rounded to FP32 once and the same value enters both parts.  The sampler and
+// the per-element constants call these functions, so both sides agree bit
+// for bit.
+constexpr double kPoisRefMax = 80.0;
+__device__ __forceinline__ double loc_dot(const float* loc, const float* x, int D) {
+  double c = 0.0;
+  for (int d = 0; d < D; ++d) c = fma((double)loc[d], (double)x[d], c);
+  return c;
+}
 __device__ __forceinline__ void pois_ref(float y, float& s0, float& ey0) {
   s0 = logf(fmaxf(y, 1.f));
   ey0 = expf(s0);
 }
+__device__ __forceinline__ float pois_exp_ref(double s0) { return (float)exp(s0); }
 
-// y s0 - e^s0 - lgamma(y + 1) of every count y < kCountTable (FP64).
+// lgamma(y + 1) of every count y < kCountTable (FP64).
 __global__ void k_count_table(double* tab) {
   const int y = blockIdx.x * blockDim.x + threadIdx.x;
   if (y >= kCountTable) return;
-  float s0, ey0;
-  pois_ref((float)y, s0, ey0);
-  tab[y] = (double)y * s0 - (double)ey0 - lgamma((double)y + 1.0);
+  tab[y] = lgamma((double)y + 1.0);
 }
 
 cudaError_t launch_count_table(double* tab, cudaStream_t s) {
@@ -139,6 +169,7 @@ __global__ void k_elem_const(LevelView v, const float* __restrict__ q) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= v.n) return;
   const int D = v.D, nobs = v.n_obs;
+  const bool rel = v.qfam == QEM_Q_GAUSS && !v.qcond;  // the sampler's relative form
   double c = 0.0;
   for (int n = 0; n < nobs; ++n) {
     const float yv = v.y[e * nobs + n];
@@ -146,12 +177,15 @@ __global__ void k_elem_const(LevelView v, const float* __restrict__ q) {
       case QEM_LIK_GAUSS: c += -0.5 * log(2.0 * 3.141592653589793 * (double)v.lik_var); break;
       case QEM_LIK_POISSON_LOG: {
         const int yi = (int)yv;
-        if (yv >= 0.f && yv < (float)kCountTable && (float)yi == yv && v.ltab) {
-          c += v.ltab[yi];
+        const double lg = (yv >= 0.f && yv < (float)kCountTable && (float)yi == yv && v.ltab)
+                              ? v.ltab[yi] : lgamma((double)yv + 1.0);
+        if (rel) {
+          const double s0 = fmin(loc_dot(q + e * 2 * D, v.x + (e * nobs + n) * D, D), kPoisRefMax);
+          c += (double)yv * s0 - (double)pois_exp_ref(s0) - lg;
         } else {
           float s0, ey0;
           pois_ref(yv, s0, ey0);
-          c += (double)yv * s0 - (double)ey0 - lgamma((double)yv + 1.0);
+          c += (double)yv * s0 - (double)ey0 - lg;
         }
         break;
       }
@@ -202,14 +236,38 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
     xs[i] = d < D ? v.x[(e * nobs + n) * D + d] : 0.f;
   }
   for (int i = threadIdx.x; i < 2 * D; i += blockDim.x) qs[i] = q[e * 2 * D + i];
+  __syncthreads();
+  // Gaussian proposals (not parent-conditioned) form s_n = loc . x_n + (scale eps) . x_n
+  // with the first term per element in FP64, so the likelihood never sees the
+  // FP32 rounding of z = loc + scale eps (a count y multiplies that rounding,
+  // ~2^-24 |z|, by y).  s0s[n] holds the FP64 part the per-sample dot adds to:
+  // loc . x_n less the Poisson-log reference point, or loc . x_n itself.
+  const bool rel = v.qfam == QEM_Q_GAUSS && !v.qcond;
   for (int n = threadIdx.x; n < nobs; n += blockDim.x) {
     const float yv = v.y[e * nobs + n];
     ys[n] = yv;
-    // y s - e^s = [y s0 - e^s0] + y (s - s0) - e^s0 expm1(s - s0): the
-    // bracket is in the element constant, the rest is evaluated per sample
-    if (v.lik == QEM_LIK_POISSON_LOG) pois_ref(yv, s0s[n], ey0s[n]);
+    if (rel) {
+      const double c = loc_dot(qs, xs + n * Dp, D);
+      if (v.lik == QEM_LIK_POISSON_LOG) {
+        const double s0 = fmin(c, kPoisRefMax);
+        s0s[n] = (float)(c - s0);
+        ey0s[n] = pois_exp_ref(s0);
+      } else {
+        s0s[n] = (float)c;
+      }
+    } else if (v.lik == QEM_LIK_POISSON_LOG) {
+      pois_ref(yv, s0s[n], ey0s[n]);
+    }
   }
   __syncthreads();
+  if (rel) {
+    // the per-sample dot then takes eps itself: (scale eps) . x_n = eps . (scale x_n)
+    for (int i = threadIdx.x; i < nobs * Dp; i += blockDim.x) {
+      const int d = i % Dp;
+      if (d < D) xs[i] *= qs[D + d];
+    }
+    __syncthreads();
+  }
   const unsigned long long seed = ctl->seed, iter = ctl->iter;
   const float4* xs4 = reinterpret_cast<const float4*>(xs);
   float lmax = -INFINITY;
@@ -231,7 +289,7 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
           for (int d = 0; d < MAXD; ++d)
             if (d < D) z[d] = src[d];
         } else {
-          const unsigned long long sample = (unsigned long long)e * K + k;
+          const unsigned long long sample = (unsigned long long)(e + v.ebase) * K + k;
 #pragma unroll
           for (int d0 = 0; d0 < MAXD; d0 += 4) {
             if (d0 < D) {
@@ -249,7 +307,7 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
           if (d < D) {
             const float ep = z[d];
             ss = fmaf(ep, ep, ss);
-            z[d] = fmaf(qs[D + d], ep, qs[d]);
+            if (!rel) z[d] = fmaf(qs[D + d], ep, qs[d]);  // rel: z stays eps until after the likelihood
           }
         }
         if (v.qcond) {
@@ -263,7 +321,7 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
         }
         lq = -0.5f * ss;
       } else {
-        const unsigned long long sample = (unsigned long long)e * K + k;
+        const unsigned long long sample = (unsigned long long)(e + v.ebase) * K + k;
         NoiseSrc ns{eps ? eps + (e * K + k) * (long long)v.nps : nullptr, seed, iter, sample, v.level, v.qfam};
         const int blk = 2 * QEM_GAMMA_TRIES + 1;
         double lqd = 0.0;
@@ -287,7 +345,7 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
       }
       float ll = 0.f;
       for (int n = 0; n < nobs; ++n) {
-        float s = 0.f;
+        float s = rel ? s0s[n] : 0.f;
 #pragma unroll
         for (int d4 = 0; d4 < MAXD / 4; ++d4) {
           if (4 * d4 < Dp) {
@@ -307,14 +365,23 @@ __global__ void __launch_bounds__(kSampleThreadsMax) k_sample_local(LevelView v,
           }
           case QEM_LIK_BERNOULLI_LOGIT: ll += yv * s - softplusf(s); break;
           case QEM_LIK_POISSON_LOG: {
-            const float dl = s - s0s[n];
-            ll += yv * dl - ey0s[n] * expm1f(dl);
+            // y dl - e^s0 expm1(dl) = (y - e^s0) dl - e^s0 (e^dl - 1 - dl): the
+            // two large products of the first form (each ~ y |dl|) never appear;
+            // dl = s - s0 is the scaled noise's dot (plus a rarely nonzero FP64
+            // remainder) when s0 is the proposal centre
+            const float dl = rel ? s : s - s0s[n];
+            ll += fmaf(yv - ey0s[n], dl, -ey0s[n] * expm1mx(dl));
             break;
           }
           case QEM_LIK_POISSON_RATE: ll += yv * logf(z[0]) - z[0]; break;
           case QEM_LIK_BERNOULLI_PROB: ll += yv * logf(z[0]) + (1.f - yv) * log1pf(-z[0]); break;
           default: break;
         }
+      }
+      if (rel) {
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d)
+          if (d < D) z[d] = fmaf(qs[D + d], z[d], qs[d]);
       }
       float lp = 0.f;
       if (v.level == 0) {
@@ -941,10 +1008,10 @@ cudaError_t launch_moments_rescale(const LevelView* lvs, int l, const double* lp
 // block per element, keys in shared memory, ranks by counting (K^2 / block).
 __global__ void k_draw_perm(LevelView v, int K, int* perm, const Ctl* ctl) {
   extern __shared__ uint32_t keys[];
-  const long long e = blockIdx.x;
+  const long long e = blockIdx.x, ge = e + v.ebase;  // ge: the element's index in the noise streams
   const unsigned long long seed = ctl->seed, iter = ctl->iter;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)(k >> 2), (uint32_t)e, (uint32_t)(e >> 32) | 0x40000000u,
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)(k >> 2), (uint32_t)ge, (uint32_t)(ge >> 32) | 0x40000000u,
                                              (uint32_t)iter),
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
