@@ -72,6 +72,8 @@ def parse(argv=None):
                    help="split: the root's mean and log-variance as separate latents (K^2 parent pairs)")
     p.add_argument("--qcond", action="store_true",
                    help="leaf level with the parent-conditioned proposal (permutation copies; two-level, FP32)")
+    p.add_argument("--unit-peaks", action="store_true",
+                   help="measure the per-SM rates of the exponential unit, the FP32 pipe and tcgen05.mma")
     p.add_argument("--train-instances", type=int, default=2000)
     p.add_argument("--test-instances", type=int, default=16)
     return p.parse_args(argv)
@@ -855,8 +857,27 @@ def run_split_root(args):
     return 0
 
 
+def run_unit_peaks():
+    """The roofline denominators' per-SM unit rates, measured on this GPU
+    (probes/unit_peaks.cu), with the clocks seen while they ran."""
+    from paper_2503_08264_gb300 import build as B
+    exe = B.build_unit_peaks()
+    clocks = ClockSampler(0)
+    clocks.start()
+    r = subprocess.run([exe], capture_output=True, text=True)
+    clk = clocks.stop()
+    if r.returncode != 0:
+        raise SystemExit(f"unit_peaks failed ({r.returncode}): {r.stderr[-500:]}")
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    line["clocks"] = clk
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     args = parse(argv)
+    if args.unit_peaks:
+        return run_unit_peaks()
     if args.impl == "reference":
         return run_reference(args)
     if args.metric == "time_to_tol":

@@ -134,7 +134,10 @@ typedef struct {
   int tile;             /* 0: default launch shapes; QEM_TILE_AUTO: autotuned (see qem_tune)  */
   void* stream;         /* cudaStream_t the plan's work is enqueued on (NULL: default stream) */
   double var_floor;     /* Gaussian M-step variance floor factor (0: 1e-10)                   */
-  double timeout_s;     /* bound of every device-side wait (0: 2 s)                           */
+  double timeout_s;     /* bound of every device-side wait of the tensor-core contraction (0: 2 s):
+                         * an expired wait stops the launch and qem_log_pmp then reports
+                         * QEM_ERR_TIMEOUT; a CTA's waits for its own copies and MMAs before it
+                         * exits keep a bound of their own (at least ~2 s of SM cycles)      */
 } qem_plan_opts;
 
 typedef struct qem_plan_s* qem_plan_t;
@@ -158,6 +161,18 @@ const char* qem_status_string(qem_status s);
  * The model's x and y pointers are kept and read by every E-step.  *out is
  * set to NULL on failure.                                                   */
 qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_plan_t* out);
+
+/* Test hook of the bounded device waits (no counterpart in the paper): with
+ * on != 0, every tensor-core contraction launched afterwards first makes its
+ * MMA-issuing thread wait on a barrier that nothing completes before the
+ * kernel's teardown.  That wait runs out after the plan's timeout_s, the CTA
+ * aborts as after any expired wait (each role stops at its next wait, the
+ * CTA waits for its own copies and MMAs, frees TMEM and exits) and
+ * qem_log_pmp then returns QEM_ERR_TIMEOUT, which stays set for the plan's
+ * life.  Plans whose contraction runs on the CUDA cores (QEM_PREC_FP32, chain
+ * levels) have no such wait and are not affected.  Invalidates qem_run's
+ * cached graph.                                                             */
+qem_status qem_test_expire_wait(qem_plan_t plan, int on);
 
 /* Release the plan and its workspace (synchronises the plan's stream). NULL is a no-op. */
 qem_status qem_plan_destroy(qem_plan_t plan);
@@ -220,6 +235,48 @@ qem_status qem_estep_split_root(qem_plan_t plan, const float* q_params, const fl
  * ordered by (key, k) ascending.  Invalidates qem_run's cached graph.
  * QEM_ERR_INVALID_ARG when the plan has no qcond level.                     */
 qem_status qem_set_perm(qem_plan_t plan, const int32_t* perm);
+
+/* Sharding one instance's plate over several processes (one GPU each).
+ * Sec. 6 sums each plate out given the parent's samples: the elements of the
+ * root's child plate are independent given the root's K samples, and the
+ * root only sees their plate sum G[i][k_p] = sum_c log mean_k exp S_c[k_p][k]
+ * (Eq. Prmp).  A shard's plan holds every root of the model and a contiguous
+ * range of the root's children (with all their descendants); each process
+ *   1. qem_estep_shard_forward: samples and contracts its range into its own
+ *      G_r (no root step);
+ *   2. sums G over the processes (an all-reduce of n_inst x K doubles, by the
+ *      caller's collective library);
+ *   3. qem_estep_shard_finish: the root step on the summed G (identical on
+ *      every shard, since the roots' samples are), then the adjoint and the
+ *      moments of its own range (the adjoint needs no exchange: the root's
+ *      weights are replicated).
+ * Then log P_MP, the root's weights and moments equal those of one process
+ * holding the whole plate, and each shard holds its range's weights and
+ * moments; the M-step stays per shard (the root's on every shard alike).
+ * The paper has no multi-process form of the method; this is the
+ * distributive law of Sec. 6 cut at the root.                                 */
+
+/* Index in the counter-based noise streams (qem_estep's in-kernel draws and
+ * qem_set_perm's default permutations) of element 0 of each level:
+ * base HOST int64 [n_levels], each >= 0 (a shard passes the index, in the
+ * whole model, of the first element it holds at each level, so that a
+ * sharded run draws the whole model's noise).  Default 0.  Invalidates
+ * qem_run's cached graph.                                                    */
+qem_status qem_set_elem_base(qem_plan_t plan, const int64_t* base);
+
+/* Step 1 above: the E-step of qem_estep up to and including the plate sums
+ * into the root, without the root step.  Arguments as qem_estep; root_G:
+ * DEVICE double [n_inst][K] receives G_r (copied on the plan's stream).
+ * QEM_ERR_UNSUPPORTED for a one-level plan.                                  */
+qem_status qem_estep_shard_forward(qem_plan_t plan, const float* q_params, const float* eps, uint64_t seed,
+                                   uint64_t iter, double* root_G);
+
+/* Step 3 above: root_G DEVICE double [n_inst][K], the sum over all shards of
+ * their G_r (read on the plan's stream); then as qem_estep: moments DEVICE
+ * double [q_len] of this shard's elements, log_pmp DEVICE double [n_inst]
+ * (nullable).  Must follow qem_estep_shard_forward on the same plan with no
+ * other E-step in between (the samples and tables of step 1 are reused).    */
+qem_status qem_estep_shard_finish(qem_plan_t plan, const double* root_G, double* moments, double* log_pmp);
 
 /* log P_MP of q_params from a fresh draw of the samples (the noise stream
  * keyed by (seed, iter), which the caller chooses distinct from the E-step's):
@@ -294,19 +351,23 @@ qem_status qem_weights(qem_plan_t plan, float* weights);
  * (level-major, [n_l][K][D_l] per level), asynchronously.                   */
 qem_status qem_samples(qem_plan_t plan, float* z);
 
-/* Run T iterations of QEM (Alg. 1) on the device in ONE graph launch: a CUDA
- * graph whose conditional (while) node repeats one iteration (E-step, EMA +
- * M-step) until T are done or an error bit is set, with no host round trip
- * between iterations.  The graph is built on the first call and kept by the
- * plan while the buffers, lambda and sched_p stay the same (a call with
- * others rebuilds it).  Asynchronous on the plan's stream (on the legacy
- * stream: a private stream, synchronised before returning):
- *   mean_params   DEVICE double [q_len]  in: m_0; out: m_T
- *   q_params      DEVICE float  [q_len]  out: parameters matched to m_T
+/* Run iterations t0 .. t0 + T - 1 of QEM (Alg. 1) on the device in ONE graph
+ * launch: a CUDA graph whose conditional (while) node repeats one iteration
+ * (E-step, EMA + M-step) until T are done or an error bit is set, with no
+ * host round trip between iterations.  The graph is built on the first call
+ * and kept by the plan while the buffers, lambda and sched_p stay the same (a
+ * call with others rebuilds it).  Asynchronous on the plan's stream (on the
+ * legacy stream: a private stream, synchronised before returning):
+ *   mean_params   DEVICE double [q_len]  in: m_{t0-1}; out: m_{t0+T-1}
+ *   q_params      DEVICE float  [q_len]  out: parameters matched to the final m
  *   moments       DEVICE double [q_len]  scratch for each iteration's estimate
  *   log_pmp_trace DEVICE double [T][n_inst] log P_MP of every iteration (nullable)
- * Iteration t draws its noise from the stream keyed by (seed, t).           */
-qem_status qem_run(qem_plan_t plan, int64_t T, double lambda, double sched_p, uint64_t seed,
+ * Iteration t draws its noise from the stream keyed by (seed, t) and, with
+ * sched_p > 0, takes the EMA weight t^-sched_p (Thm. 1), so the state of a run
+ * is its mean parameters and its next t: a run of T1 iterations (t0 = 1)
+ * followed by a run of T2 from t0 = T1 + 1 on the saved mean parameters gives
+ * the same bits as one run of T1 + T2 (checkpoint and resume).  t0 >= 1.   */
+qem_status qem_run(qem_plan_t plan, int64_t T, int64_t t0, double lambda, double sched_p, uint64_t seed,
                    double* mean_params, float* q_params, double* moments, double* log_pmp_trace);
 
 /* Autotuning of the launch shapes (sampler and moments block sizes; FP32

@@ -77,8 +77,11 @@ def _first_prior(u, z, g):
     raise ValueError("first-day prior must be N(parent, a I) or N(mean, diag exp logvar)")
 
 
-def estep(model, q, K: int, eps) -> dict:
+def estep(model, q, K: int, eps, root_extra=None) -> dict:
     """One E-step in FP64 of a model [root level, chain level] (every instance).
+
+    root_extra: [n_inst, K] or None; added to each root's sum over its chains
+    (the sums of chains the model does not hold: a sharded plate).
 
     Returns log_pmp [n_inst], w per level ([n0, K], [n1, K]), mom per level
     ([n, 2, dim]), z per level, and the chain's tables: L [n_chains, K]
@@ -123,7 +126,7 @@ def estep(model, q, K: int, eps) -> dict:
     w1 = np.zeros((u.n, K))
     for i in range(r.n):
         f0 = (_lognorm(z0[i], 0.0, r.prior_a) - _lognorm(z0[i], q0[i, 0], q0[i, 1] ** 2)).sum(1)
-        A = f0 + L[chain_par == i].sum(0)
+        A = f0 + L[chain_par == i].sum(0) + (0.0 if root_extra is None else np.asarray(root_extra, np.float64)[i])
         lse = float(_lse(A, axis=0))
         log_pmp[i] = lse - lK
         w0[i] = np.exp(A - lse)

@@ -37,7 +37,7 @@ class _Level(C.Structure):
                 ("lik", C.c_int), ("lik_var", C.c_double), ("n_obs", C.c_int), ("qfam", C.c_int),
                 ("parent", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p), ("q", C.c_void_p),
                 ("eps", C.c_void_p), ("z", C.c_void_p), ("w", C.c_void_p), ("mom", C.c_void_p),
-                ("logL", C.c_void_p)]
+                ("logL", C.c_void_p), ("H_extra", C.c_void_p)]
 
 
 _lib = None
@@ -76,12 +76,14 @@ def noise_per_sample(lv) -> int:
     return lv.dim * (1 if lv.qfam == Q_GAMMA else 2) * (2 * GAMMA_TRIES + 1)
 
 
-def estep(model, q, K: int, eps=None, seed: int = 0, it: int = 0) -> dict:
+def estep(model, q, K: int, eps=None, seed: int = 0, it: int = 0, root_extra=None) -> dict:
     """One MPIW E-step in FP64.
 
     q:   per level, array [n, 2, dim] of proposal parameters
     eps: per level, array [n, K, noise_per_sample] of supplied noise, or None
          to draw it from the counter-based stream (seed, it)
+    root_extra: [n_inst, K] or None; added to the root's sum over its children
+         (the plate sums of children the model does not hold: a sharded plate)
     Returns log_pmp [n_inst] and per level z, w (marginal weights), mom
     (E_w[T(z)], [n, 2, dim]) and logL (levels > 0: [n, K_parent]).
     """
@@ -107,6 +109,10 @@ def estep(model, q, K: int, eps=None, seed: int = 0, it: int = 0) -> dict:
         c.parent, c.x, c.y, c.q, c.eps = _p(par), _p(x), _p(y), _p(qq), _p(ee)
         c.z, c.w, c.mom, c.logL = _p(z), _p(w), _p(mom), _p(logL)
         out["z"].append(z); out["w"].append(w); out["mom"].append(mom); out["logL"].append(logL)
+    if root_extra is not None:
+        hx = np.ascontiguousarray(root_extra, np.float64).reshape(model.levels[0].n, K)
+        keep.append(hx)
+        arr[0].H_extra = _p(hx)
     lp = np.zeros(model.levels[0].n)
     rc = lib().orc_estep(L, arr, K, seed, it, _p(lp))
     if rc != 0:

@@ -57,6 +57,8 @@ typedef struct {
   double* w;            /* out [n][K] marginal weights */
   double* mom;          /* out [n][2][dim] E_w[T(z)] */
   double* logL;         /* out [n][K] (levels>0): log mean_k exp S_e[kp][k] per parent sample kp */
+  const double* H_extra;/* [n][K] (level 0, or NULL): plate sums of root children that this call does
+                           not hold (another shard's), added to the root's children sum */
 } orc_level;
 
 int orc_max_threads(void) {
@@ -331,7 +333,8 @@ int orc_estep(int n_levels, orc_level* lv, int K, uint64_t seed, uint64_t iter, 
     double* a = malloc(sizeof(double) * (size_t)K);
     for (int64_t i = 0; i < R->n; ++i) {
       for (int k = 0; k < K; ++k)
-        a[k] = log_prior(R, R->z + (i * K + k) * R->dim, NULL) + local[0][i * K + k] + H[0][i * K + k];
+        a[k] = log_prior(R, R->z + (i * K + k) * R->dim, NULL) + local[0][i * K + k] + H[0][i * K + k] +
+               (R->H_extra ? R->H_extra[i * K + k] : 0.0);
       double lme = log_mean_exp(a, K);
       log_pmp[i] = lme;
       double lse = lme + log((double)K);

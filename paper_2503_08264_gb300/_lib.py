@@ -53,6 +53,10 @@ SIGNATURES = {
     "qem_estep_split_root": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p,
                                        C.c_void_p, C.c_void_p]),
     "qem_set_perm": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "qem_set_elem_base": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "qem_test_expire_wait": (C.c_int, [C.c_void_p, C.c_int]),
+    "qem_estep_shard_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p]),
+    "qem_estep_shard_finish": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "qem_log_pmp_fresh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p]),
     "qem_predictive": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "qem_moments_rescale": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -62,8 +66,8 @@ SIGNATURES = {
     "qem_log_pmp": (C.c_int, [C.c_void_p, C.c_void_p]),
     "qem_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "qem_samples": (C.c_int, [C.c_void_p, C.c_void_p]),
-    "qem_run": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_uint64, C.c_void_p, C.c_void_p,
-                          C.c_void_p, C.c_void_p]),
+    "qem_run": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_uint64, C.c_void_p,
+                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "qem_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "qem_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "qem_profile_name": (C.c_char_p, [C.c_int]),

@@ -59,6 +59,17 @@ def build(verbose: bool = False, extra: list | None = None) -> str:
     return OUT
 
 
+def build_unit_peaks() -> str:
+    """Compile the unit-rate probe (probes/unit_peaks.cu, a standalone program
+    that measures the per-SM rates behind the rooflines); returns its path."""
+    src = os.path.join(HERE, "probes", "unit_peaks.cu")
+    exe = os.path.join(BUILD, "unit_peaks")
+    os.makedirs(BUILD, exist_ok=True)
+    if _stale(exe, [src]):
+        subprocess.check_call([nvcc(), *ARCH, "-O3", "-o", exe, src])
+    return exe
+
+
 if __name__ == "__main__":
     import sys
     print(build(verbose="-v" in sys.argv, extra=["-Xptxas", "-v"] if "-v" in sys.argv else None))

@@ -168,9 +168,9 @@ inline RunGraph* run_of(qem_plan_t P) { return static_cast<RunGraph*>(P->run); }
     }                                                                      \
   } while (0)
 
-// Forward half of the E-step (sampling through log P_MP and the root
-// weights: Eq. Prmp over the plate tree), enqueued on the plan's stream.
-qem_status estep_forward(qem_plan_t P, const float* q, const float* eps, double* user_lp, double* trace) {
+// The E-step from sampling through the plate sums into the root (Eq. Prmp
+// over the plate tree, leaves first), enqueued on the plan's stream.
+qem_status estep_tree(qem_plan_t P, const float* q, const float* eps) {
   cudaStream_t s = P->stream;
   const int L = P->L, K = P->K;
   for (int l = 0; l < L; ++l) {
@@ -194,16 +194,21 @@ qem_status estep_forward(qem_plan_t P, const float* q, const float* eps, double*
     }
     QEM_LAUNCH(P, QEM_K_PLATE_SUM, launch_plate_sum(P->lv[l - 1], P->lv[l], K, s));
   }
-  QEM_LAUNCH(P, QEM_K_ROOT, launch_root(P->lv[0], K, L > 1, P->log_pmp, user_lp, trace, P->ctl, s));
   return QEM_OK;
 }
 
-// The E-step body (Eq. mp_iw over the plate tree): the forward half, then the
-// adjoint (marginal weights, Eq. mmp) and the moments.
-qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* moments, double* user_lp,
-                      double* trace) {
-  const qem_status st = estep_forward(P, q, eps, user_lp, trace);
+// Forward half of the E-step (sampling through log P_MP and the root
+// weights: Eq. Prmp over the plate tree), enqueued on the plan's stream.
+qem_status estep_forward(qem_plan_t P, const float* q, const float* eps, double* user_lp, double* trace) {
+  const qem_status st = estep_tree(P, q, eps);
   if (st != QEM_OK) return st;
+  QEM_LAUNCH(P, QEM_K_ROOT, launch_root(P->lv[0], P->K, P->L > 1, P->log_pmp, user_lp, trace, P->ctl, P->stream));
+  return QEM_OK;
+}
+
+// Second half of the E-step: the adjoint (marginal weights, Eq. mmp) root to
+// leaves and the moments, after the root step.
+qem_status estep_adjoint(qem_plan_t P, double* moments) {
   cudaStream_t s = P->stream;
   const int L = P->L, K = P->K;
   for (int l = 1; l < L; ++l) {
@@ -230,6 +235,15 @@ qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* mo
                  launch_residual_moments(P->lv[l], K, moments + P->q_off[l - 1], moments + P->q_off[l], s));
   }
   return QEM_OK;
+}
+
+// The E-step body (Eq. mp_iw over the plate tree): the forward half, then the
+// adjoint and the moments.
+qem_status estep_body(qem_plan_t P, const float* q, const float* eps, double* moments, double* user_lp,
+                      double* trace) {
+  const qem_status st = estep_forward(P, q, eps, user_lp, trace);
+  if (st != QEM_OK) return st;
+  return estep_adjoint(P, moments);
 }
 
 qem_status mstep_body(qem_plan_t P, const double* moments, double* m, float* q, double lambda, double sched_p,
@@ -607,6 +621,7 @@ qem_status qem_plan(const qem_model_desc* desc, const qem_plan_opts* opts, qem_p
       lv.nps = noise_per_sample(d);
       lv.level = l;
       lv.chain = d.chain > 1 ? d.chain : 1;
+      lv.ebase = 0;
       lv.qcond = d.qcond;
       lv.pD = l > 0 ? desc->levels[l - 1].dim : 0;
       lv.x = d.x;
@@ -767,6 +782,49 @@ qem_status qem_set_perm(qem_plan_t P, const int32_t* perm) {
   return QEM_OK;
 }
 
+qem_status qem_test_expire_wait(qem_plan_t P, int on) {
+  if (!P) return QEM_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEM_ERR_CUDA;
+  P->expire_test = on ? 1 : 0;
+  delete run_of(P);  // the loop graph holds the old kernel arguments
+  P->run = nullptr;
+  return QEM_OK;
+}
+
+qem_status qem_set_elem_base(qem_plan_t P, const int64_t* base) {
+  if (!P || !base) return QEM_ERR_INVALID_ARG;
+  for (int l = 0; l < P->L; ++l)
+    if (base[l] < 0) return QEM_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(P->stream) != cudaSuccess) return QEM_ERR_CUDA;
+  for (int l = 0; l < P->L; ++l) P->lv[l].ebase = (long long)base[l];
+  delete run_of(P);  // the loop graph holds the old level views
+  P->run = nullptr;
+  return QEM_OK;
+}
+
+qem_status qem_estep_shard_forward(qem_plan_t P, const float* q_params, const float* eps, uint64_t seed,
+                                   uint64_t iter, double* root_G) {
+  if (!P || !q_params || !root_G) return QEM_ERR_INVALID_ARG;
+  if (P->L < 2) return QEM_ERR_UNSUPPORTED;
+  const qem_status ts = maybe_autotune(P, q_params);
+  if (ts != QEM_OK) return ts;
+  QEM_TRY(launch_set_ctl(P->ctl, seed, iter, 1, -1, P->stream));
+  const qem_status st = estep_tree(P, q_params, eps);
+  if (st != QEM_OK) return st;
+  QEM_TRY(cudaMemcpyAsync(root_G, P->lv[0].hsum, sizeof(double) * (size_t)P->lv[0].n * P->K,
+                          cudaMemcpyDeviceToDevice, P->stream));
+  return QEM_OK;
+}
+
+qem_status qem_estep_shard_finish(qem_plan_t P, const double* root_G, double* moments, double* log_pmp) {
+  if (!P || !root_G || !moments) return QEM_ERR_INVALID_ARG;
+  if (P->L < 2) return QEM_ERR_UNSUPPORTED;
+  QEM_TRY(cudaMemcpyAsync(P->lv[0].hsum, root_G, sizeof(double) * (size_t)P->lv[0].n * P->K,
+                          cudaMemcpyDeviceToDevice, P->stream));
+  QEM_LAUNCH(P, QEM_K_ROOT, launch_root(P->lv[0], P->K, true, P->log_pmp, log_pmp, nullptr, P->ctl, P->stream));
+  return estep_adjoint(P, moments);
+}
+
 qem_status qem_estep_split_root(qem_plan_t P, const float* q_params, const float* eps, uint64_t seed, uint64_t iter,
                                 double* moments, double* log_pmp, float* root_weights) {
   if (!P || !q_params || !moments) return QEM_ERR_INVALID_ARG;
@@ -884,9 +942,9 @@ qem_status qem_samples(qem_plan_t P, float* z) {
   return QEM_OK;
 }
 
-qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint64_t seed, double* mean_params,
-                   float* q_params, double* moments, double* log_pmp_trace) {
-  if (!P || T < 0 || !mean_params || !q_params || !moments) return QEM_ERR_INVALID_ARG;
+qem_status qem_run(qem_plan_t P, int64_t T, int64_t t0, double lambda, double sched_p, uint64_t seed,
+                   double* mean_params, float* q_params, double* moments, double* log_pmp_trace) {
+  if (!P || T < 0 || t0 < 1 || !mean_params || !q_params || !moments) return QEM_ERR_INVALID_ARG;
   if (!(lambda >= 0.0 && lambda <= 1.0) || !(sched_p >= 0.0 && sched_p < 1.0)) return QEM_ERR_INVALID_ARG;
   cudaStream_t own = nullptr;
   Prof* pf = prof_of(P);
@@ -905,7 +963,11 @@ qem_status qem_run(qem_plan_t P, int64_t T, double lambda, double sched_p, uint6
     st = mstep_body(P, nullptr, mean_params, q_params, lambda, sched_p, 1);  // Q_1 = set(m_0)
     if (st == QEM_OK && T > 0) st = maybe_autotune(P, q_params);
     if (st != QEM_OK) break;
-    if (launch_set_ctl(P->ctl, seed, 1, 1, log_pmp_trace ? 0 : -1, P->stream) != cudaSuccess) { st = QEM_ERR_CUDA; break; }
+    // iteration t0 first: the noise stream (seed, t) and the schedule's t continue a saved run
+    if (launch_set_ctl(P->ctl, seed, (unsigned long long)t0, t0, log_pmp_trace ? 0 : -1, P->stream) != cudaSuccess) {
+      st = QEM_ERR_CUDA;
+      break;
+    }
     if (T == 0) break;
     RunGraph* R = run_of(P);
     const void* key[4] = {mean_params, q_params, moments, log_pmp_trace};

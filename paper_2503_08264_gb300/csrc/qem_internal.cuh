@@ -44,6 +44,7 @@ struct LevelView {
   int nps;            // noise numbers per sample
   int level;          // index of this level
   int chain;          // days per region of a chain plate (1: plain plate)
+  long long ebase;    // index of element 0 in the counter-based noise streams (a shard's offset)
   int qcond;          // parent-conditioned proposal (copies drawn from permuted parent copies)
   const int* perm;    // [n][K] qcond: parent copy of each sample
   const float* pz;    // qcond: the parent level's samples [n_parent][K][pD]
@@ -125,6 +126,7 @@ struct qem_plan_s {
   cudaStream_t stream = nullptr;
   double var_floor = 1e-10;
   double timeout_s = 2.0;
+  int expire_test = 0;         // qem_test_expire_wait
   int device = 0;
   int num_sms = 0;
   long long clock_khz = 0;

@@ -440,6 +440,7 @@ struct ContractArgs {
   float* w_out;                     //          output [n][K]
   Ctl* ctl;
   long long timeout_cycles;
+  int expire_test;                  // qem_test_expire_wait
 };
 
 struct Smem {
@@ -687,10 +688,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       volatile int never = 0;
       if (is_a) {
         for (int i = 0; i < NA; ++i)
-          if (armed & (1u << i)) mbar_wait(&s.a_full[i], (last >> i) & 1u, lim, &never);
+          if (armed & (1u << i)) mbar_wait(&s.a_full[i], (last >> i) & 1u, drain_bound(lim), &never);
       } else {
-        if (armed & 4u) mbar_wait(&s.b_full[my_stage], (last >> 2) & 1u, lim, &never);
-        if (armed & 8u) mbar_wait(&s.d_full[my_stage], (last >> 3) & 1u, lim, &never);
+        if (armed & 4u) mbar_wait(&s.b_full[my_stage], (last >> 2) & 1u, drain_bound(lim), &never);
+        if (armed & 8u) mbar_wait(&s.d_full[my_stage], (last >> 3) & 1u, drain_bound(lim), &never);
       }
     }
   } else if (warp == kMmaWarp) {
@@ -713,6 +714,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       const uint32_t a_step = s.a_stride >> 4, b_step = s.b_stride >> 4, t_step = tile_bytes >> 4;
       long long prev_row = -1;
       bool ok = true;
+      // test hook (qem_test_expire_wait): a wait on the teardown barrier, which
+      // nothing completes before the teardown, runs out and aborts the CTA
+      if (a.expire_test) ok = mbar_spin(s.done, 0, lim, s.abort_flag);
       Walker<ADJ> wk(a);
       Unit x;
       while (ok && wk.next(x)) {
@@ -755,7 +759,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       // abort (the wait ignores the abort flag; it is still bounded)
       mma_commit(s.done);
       volatile int never = 0;
-      mbar_wait(s.done, 0, lim, &never);
+      mbar_wait(s.done, 0, drain_bound(lim), &never);
     }
     __syncwarp();
   } else {
@@ -924,8 +928,8 @@ __global__ void __launch_bounds__(128, 1) k_diag_gemm(const __nv_bfloat16* A, co
     // neither the bulk copies nor the MMAs may still be in flight at the
     // teardown, also after an abort (bounded waits that ignore the flag)
     volatile int never = 0;
-    mbar_wait(&bars[0], 0, lim, &never);
-    mbar_wait(&bars[1], 0, lim, &never);
+    mbar_wait(&bars[0], 0, drain_bound(lim), &never);
+    mbar_wait(&bars[1], 0, drain_bound(lim), &never);
   }
   tc_fence_before();
   __syncthreads();
@@ -1136,6 +1140,7 @@ static cudaError_t launch_contract(qem_plan_t P, int l, bool adj) {
   a.parent = ch.parent;
   a.ctl = P->ctl;
   a.timeout_cycles = timeout_cycles(P);
+  a.expire_test = P->expire_test;
   if (!adj) {
     a.rows_feat = T.afeat[l];
     a.cols_feat = T.bfeat[l];

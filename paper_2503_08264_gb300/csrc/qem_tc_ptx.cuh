@@ -88,6 +88,14 @@ __device__ __forceinline__ bool mbar_spin(uint64_t* b, uint32_t parity, long lon
     }
   }
 }
+// Bound of the teardown waits (a CTA's own bulk copies and MMAs must land
+// before it frees TMEM or exits, also after an abort): the plan's wait bound,
+// but never below ~2 s of SM cycles, so that a tiny timeout_s aborts the
+// contraction without cutting these waits short.
+__device__ __forceinline__ long long drain_bound(long long lim) {
+  constexpr long long kDrainCycles = 4000000000LL;
+  return lim > kDrainCycles ? lim : kDrainCycles;
+}
 __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 

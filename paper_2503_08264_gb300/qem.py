@@ -85,8 +85,9 @@ def qem_tune_get(h) -> dict:
     return {"sample_threads": a[0], "mom_threads": a[1], "fwd_rows": a[2], "fwd_chunk": a[3], "tc_sched": a[4]}
 
 
-def qem_run(h, T: int, lam: float, sched_p: float, seed: int, mean_params, q_params, moments, trace=None) -> None:
-    L.check(L.load().qem_run(h, T, lam, sched_p, seed, _ptr(mean_params), _ptr(q_params), _ptr(moments),
+def qem_run(h, T: int, t0: int, lam: float, sched_p: float, seed: int, mean_params, q_params, moments,
+            trace=None) -> None:
+    L.check(L.load().qem_run(h, T, t0, lam, sched_p, seed, _ptr(mean_params), _ptr(q_params), _ptr(moments),
                              _ptr(trace)), "qem_run")
 
 
@@ -202,6 +203,36 @@ class Plan:
         self._perm = None if perm is None else torch.as_tensor(perm, dtype=torch.int32).to(self.device).contiguous()
         L.check(L.load().qem_set_perm(self.h, _ptr(self._perm)), "qem_set_perm")
 
+    def test_expire_wait(self, on: bool = True) -> None:
+        """Test hook: make the tensor-core contractions' first wait run out
+        (after timeout_s), so that the E-step reports QEM_ERR_TIMEOUT."""
+        L.check(L.load().qem_test_expire_wait(self.h, 1 if on else 0), "qem_test_expire_wait")
+
+    def set_elem_base(self, base) -> None:
+        """Index of element 0 of each level in the counter-based noise streams
+        (a shard passes its first element's index in the whole model)."""
+        a = (C.c_int64 * len(self.model.levels))(*[int(b) for b in base])
+        L.check(L.load().qem_set_elem_base(self.h, a), "qem_set_elem_base")
+
+    def shard_forward(self, q, eps=None, seed: int = 0, it: int = 0, root_G=None) -> torch.Tensor:
+        """Sampling and contraction up to the plate sums into the root; returns
+        this shard's G [n_inst, K] (device double) for the caller's sum over shards."""
+        if root_G is None:
+            root_G = torch.empty((self.n_inst, self.K), dtype=torch.float64, device=self.device)
+        L.check(L.load().qem_estep_shard_forward(self.h, _ptr(q), _ptr(eps), seed, it, _ptr(root_G)),
+                "qem_estep_shard_forward")
+        return root_G
+
+    def shard_finish(self, root_G, moments=None, log_pmp=None):
+        """Root step on the summed G, then this shard's adjoint and moments."""
+        if moments is None:
+            moments = torch.empty(self.q_len, dtype=torch.float64, device=self.device)
+        if log_pmp is None:
+            log_pmp = torch.empty(self.n_inst, dtype=torch.float64, device=self.device)
+        L.check(L.load().qem_estep_shard_finish(self.h, _ptr(root_G), _ptr(moments), _ptr(log_pmp)),
+                "qem_estep_shard_finish")
+        return moments, log_pmp
+
     def log_pmp_fresh(self, q, seed: int, it: int, log_pmp=None):
         """log P_MP of q from a fresh draw of the samples (device double [n_inst])."""
         if log_pmp is None:
@@ -245,10 +276,12 @@ class Plan:
         return z
 
     def run(self, T: int, lam: float, mean_params, q_params, moments=None, sched_p: float = 0.0, seed: int = 0,
-            trace=None):
+            trace=None, t0: int = 1):
+        """Iterations t0 .. t0 + T - 1 of Alg. 1 as one graph launch (t0 > 1
+        continues a run from its saved mean parameters)."""
         if moments is None:
             moments = torch.empty(self.q_len, dtype=torch.float64, device=self.device)
-        qem_run(self.h, T, lam, sched_p, seed, mean_params, q_params, moments, trace)
+        qem_run(self.h, T, t0, lam, sched_p, seed, mean_params, q_params, moments, trace)
         return moments
 
     def run_kernels(self) -> tuple:

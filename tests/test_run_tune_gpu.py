@@ -7,8 +7,12 @@ launch-shape autotuner (qem_tune).
   qem_estep / qem_mstep with the same noise stream, and a second call
   (the cached graph) does too.
 * qem_tune picks launch shapes from its candidate sets; an autotuned plan
-  still matches the FP64 oracle at the FP32 tolerance; a second plan of the
+  still matches the FP64 oracle at the path's tolerance; a second plan of the
   same shapes takes the cached choice.
+* Checkpoint and resume: a run of T1 iterations, then a run of T2 from
+  t0 = T1 + 1 on its saved mean parameters, equals one run of T1 + T2 bit
+  for bit (mean parameters, proposal and the log P_MP trace), with the noise
+  stream and Thm. 1's schedule both keyed by the iteration t.
 """
 import numpy as np
 import pytest
@@ -98,3 +102,39 @@ def test_autotuned_plan_matches_oracle_and_caches(precision, K, tol):
     plan2 = qem.Plan(model, K, precision=precision)
     assert plan2.tune(plan2.flat(q)) == forced
     plan2.close()
+
+
+@pytest.mark.parametrize("case", ["bf16x3_hier_logistic", "fp32_chain"])
+def test_run_resumes_bit_identically(case):
+    from paper_2503_08264_gb300 import qem
+    if case == "bf16x3_hier_logistic":
+        model, K, prec = S.hier_logistic(M=60, N=5, seed=81), 256, "bf16x3"
+    else:
+        model, K, prec = S.chain_poisson(n_inst=2, R=5, T=12, D=1, seed=82), 64, "fp32"
+    T1, T2, lam, sched_p, seed = 4, 5, 0.5, 0.6, 17
+    plan = qem.Plan(model, K, precision=prec)
+    q0 = plan.flat(S.initial_q(model))
+    m0 = plan.mean_params(q0)
+    n = plan.n_inst
+    # one run of T1 + T2
+    m_a, q_a = m0.clone(), torch.empty_like(q0)
+    tr_a = torch.empty((T1 + T2) * n, dtype=torch.float64, device="cuda")
+    plan.run(T1 + T2, lam, m_a, q_a, sched_p=sched_p, seed=seed, trace=tr_a)
+    # T1, a checkpoint of the mean parameters (host copy), then T2 from t0 = T1 + 1
+    m_b, q_b = m0.clone(), torch.empty_like(q0)
+    tr_b1 = torch.empty(T1 * n, dtype=torch.float64, device="cuda")
+    plan.run(T1, lam, m_b, q_b, sched_p=sched_p, seed=seed, trace=tr_b1)
+    saved = m_b.cpu()
+    m_c, q_c = saved.cuda(), torch.empty_like(q0)
+    tr_b2 = torch.empty(T2 * n, dtype=torch.float64, device="cuda")
+    plan.run(T2, lam, m_c, q_c, sched_p=sched_p, seed=seed, trace=tr_b2, t0=T1 + 1)
+    torch.cuda.synchronize()
+    assert torch.equal(m_c, m_a)
+    assert torch.equal(q_c, q_a)
+    assert torch.equal(torch.cat([tr_b1, tr_b2]), tr_a)
+    # a resume from another t gives another run (the schedule and the noise move with t)
+    m_d, q_d = saved.cuda(), torch.empty_like(q0)
+    plan.run(T2, lam, m_d, q_d, sched_p=sched_p, seed=seed, t0=T1 + 2)
+    torch.cuda.synchronize()
+    assert not torch.equal(m_d, m_a)
+    plan.close()

@@ -207,3 +207,33 @@ def test_tf32_three_level_reports_error():
     print(f"tf32 three-level: log_pmp rel {lp:.2e}, moments",
           ["%.2e" % e for e in moment_errors(model, q, got["mom"], ref["mom"])])
     assert lp < 1e-2
+
+
+def test_expired_wait_reports_timeout_and_the_next_plan_works():
+    """A device wait that runs out: with the test hook on, the contraction's
+    MMA-issuing thread first waits on a barrier that nothing completes before
+    the teardown (a flag nothing sets); the wait ends after timeout_s = 10 ms,
+    every role of the CTA stops at its next wait, the CTA waits for its own
+    copies and MMAs under a separate bound before it frees TMEM and exits, and
+    qem_log_pmp reports QEM_ERR_TIMEOUT; under each tensor-core schedule (the
+    forward's and the adjoint's resident and streaming kernels).  The context
+    stays usable: a fresh plan in the same process then matches the oracle.
+    (A short timeout_s alone makes no wait run out: mbarrier.try_wait
+    suspends until the phase completes, and the copies land within that.)"""
+    from paper_2503_08264_gb300 import _lib as L
+    from paper_2503_08264_gb300 import qem
+    model = S.hier_logistic(M=40, N=5, seed=91)
+    K = 256
+    q = S.random_q(model, seed=92, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    eps = S.noise(model, K, seed=93)
+    for sched in (1, 0, 3, 2):
+        plan = qem.Plan(model, K, precision="bf16x3", timeout_s=0.01)
+        plan.set_tuning(tc_sched=sched)
+        plan.test_expire_wait(True)
+        plan.estep(plan.flat(q), plan.flat(eps))
+        with pytest.raises(L.QemError) as ei:
+            plan.log_pmp()
+        assert ei.value.code == L.QEM_ERR_TIMEOUT, (sched, ei.value.code)
+        plan.close()
+    got, ref = run_pair(model, K, q, eps, precision="bf16x3")
+    assert_parity(model, q, got, ref, 1e-3, 1e-3, 1e-3)
