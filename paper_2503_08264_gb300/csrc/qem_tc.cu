@@ -863,9 +863,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
     }
   }
 
-  if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
   tc_fence_before();
   __syncthreads();
+  // after the barrier: every role has stopped, so an abort by any of them is seen
+  if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
   if (warp == kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);

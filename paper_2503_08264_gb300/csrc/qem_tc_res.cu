@@ -81,18 +81,13 @@ struct ResSmem {
   uint32_t* tmem_base;
   volatile int* abort_flag;
   volatile int* stop_flag;
-  float2* merge;     // [res_merge_bufs][kRows][4] partial (max, sum) of every row, by row block
+  float2* merge;     // [kRows][4] partial (max, sum) of every row
 };
-
-// Row-block merge buffers of the forward: a column part can run at most one
-// row block ahead of the part that merges (two when a row block is a single
-// tile); see the epilogue.
-__host__ __device__ inline int res_merge_bufs(int C) { return C >= 2 ? 2 : 4; }
 
 __host__ __device__ inline size_t res_smem_bytes(int frow, int fcol, int K) {
   const size_t a = (size_t)kRows * frow * 2, b = (size_t)imin(K, kMaxN) * fcol * 2;
   const int C = (K + kMaxN - 1) / kMaxN;
-  return 1024 + 2 * a + (size_t)C * b + 32 * 8 + 16 + (size_t)res_merge_bufs(C) * kRows * 4 * sizeof(float2);
+  return 1024 + 2 * a + (size_t)C * b + 32 * 8 + 16 + kRows * 4 * sizeof(float2);
 }
 
 __device__ __forceinline__ ResSmem res_carve(uint8_t* raw, int frow, int fcol, int K) {
@@ -126,28 +121,36 @@ __device__ __forceinline__ ResSmem res_carve(uint8_t* raw, int frow, int fcol, i
 // element's column chunks, warp 2 issues the MMAs and owns TMEM, warp 3 is
 // idle, warps 4..19 are the epilogue (640 threads: up to 96 registers per
 // thread, room for a warp to hold its 64 values of a tile at once).
-constexpr int kFwdThreads = 608;
-constexpr int kFwdMmaWarp = 2, kFwdEpiWarp0 = 3;
-constexpr int kAdjThreads = 640;
-constexpr int kAdjMmaWarp = 2, kAdjEpiWarp0 = 4;
+constexpr int kFwdThreads = 640;
+constexpr int kFwdMmaWarp = 2, kFwdEpiWarp0 = 4;
 
-// 32 values of one row (a warp's half of its part of a tile), in registers,
-// folded into the row's online log-sum-exp: shift by the running maximum
-// (set from the first group when still -inf), 2^, summed in four chains as
+// The 64 values of one row in one warp's part of a tile, already in
+// registers, folded into the row's online log-sum-exp: shift by the running
+// maximum (set from the tile's first group when still -inf), 2^, summed as
 // they are produced; a partial sum above 2^32 (values far above the shift)
 // is redone from the registers at the exact maximum.
-__device__ __forceinline__ void lse_vals32(const uint32_t (&v)[32], float& m, float& sacc) {
+__device__ __forceinline__ void lse_regs64(const uint32_t (&va)[32], const uint32_t (&vb)[32], float& m, float& sacc) {
   if (m == -INFINITY) {
-    float mx = __uint_as_float(v[0]);
+    float mx = __uint_as_float(va[0]);
 #pragma unroll
-    for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(v[j]));
+    for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(va[j]));
     m = mx;
   }
   float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
   for (int j = 0; j < 32; j += 4) {
-    float x0 = __uint_as_float(v[j]), x1 = __uint_as_float(v[j + 1]);
-    float x2 = __uint_as_float(v[j + 2]), x3 = __uint_as_float(v[j + 3]);
+    float x0 = __uint_as_float(va[j]), x1 = __uint_as_float(va[j + 1]);
+    float x2 = __uint_as_float(va[j + 2]), x3 = __uint_as_float(va[j + 3]);
+    sub2(x0, x1, m);
+    sub2(x2, x3, m);
+    const float e0 = ex2f(x0), e1 = ex2f(x1), e2 = ex2f(x2), e3 = ex2f(x3);
+    add2(p0, p1, e0, e1);
+    add2(p2, p3, e2, e3);
+  }
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    float x0 = __uint_as_float(vb[j]), x1 = __uint_as_float(vb[j + 1]);
+    float x2 = __uint_as_float(vb[j + 2]), x3 = __uint_as_float(vb[j + 3]);
     sub2(x0, x1, m);
     sub2(x2, x3, m);
     const float e0 = ex2f(x0), e1 = ex2f(x1), e2 = ex2f(x2), e3 = ex2f(x3);
@@ -159,12 +162,12 @@ __device__ __forceinline__ void lse_vals32(const uint32_t (&v)[32], float& m, fl
   if (!(pt <= 4294967296.0f)) {  // per thread: the values are in its own registers
     float mx = m;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(v[j]));
+    for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fmaxf(__uint_as_float(va[j]), __uint_as_float(vb[j])));
     sacc *= ex2f(m - mx);
     m = mx;
     pt = 0.f;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) pt += ex2f(__uint_as_float(v[j]) - m);
+    for (int j = 0; j < 32; ++j) pt += ex2f(__uint_as_float(va[j]) - m) + ex2f(__uint_as_float(vb[j]) - m);
   }
   sacc += pt;
 }
@@ -315,106 +318,79 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_res(ResArgs a) {
   } else if (warp >= kFwdEpiWarp0) {
     // ------------------------------------------------------------ epilogue (16 warps)
     // Warp w reads TMEM lanes 32 (w % 4) .. +31 (tcgen05.ld's lane-quarter
-    // rule; the four warps of a quarter share one SM sub-partition) and
-    // column part p = (w - kFwdEpiWarp0) / 4 of every tile: 64 columns, taken
-    // as two halves of 32 so that a load is always in flight under the
-    // exponentials of the other half:
-    //   wait half 0 | load half 1 | 2^ half 0 | wait half 1 | hand the slot
-    //   back | wait for the next tile, load its half 0 | 2^ half 1 | ...
-    // (tcgen05.wait::ld waits for every load of the thread, so exactly one
-    // is outstanding at each wait).  At the end of a row block each part
-    // leaves its rows' partial (max, sum) in shared memory and the part
-    // rb % 4 of the quarter merges them and writes lt: a named barrier of
-    // the quarter's four warps (arrive for three of them, sync for the
-    // merging one), no CTA-wide barrier.  A part cannot get more than two
-    // tiles ahead of the merging part, because every tile's slot needs all
-    // sixteen warps to hand it back two tiles earlier: at most one row block
-    // ahead for C >= 2 tiles per row block, two for C = 1.  So the merge
-    // buffer of row block rb is reused by rb + nbuf (nbuf = 2 and 4) and its
-    // barrier by rb + 3 (three ids per quarter in turn): neither is touched
-    // again before the merging part is done with rb.  After an expired wait
-    // a warp skips all work but still takes part in every row block's
-    // barrier, so each barrier always sees its four warps.
+    // rule) and a quarter of each tile's columns, all of them into registers
+    // before it hands the slot back, so the next tile's MMAs start while it
+    // exponentiates.  The four quarters of a row are merged through shared
+    // memory between two named barriers that every epilogue warp executes
+    // for every row block it enters, and the decision to stop is read from a
+    // flag written between them.
     const int quarter = warp & 3;
     const int part = (warp - kFwdEpiWarp0) >> 2;
     const int row = quarter * 32 + lane;
-    const int nbuf = res_merge_bufs(C);
     const float lnK = logf((float)K);
-    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    int ts = 0, nrb_all = 0;
+    int ts = 0;
     uint32_t tph = 0;
-    bool ok = true;
-    uint32_t va[32], vb[32];
-    // TMEM address of this warp's columns of the tile in slot t of a chunk with nc columns
-    auto taddr = [&](int t, int nc) { return tmem + lane_off + (uint32_t)(t * kMaxN + part * (nc >> 2)); };
-    // the first tile of the CTA: its half 0 is loaded ahead of the loop
-    if (blockIdx.x < a.n_elts) {
-      ok = __all_sync(0xffffffffu, mbar_wait(&s.t_full[0], 0, lim, s.abort_flag));
-      if (ok) {
-        tc_fence_after();
-        tmem_ld32_issue(taddr(0, imin(kMaxN, K)), va);
-      }
-    }
-    for (long long e = blockIdx.x; e < a.n_elts; e += gridDim.x) {
+    bool stop = false;
+    for (long long e = blockIdx.x; e < a.n_elts && !stop; e += gridDim.x) {
       const long long p = a.parent[e];
-      for (int rb = 0; rb < R; ++rb, ++nrb_all) {
+      for (int rb = 0; rb < R; ++rb) {
         float m = -INFINITY, sacc = 0.f;
+        bool ok = true;
         const long long k = (long long)rb * kRows + row;
-        const bool merger = part == (rb & 3);
         // the row constant, read now so that its latency is spent under this row block's tiles
-        const float rc = (merger && ok) ? a.rowc[p * K + k] : 0.f;
-        for (int c = 0; c < C; ++c) {
+        const float rc = part == 0 ? a.rowc[p * K + k] : 0.f;
+        for (int c = 0; c < C && ok; ++c) {
           const int nc = imin(kMaxN, K - c * kMaxN);
-          if (ok) {
+          ok = mbar_wait(&s.t_full[ts], tph, lim, s.abort_flag);
+          ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ts * kMaxN + part * (nc >> 2));
+          if (nc == kMaxN) {
+            uint32_t va[32], vb[32];
+            tmem_ld32_issue(tbase, va);
+            tmem_ld32_issue(tbase + 32u, vb);
             tmem_wait32(va);
-            if (nc == kMaxN) tmem_ld32_issue(taddr(ts, nc) + 32u, vb);
-            lse_vals32(va, m, sacc);
-            if (nc == kMaxN) tmem_wait32(vb);
+            tmem_wait32(vb);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s.t_empty[ts]);
+            lse_regs64(va, vb, m, sacc);
+          } else {  // a 128-column last chunk: 32 columns per warp
+            lse_group32(tbase, m, sacc);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&s.t_empty[ts]);
           }
           ts ^= 1;
           if (ts == 0) tph ^= 1u;
-          // the CTA's next tile: (rb, c + 1), (rb + 1, 0) or the next element's first
-          const bool more = c + 1 < C || rb + 1 < R || e + gridDim.x < a.n_elts;
-          if (ok && more) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&s.t_full[ts], tph, lim, s.abort_flag));
-            if (ok) {
-              tc_fence_after();
-              const int nn = c + 1 < C ? imin(kMaxN, K - (c + 1) * kMaxN) : imin(kMaxN, K);
-              tmem_ld32_issue(taddr(ts, nn), va);
-            }
-          }
-          if (ok && nc == kMaxN) lse_vals32(vb, m, sacc);
         }
-        float2* mb = s.merge + (size_t)(nrb_all % nbuf) * kRows * 4;
-        const uint32_t bar_id = 1u + (uint32_t)(quarter * 3 + nrb_all % 3);  // ids 1..12
-        if (!merger) {
-          mb[row * 4 + part] = make_float2(m, sacc);
-          asm volatile("bar.arrive %0, 128;" ::"r"(bar_id) : "memory");
-        } else {
-          asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
-          if (ok) {
-            float M = m;
-            for (int j = 0; j < 4; ++j)
-              if (j != part) M = fmaxf(M, mb[row * 4 + j].x);
-            float S = m != -INFINITY ? sacc * ex2f(m - M) : 0.f;
-            for (int j = 0; j < 4; ++j) {
-              if (j == part) continue;
-              const float2 o = mb[row * 4 + j];
-              if (o.x != -INFINITY) S += o.y * ex2f(o.x - M);
-            }
-            a.lt[e * K + k] = rc + (M + log2f(S)) * kLn2 - lnK;
+        s.merge[row * 4 + part] = make_float2(m, sacc);
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        if (threadIdx.x == 32 * kFwdEpiWarp0) *s.stop_flag = *s.abort_flag;
+        if (part == 0 && ok) {
+          float M = -INFINITY;
+          for (int j = 0; j < 4; ++j) M = fmaxf(M, s.merge[row * 4 + j].x);
+          float S = 0.f;
+          for (int j = 0; j < 4; ++j) {
+            const float2 o = s.merge[row * 4 + j];
+            if (o.x != -INFINITY) S += o.y * ex2f(o.x - M);
           }
+          a.lt[e * K + k] = rc + (M + log2f(S)) * kLn2 - lnK;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        if (*s.stop_flag) {
+          stop = true;
+          break;
         }
       }
     }
   }
 
-  if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
   tc_fence_before();
   __syncthreads();
+  // after the barrier: every role has stopped, so an abort by any of them is seen
+  if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
   if (warp == kFwdMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
@@ -525,7 +501,7 @@ __device__ __forceinline__ float adj_sum_f32(const float (&v)[32], const float* 
 }
 
 template <bool TF32>
-__global__ void __launch_bounds__(kAdjThreads, 1) k_adj_res(AdjResArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, 1) k_adj_res(AdjResArgs a) {
   extern __shared__ uint8_t smem_raw[];
   const int NS = a.nst;
   AdjSmem s = adj_carve(smem_raw, a.frow, a.fcol, NS);
@@ -556,7 +532,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adj_res(AdjResArgs a) {
     *s.stop_flag = 0;
     fence_barrier_init();
   }
-  if (warp == kAdjMmaWarp) {
+  if (warp == kFwdMmaWarp) {
     tmem_alloc(s.tmem_base, 512);
     tmem_relinquish();
   }
@@ -632,7 +608,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adj_res(AdjResArgs a) {
         if (armed_d & (1u << st)) mbar_wait(&s.d_full[st], (last_d >> st) & 1u, drain_bound(lim), &never);
       }
     }
-  } else if (warp == kAdjMmaWarp) {
+  } else if (warp == kFwdMmaWarp) {
     // ------------------------------------------------------------ MMA issuer (one thread)
     if (lane == 0) {
       const int nks = a.ksteps;
@@ -691,7 +667,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adj_res(AdjResArgs a) {
       mbar_wait(s.done, 0, drain_bound(lim), &never);
     }
     __syncwarp();
-  } else if (warp >= kAdjEpiWarp0) {
+  } else if (warp >= kFwdEpiWarp0) {
     // ------------------------------------------------------------ epilogue (16 warps)
     // Warp w takes TMEM lanes 32 (w % 4) .. +31 and column quarter `part` of
     // every tile (loaded into registers before the slot is handed back) and
@@ -700,7 +676,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adj_res(AdjResArgs a) {
     // named barriers that every epilogue warp executes, and the decision to
     // stop is read from a flag written between them.
     const int quarter = warp & 3;
-    const int part = (warp - kAdjEpiWarp0) >> 2;
+    const int part = (warp - kFwdEpiWarp0) >> 2;
     const int row = quarter * 32 + lane;
     int ts = 0;
     uint32_t tph = 0;
@@ -762,7 +738,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adj_res(AdjResArgs a) {
 #pragma unroll
         for (int j = 0; j < kAdjPassRows; ++j) s.merge[(j * kRows + row) * 4 + part] = acc[j];
         asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
-        if (threadIdx.x == 32 * kAdjEpiWarp0) *s.stop_flag = *s.abort_flag;
+        if (threadIdx.x == 32 * kFwdEpiWarp0) *s.stop_flag = *s.abort_flag;
         if (ok && part < nrb) {  // warp part p writes row block p of the pass
           const float* mr = s.merge + (part * kRows + row) * 4;
           a.w_out[e * K + (long long)(h * kAdjPassRows + part) * kRows + row] = (mr[0] + mr[1]) + (mr[2] + mr[3]);
@@ -773,10 +749,11 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adj_res(AdjResArgs a) {
     }
   }
 
-  if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
   tc_fence_before();
   __syncthreads();
-  if (warp == kAdjMmaWarp) {
+  // after the barrier: every role has stopped, so an abort by any of them is seen
+  if (*s.abort_flag && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
+  if (warp == kFwdMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
@@ -884,9 +861,9 @@ cudaError_t tc_adjoint_res(qem_plan_t P, int l, bool tf32) {
   const long long grid = ch.n < P->num_sms ? ch.n : P->num_sms;
   const size_t smem = adj_res_smem_bytes(a.frow, a.fcol, a.nst);
   if (tf32)
-    k_adj_res<true><<<(unsigned)grid, kAdjThreads, smem, P->stream>>>(a);
+    k_adj_res<true><<<(unsigned)grid, kFwdThreads, smem, P->stream>>>(a);
   else
-    k_adj_res<false><<<(unsigned)grid, kAdjThreads, smem, P->stream>>>(a);
+    k_adj_res<false><<<(unsigned)grid, kFwdThreads, smem, P->stream>>>(a);
   return cudaGetLastError();
 }
 
