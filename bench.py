@@ -74,6 +74,10 @@ def parse(argv=None):
                    help="leaf level with the parent-conditioned proposal (permutation copies; two-level, FP32)")
     p.add_argument("--unit-peaks", action="store_true",
                    help="measure the per-SM rates of the exponential unit, the FP32 pipe and tcgen05.mma")
+    p.add_argument("--small-case", choices=["estep", "mlp"], default=None,
+                   help="run a small case for a profiler (no JSON line): estep = 12 EM iterations of "
+                        "hier_logistic M=1000 N=10 K=1024 bf16x3 on the host loop; mlp = the warm-start "
+                        "network's forward and gradient on 16384 users, twice")
     p.add_argument("--train-instances", type=int, default=2000)
     p.add_argument("--test-instances", type=int, default=16)
     return p.parse_args(argv)
@@ -484,22 +488,6 @@ def iterations_to_tol(plan, q0, T_max=TOL_T_MAX, seed=777):
     return hit, [float(x) for x in plateau]
 
 
-def graph_ms_per_iter(plan, q0, T=20, seed=99):
-    """Milliseconds per iteration of the single-launch loop (qem_run)."""
-    import torch
-    m = plan.mean_params(q0)
-    q = q0.clone()
-    mom = torch.empty(plan.q_len, dtype=torch.float64, device=q.device)
-    plan.run(2, TOL_LAMBDA, m.clone(), q, moments=mom, seed=seed)  # builds the graph
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    plan.run(T, TOL_LAMBDA, m, q, moments=mom, seed=seed)
-    e1.record()
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / T
-
-
 def train_warm_start(n_train, seed=TRAIN_SEED, T=60, epochs=8, batch=4096, lr=2e-3, shuffle_seed=5):
     """QEM on n_train seeded instances (split-BF16, batched), then the network
     trained on the users' final proposals.  Returns (network, seconds, losses)."""
@@ -525,63 +513,196 @@ def train_warm_start(n_train, seed=TRAIN_SEED, T=60, epochs=8, batch=4096, lr=2e
     return net, time.perf_counter() - t0, losses
 
 
-def warm_q0(plan, net):
-    """Cold proposal with the users' q replaced by the network's prediction."""
+def warm_start_fn(plan, net):
+    """A function that writes the network's proposal for the users into a
+    fresh copy of the cold proposal (features, forward and to_q run on the
+    device each call); the instance data and the cold proposal are uploaded
+    once, outside it."""
     import torch
     lv = plan.model.levels[1]
-    q0 = S.initial_q(plan.model)
-    feats = net.features(torch.as_tensor(lv.x).cuda(), torch.as_tensor(lv.y).cuda())
-    qu = net.predict_q(feats)
-    flat = plan.flat(q0)
+    x_d = torch.as_tensor(lv.x).cuda()
+    y_d = torch.as_tensor(lv.y).cuda()
+    cold = plan.flat(S.initial_q(plan.model))
     off = plan.model.levels[0].n * 2 * plan.model.levels[0].dim
-    flat[off:off + qu.numel()].copy_(qu.reshape(-1))
-    return flat
+
+    def fn():
+        q = cold.clone()
+        qu = net.predict_q(net.features(x_d, y_d))
+        q[off:off + qu.numel()].copy_(qu.reshape(-1))
+        return q
+    return fn
+
+
+def cold_start_fn(plan):
+    cold = plan.flat(S.initial_q(plan.model))
+    return lambda: cold.clone()
+
+
+def timed_qem(plan, q_init, T, seed):
+    """CUDA-event seconds of q_init() (the warm start's kernels, or a copy of
+    the cold proposal) plus T iterations of Alg. 1 in one qem_run launch,
+    on the plan's stream; returns (seconds, final q on the device).  The loop
+    graph is built by an untimed 2-iteration run first."""
+    import torch
+    q = q_init()
+    plan.run(2, TOL_LAMBDA, plan.mean_params(q), q, seed=seed + 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    q = q_init()
+    plan.run(T, TOL_LAMBDA, plan.mean_params(q), q, seed=seed)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3, q
+
+
+def oracle_reference(n_inst, T, seed, K=TOL_K):
+    """Alg. 1 in FP64 with the oracle's E-step on the first n_inst test
+    instances, from the cold proposal with the counter-based noise of `seed`
+    (the GPU runs' stream for the same instances of the batch).  Returns per
+    user [n_users, 2, D] the proposal (loc, scale) averaged over iterations
+    T/2+1..T, and per instance the mean log P_MP over those iterations."""
+    from oracle import oracle as O
+    O.build()
+    model = S.hier_logistic_batch(n_inst, M=TOL_M, N=TOL_N, seed=TEST_SEED)
+    q = [np.asarray(a, np.float64) for a in S.initial_q(model)]
+    m = [np.stack([a[:, 0], a[:, 0] ** 2 + a[:, 1] ** 2], 1) for a in q]
+    acc, lp = None, []
+    for t in range(1, T + 1):
+        r = O.estep(model, q, K, None, seed=seed, it=t)
+        m = [O.ema(m[l], r["mom"][l], TOL_LAMBDA) for l in range(2)]
+        q = [O.mstep(O.Q_GAUSS, m[l]) for l in range(2)]
+        if t > T // 2:
+            acc = q[1].copy() if acc is None else acc + q[1]
+            lp.append(r["log_pmp"])
+    return acc / (T - T // 2), np.mean(lp, 0)
+
+
+def moment_error(q_users, ref):
+    """Per user and dimension: |loc - loc_ref| / scale_ref and
+    |scale - scale_ref| / scale_ref; their mean and maximum."""
+    q_users = np.asarray(q_users, np.float64)[:ref.shape[0]]
+    el = np.abs(q_users[:, 0] - ref[:, 0]) / ref[:, 1]
+    es = np.abs(q_users[:, 1] - ref[:, 1]) / ref[:, 1]
+    return {"loc_mean": float(el.mean()), "loc_max": float(el.max()), "scale_mean": float(es.mean()),
+            "scale_max": float(es.max())}
+
+
+def iterations_to_target(plan, q0, target, T_max=TOL_T_MAX, seed=777):
+    """Per instance: the first iteration at which the mean log P_MP over the
+    last TOL_WINDOW iterations reaches target[i] (T_max when never)."""
+    tr = log_pmp_trace(plan, q0, T_max, seed)
+    hit = []
+    for j in range(tr.shape[1]):
+        h = T_max
+        for t in range(TOL_WINDOW, T_max + 1):
+            if tr[t - TOL_WINDOW:t, j].mean() >= target[j]:
+                h = t
+                break
+        hit.append(h)
+    return hit
 
 
 def run_time_to_tol(args):
     import torch
     from paper_2503_08264_gb300 import qem
     torch.cuda.set_device(0)
+    seed = 777                                    # the noise stream of every run below
     net, train_s, losses = train_warm_start(args.train_instances)
     n_test = args.test_instances
-    # the plain FP32 baseline, one instance per plan
-    it_plain, pl_plain, ms_single = [], [], []
+    t0 = time.perf_counter()
+    ref, ref_lp = oracle_reference(n_test, TOL_REF_T, seed)
+    oracle_s = time.perf_counter() - t0
+    # the same reference from another noise stream on two instances: the
+    # chain-to-chain spread of the converged moments (the floor of moment_err)
+    ref2, _ = oracle_reference(2, TOL_REF_T, seed + 1)
+    spread = moment_error(ref2, ref[:2 * TOL_M])
+    target = ref_lp - TOL_DELTA
+    # the plain FP32 baseline, one instance per plan, each run for its own iterations
+    it_plain, sec_plain, q_plain = [], [], []
     for i in range(n_test):
         mdl = S.hier_logistic(M=TOL_M, N=TOL_N, seed=TEST_SEED + i)
         plan = qem.Plan(mdl, TOL_K, precision="fp32")
-        q0 = plan.flat(S.initial_q(mdl))
-        h, pl = iterations_to_tol(plan, q0)
+        init = cold_start_fn(plan)
+        h = iterations_to_target(plan, init(), target[i:i + 1], seed=seed)
+        sec, q = timed_qem(plan, init, h[0], seed)
         it_plain += h
-        pl_plain += pl
-        ms_single.append(graph_ms_per_iter(plan, q0))
+        sec_plain.append(sec)
+        q_plain.append(plan.split_q(q)[1])
         plan.close()
     batch = S.hier_logistic_batch(n_test, M=TOL_M, N=TOL_N, seed=TEST_SEED)
     out = {}
     for name, prec, warm in (("batched_bf16x3_cold", "bf16x3", False), ("batched_bf16x3_warm", "bf16x3", True),
                              ("batched_fp32_warm", "fp32", True)):
         plan = qem.Plan(batch, TOL_K, precision=prec)
-        q0 = warm_q0(plan, net) if warm else plan.flat(S.initial_q(batch))
-        its, pl = iterations_to_tol(plan, q0)
-        ms = graph_ms_per_iter(plan, q0)
-        out[name] = {"iterations": its, "ms_per_iteration": ms, "seconds": max(its) * ms * 1e-3,
-                     "plateau_minus_plain": float(np.mean(np.array(pl) - np.array(pl_plain)))}
+        init = warm_start_fn(plan, net) if warm else cold_start_fn(plan)
+        its = iterations_to_target(plan, init(), target, seed=seed)
+        sec, q = timed_qem(plan, init, max(its), seed)
+        out[name] = {"iterations": its, "seconds": sec, "ms_per_iteration": sec * 1e3 / max(its),
+                     "moment_err": moment_error(plan.split_q(q)[1], ref)}
         plan.close()
-    plain_s = sum(i * m for i, m in zip(it_plain, ms_single)) * 1e-3
+    plain_s = float(sum(sec_plain))
     fast = out["batched_bf16x3_warm"]
     line = {"metric": "time to tolerance (all test instances)", "value": fast["seconds"], "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "dtype": "bf16x3", "data": "synthetic",
             "vs_plain_fp32": plain_s / fast["seconds"] if fast["seconds"] > 0 else None,
             "plain_fp32": {"seconds": plain_s, "iterations": it_plain,
-                           "ms_per_iteration_mean": float(np.mean(ms_single))},
+                           "moment_err": moment_error(np.concatenate(q_plain), ref)},
             "variants": out,
+            "oracle_reference": {"instances": n_test, "iterations": TOL_REF_T, "seconds": round(oracle_s, 1),
+                                 "plateau_log_pmp": [round(float(x), 2) for x in ref_lp],
+                                 "chain_to_chain_moment_spread": spread},
             "config": {"workload": f"hier_logistic_M{TOL_M}_N{TOL_N}_K{TOL_K} x {n_test} test instances",
                        "train": f"{args.train_instances} instances, {len(losses)} epochs, {train_s:.1f} s",
-                       "train_loss_last": losses[-1], "lambda": TOL_LAMBDA,
-                       "criterion": f"mean log P_MP over {TOL_WINDOW} iterations within {TOL_DELTA} nats of "
-                                    "the plateau",
-                       "plateau": f"each run's mean log P_MP over iterations {TOL_T_MAX // 2 + 1}-{TOL_T_MAX}",
-                       "max_iterations": TOL_T_MAX, "time": "iterations x graph-loop ms per iteration"}}
+                       "train_loss_last": losses[-1], "lambda": TOL_LAMBDA, "noise_seed": seed,
+                       "criterion": f"per instance, the mean log P_MP over {TOL_WINDOW} iterations reaches the "
+                                    f"FP64 oracle's plateau less {TOL_DELTA} nats (the same target for every "
+                                    "run); plateau: the oracle's Alg. 1 from the cold proposal, mean log P_MP "
+                                    f"over its iterations {TOL_REF_T // 2 + 1}-{TOL_REF_T}",
+                       "max_iterations": TOL_T_MAX,
+                       "time": "CUDA events around each run: the warm start's features, forward and to_q "
+                               "(warm variants) and the iterations to tolerance in one qem_run launch; "
+                               "plain FP32 sums its per-instance runs",
+                       "moment_err": "every user at the iteration of tolerance (the last instance's, for the "
+                                     "batched runs) against the oracle's proposal averaged over iterations "
+                                     f"{TOL_REF_T // 2 + 1}-{TOL_REF_T}: |loc - loc_ref| / scale_ref and "
+                                     "|scale - scale_ref| / scale_ref; chain_to_chain_moment_spread is the same "
+                                     "measure between two oracle runs that differ only in their noise stream "
+                                     "(two instances): the floor of any run's moment error"}}
     print(json.dumps(line))
+    return 0
+
+
+def run_small_case(kind: str):
+    """Small, short workloads for ncu captures (a few GB at most, seconds of GPU time)."""
+    import torch
+    from paper_2503_08264_gb300 import qem
+    if kind == "estep":
+        model = S.hier_logistic(M=1000, N=10, seed=1000)
+        plan = qem.Plan(model, 1024, precision="bf16x3")
+        q = plan.flat(S.initial_q(model))
+        m = plan.mean_params(q)
+        mom = torch.empty(plan.q_len, dtype=torch.float64, device="cuda")
+        for t in range(1, 13):
+            plan.estep(q, None, seed=5, it=t, moments=mom)
+            plan.mstep(mom, m, q, EMA_LAMBDA, t=t)
+        torch.cuda.synchronize()
+        print("small case estep: log P_MP", plan.log_pmp())
+        return 0
+    from paper_2503_08264_gb300.warmstart import WarmStart
+    n = 16384
+    model = S.hier_logistic(M=n, N=5, seed=3)
+    rng = np.random.default_rng(1)
+    target = torch.as_tensor(np.stack([rng.standard_normal((n, 18)), rng.uniform(0.2, 1.2, (n, 18))],
+                                      1).astype(np.float32)).cuda()
+    net = WarmStart(seed=1)
+    f = net.features(torch.as_tensor(model.levels[1].x).cuda(), torch.as_tensor(model.levels[1].y).cuda())
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        net.forward(f)
+        net.loss_grad(f, target, loss)
+    torch.cuda.synchronize()
+    print("small case mlp: loss", loss.item())
     return 0
 
 
@@ -880,6 +1001,8 @@ def main(argv=None):
         return run_unit_peaks()
     if args.impl == "reference":
         return run_reference(args)
+    if args.small_case:
+        return run_small_case(args.small_case)
     if args.metric == "time_to_tol":
         return run_time_to_tol(args)
     if args.root == "split":

@@ -61,7 +61,7 @@ def test_warm_start_reaches_plateau_in_fewer_iterations():
     batch = S.hier_logistic_batch(n_test, M=bench.TOL_M, N=bench.TOL_N, seed=bench.TEST_SEED)
     plan = qem.Plan(batch, bench.TOL_K, precision="bf16x3")
     cold, pl_cold = bench.iterations_to_tol(plan, plan.flat(S.initial_q(batch)))
-    warm, pl_warm = bench.iterations_to_tol(plan, bench.warm_q0(plan, net))
+    warm, pl_warm = bench.iterations_to_tol(plan, bench.warm_start_fn(plan, net)())
     print("iterations to the plateau: cold", cold, "warm", warm)
     print("plateaus: cold", [round(x, 1) for x in pl_cold], "warm", [round(x, 1) for x in pl_warm])
     assert sum(warm) < sum(cold)
