@@ -229,9 +229,8 @@ size_t chain_smem(int D, int K, bool adjoint) {
 
 template <int MAXD, int G>
 static cudaError_t chain_cfg(size_t fwd, size_t adj) {
-  cudaError_t e = cudaFuncSetAttribute(k_chain_forward<MAXD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_chain_adjoint<MAXD, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj);
+  cudaError_t e = opt_in_smem(k_chain_forward<MAXD, G>, fwd);
+  if (e == cudaSuccess) e = opt_in_smem(k_chain_adjoint<MAXD, G>, adj);
   return e;
 }
 

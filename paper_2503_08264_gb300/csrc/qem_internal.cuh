@@ -324,6 +324,23 @@ cudaError_t launch_set_ctl(Ctl* ctl, unsigned long long seed, unsigned long long
 cudaError_t launch_advance_ctl(Ctl* ctl, long long n_inst, cudaStream_t s);
 // Counts y < kCountTable of a Poisson-log likelihood take their constant
 // y s0 - e^s0 - lgamma(y + 1) from a table built once per plan.
+// Dynamic shared memory a kernel is opted into (the sm_103a per-block
+// maximum).  Kernels are opted into the maximum, not the current plan's
+// need: the attribute is per kernel and process-wide, so a plan that set a
+// smaller value would make an earlier plan's larger launches fail.
+constexpr int kSmemOptIn = 227 * 1024;
+// Opt kernel f into all the dynamic shared memory it can have (the maximum
+// less its static shared memory); cudaErrorInvalidValue when `need` bytes
+// do not fit.
+template <class T>
+inline cudaError_t opt_in_smem(T* f, size_t need) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, f);
+  if (e != cudaSuccess) return e;
+  const int avail = kSmemOptIn - (int)fa.sharedSizeBytes;
+  if (need > (size_t)avail) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
+}
 constexpr int kCountTable = 4096;
 cudaError_t launch_count_table(double* tab, cudaStream_t s);
 cudaError_t launch_elem_const(const LevelView& v, const float* q, cudaStream_t s);

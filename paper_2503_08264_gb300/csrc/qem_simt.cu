@@ -459,7 +459,7 @@ size_t sample_local_smem(const LevelView& v, int K, int threads) {
 template <int MAXD>
 static cudaError_t sample_cfg(size_t smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(k_sample_local<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return opt_in_smem(k_sample_local<MAXD>, smem);
 }
 
 cudaError_t configure_sample_local(size_t smem) {

@@ -254,7 +254,7 @@ cudaError_t launch_adj_small(const LevelView& v, const LevelView& par, int K, cu
 
 template <int MAXD>
 static cudaError_t adj_small_cfg(size_t sm) {
-  return cudaFuncSetAttribute(k_adj_small<MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return opt_in_smem(k_adj_small<MAXD>, sm);
 }
 
 cudaError_t configure_adj_small(int D, int K) {

@@ -1043,24 +1043,21 @@ qem_status tc_plan_reserve(qem_plan_t P, const qem_model_desc* desc, char* base,
 qem_status tc_plan_init(qem_plan_t P, const qem_model_desc*) {
   if (P->precision == QEM_PREC_FP32) return QEM_OK;
   const bool tf32 = P->tc->tf32;
-  size_t sf = 0, sa = 0;
   for (int l = 1; l < P->L; ++l) {
     const Layout& L = P->tc->lay[l];
     int na, ns;
     if (!contract_config(L.fka, L.fkb, false, na, ns)) return QEM_ERR_UNSUPPORTED;
-    sf = std::max(sf, contract_smem_bytes(L.fka, L.fkb, false, na, ns));
     if (!contract_config(L.fkb, L.fka, true, na, ns)) return QEM_ERR_UNSUPPORTED;
-    sa = std::max(sa, contract_smem_bytes(L.fkb, L.fka, true, na, ns));
     const qem_status rs = tc_res_init(L.fka, L.fkb, P->K, tf32);
     if (rs != QEM_OK) return rs;
   }
   cudaError_t e1, e2;
   if (tf32) {
-    e1 = cudaFuncSetAttribute(k_contract<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
-    e2 = cudaFuncSetAttribute(k_contract<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+    e1 = opt_in_smem(k_contract<false, true>, 0);
+    e2 = opt_in_smem(k_contract<true, true>, 0);
   } else {
-    e1 = cudaFuncSetAttribute(k_contract<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
-    e2 = cudaFuncSetAttribute(k_contract<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+    e1 = opt_in_smem(k_contract<false, false>, 0);
+    e2 = opt_in_smem(k_contract<true, false>, 0);
   }
   return e1 == cudaSuccess && e2 == cudaSuccess ? QEM_OK : QEM_ERR_CUDA;
 }

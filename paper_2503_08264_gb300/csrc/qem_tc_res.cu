@@ -780,16 +780,14 @@ bool tc_adj_res_fits(int frow, int fcol, int K) { return tc_adj_res_stages(frow,
 qem_status tc_res_init(int frow, int fcol, int K, bool tf32) {
   cudaError_t e = cudaSuccess;
   if (tc_res_fits(frow, fcol, K)) {
-    const int bytes = (int)res_smem_bytes(frow, fcol, K);
-    e = tf32 ? cudaFuncSetAttribute(k_fwd_res<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-             : cudaFuncSetAttribute(k_fwd_res<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const size_t bytes = res_smem_bytes(frow, fcol, K);
+    e = tf32 ? opt_in_smem(k_fwd_res<true>, bytes) : opt_in_smem(k_fwd_res<false>, bytes);
   }
   // the adjoint's rows are the child operand (fcol wide), its columns the parent's (frow wide)
   const int nst = tc_adj_res_stages(fcol, frow, K);
   if (e == cudaSuccess && nst > 0) {
-    const int bytes = (int)adj_res_smem_bytes(fcol, frow, nst);
-    e = tf32 ? cudaFuncSetAttribute(k_adj_res<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-             : cudaFuncSetAttribute(k_adj_res<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const size_t bytes = adj_res_smem_bytes(fcol, frow, nst);
+    e = tf32 ? opt_in_smem(k_adj_res<true>, bytes) : opt_in_smem(k_adj_res<false>, bytes);
   }
   return e == cudaSuccess ? QEM_OK : QEM_ERR_CUDA;
 }

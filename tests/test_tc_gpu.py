@@ -237,3 +237,25 @@ def test_expired_wait_reports_timeout_and_the_next_plan_works():
         plan.close()
     got, ref = run_pair(model, K, q, eps, precision="bf16x3")
     assert_parity(model, q, got, ref, 1e-3, 1e-3, 1e-3)
+
+
+def test_plans_of_different_shapes_coexist():
+    """Kernels are opted into the maximum dynamic shared memory once: a plan
+    with smaller operands made after a larger one must not lower the limit
+    the larger plan's launches need (K = 1024 rows need ~220 KB per CTA)."""
+    from paper_2503_08264_gb300 import qem
+    big_model = S.hier_logistic(M=24, N=5, seed=95)
+    small_model = S.hier_logistic(M=24, N=5, seed=96)
+    big = qem.Plan(big_model, 1024, precision="bf16x3")
+    small = qem.Plan(small_model, 256, precision="bf16x3")
+    q_small = S.random_q(small_model, seed=97, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    small.estep(small.flat(q_small), small.flat(S.noise(small_model, 256, seed=98)))
+    small.log_pmp()
+    small.close()
+    q = S.random_q(big_model, seed=99, loc_scale=0.3, sd_lo=0.3, sd_hi=0.8)
+    eps = S.noise(big_model, 1024, seed=100)
+    mom, _ = big.estep(big.flat(q), big.flat(eps))
+    torch.cuda.synchronize()
+    got = {"log_pmp": big.log_pmp(), "mom": big.split_q(mom), "w": big.split_w(big.weights())}
+    big.close()
+    assert_parity(big_model, q, got, O.estep(big_model, q, 1024, eps=eps), 1e-3, 1e-3, 1e-3)
