@@ -74,9 +74,10 @@ def parse(argv=None):
                    help="leaf level with the parent-conditioned proposal (permutation copies; two-level, FP32)")
     p.add_argument("--unit-peaks", action="store_true",
                    help="measure the per-SM rates of the exponential unit, the FP32 pipe and tcgen05.mma")
-    p.add_argument("--small-case", choices=["estep", "mlp"], default=None,
+    p.add_argument("--small-case", choices=["estep", "estep_steady", "mlp"], default=None,
                    help="run a small case for a profiler (no JSON line): estep = 12 EM iterations of "
-                        "hier_logistic M=1000 N=10 K=1024 bf16x3 on the host loop; mlp = the warm-start "
+                        "hier_logistic M=1000 N=10 K=1024 bf16x3 on the host loop; estep_steady = 100 "
+                        "iterations, then 3 inside the NVTX range small_case; mlp = the warm-start "
                         "network's forward and gradient on 16384 users, twice")
     p.add_argument("--train-instances", type=int, default=2000)
     p.add_argument("--test-instances", type=int, default=16)
@@ -270,14 +271,19 @@ PEAK_SOURCE = "profiles/mufu_fp32_peaks.md"
 # kernel's source file at capture time: reported only while that file is
 # unchanged (the summary under profiles/ gives the capture command).
 NCU_TRAFFIC = {
-    # the element-resident forward (k_fwd_res); captured on the 1000-element
-    # small case (bench.py --small-case estep) and scaled by elements to the
-    # 5000 of this workload: its traffic is per element (the element's column
-    # rows once, lt written once; the parent's rows stay in L2)
+    # the element-resident forward (k_fwd_res) and adjoint (k_adj_res),
+    # captured at the EM steady state of the 1000-element small case
+    # (bench.py --small-case estep_steady) and scaled by elements to the 5000
+    # of this workload: their traffic is per element (the element's rows
+    # once, its output row written once; the parent's rows stay in L2)
     ("forward", "hier_logistic_M5000_N10_K1024", "bf16x3"): {
-        "bytes": 5 * (164151040 + 5275904), "source": "paper_2503_08264_gb300/csrc/qem_tc_res.cu",
-        "blob": "1d4dee857afcc792302c112092a2b44f1201f0e6",
+        "bytes": 5 * (164132864 + 5216512), "source": "paper_2503_08264_gb300/csrc/qem_tc_res.cu",
+        "blob": "094144963c8e839857c3dbd9c6f37c9d9fc1db7f",
         "profile": "profiles/fwd_res_bf16x3_hier_logistic_M1000_K1024.md"},
+    ("adjoint", "hier_logistic_M5000_N10_K1024", "bf16x3"): {
+        "bytes": 5 * (167698432 + 5387776), "source": "paper_2503_08264_gb300/csrc/qem_tc_res.cu",
+        "blob": "094144963c8e839857c3dbd9c6f37c9d9fc1db7f",
+        "profile": "profiles/adj_res_bf16x3_hier_logistic_M1000_K1024.md"},
 }
 
 
@@ -680,17 +686,28 @@ def run_small_case(kind: str):
     """Small, short workloads for ncu captures (a few GB at most, seconds of GPU time)."""
     import torch
     from paper_2503_08264_gb300 import qem
-    if kind == "estep":
+    if kind in ("estep", "estep_steady"):
+        # estep: 12 iterations from q_0 (the adjoint still on the small-set
+        # kernel); estep_steady: 100 iterations to the EM steady state, then 3
+        # inside the NVTX range "small_case" (both tensor-core contractions
+        # element-resident, the adjoint over ~800 kept parent samples)
         model = S.hier_logistic(M=1000, N=10, seed=1000)
         plan = qem.Plan(model, 1024, precision="bf16x3")
         q = plan.flat(S.initial_q(model))
         m = plan.mean_params(q)
         mom = torch.empty(plan.q_len, dtype=torch.float64, device="cuda")
-        for t in range(1, 13):
+        n_pre, n_in = (12, 0) if kind == "estep" else (100, 3)
+        for t in range(1, n_pre + n_in + 1):
+            if t == n_pre + 1:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push("small_case")
             plan.estep(q, None, seed=5, it=t, moments=mom)
             plan.mstep(mom, m, q, EMA_LAMBDA, t=t)
+        if n_in:
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-        print("small case estep: log P_MP", plan.log_pmp())
+        print("small case", kind, ": log P_MP", plan.log_pmp(), "tensor-core adjoint pairs", plan.adjoint_pairs())
         return 0
     from paper_2503_08264_gb300.warmstart import WarmStart
     n = 16384

@@ -271,7 +271,7 @@ const int kSampleCand[] = {64, 128, 256};
 const int kMomCand[] = {128, 256, 512};
 const int kRowsCand[] = {64, 128, 256};
 const int kChunkCand[] = {16, 32, 64};
-const int kSchedCand[] = {1, 3, 0, 2};
+const int kSchedCand[] = {3, 1, 0, 2};
 
 template <size_t N>
 bool one_of(int v, const int (&c)[N]) {

@@ -113,7 +113,7 @@ struct Tune {
   int mom_threads = 256;     // threads per block of the moments kernel (one block per element)
   int fwd_rows = 128;        // FP32 contraction: parent samples per block (one per thread)
   int fwd_chunk = 32;        // FP32 contraction: child samples staged per shared-memory round
-  int tc_sched = 1;          // tensor-core schedules, bit 0: element-resident forward, bit 1: element-resident
+  int tc_sched = 3;          // tensor-core schedules, bit 0: element-resident forward, bit 1: element-resident
                              // adjoint (each when its operands fit); a clear bit: the streaming schedule
 };
 }  // namespace qem

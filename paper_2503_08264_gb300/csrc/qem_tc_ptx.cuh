@@ -88,6 +88,31 @@ __device__ __forceinline__ bool mbar_spin(uint64_t* b, uint32_t parity, long lon
     }
   }
 }
+// The same wait for a whole converged warp: every lane polls and the outcome
+// is a vote, so it is the same in every lane and the code after it stays
+// warp-uniform.
+__device__ __forceinline__ bool mbar_spin_warp(uint64_t* b, uint32_t parity, long long limit,
+                                               volatile int* abort_flag) {
+  const long long t0 = clock64();
+  for (int i = 0;; ++i) {
+    if (__any_sync(0xffffffffu, mbar_test(b, parity))) return true;
+    if ((i & 63) == 63) {
+      const bool late = clock64() - t0 > limit;
+      if (__any_sync(0xffffffffu, late || *abort_flag != 0)) {
+        if (late) *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+// One lane of a converged warp (elect.sync).  An MMA issuer runs its loop in
+// all 32 lanes, so that its control flow, descriptors and barrier addresses
+// are warp-uniform, and only the tcgen05 issue itself is single-lane.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t e;
+  asm volatile("{\n .reg .pred p;\n elect.sync _|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n" : "=r"(e));
+  return e != 0;
+}
 // Bound of the teardown waits (a CTA's own bulk copies and MMAs must land
 // before it frees TMEM or exits, also after an abort): the plan's wait bound,
 // but never below ~2 s of SM cycles, so that a tiny timeout_s aborts the

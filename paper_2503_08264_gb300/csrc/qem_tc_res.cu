@@ -25,13 +25,19 @@
 // issue rate) in two TMEM slots of 256 columns.  Roles (640 threads, one CTA
 // per SM): warp 0 loads the row side, warp 1 the column side (and the
 // adjoint's column shifts), warp 2 issues the MMAs (one thread) and owns
-// TMEM, warp 3 is idle, warps 4..19 are the epilogue: warp w reads TMEM lanes
-// 32 (w % 4) .. +31 (the rule of tcgen05.ld) and a quarter of every tile's
-// columns, all 64 of its values into registers before it hands the slot
-// back, so the next tile's MMAs run while it exponentiates; four warps per
-// SM sub-partition cover one another's load and hand-off latencies.  The
-// four quarters of a row are merged through shared memory once per row
-// block (forward) or once per pass (adjoint).
+// TMEM, warp 3 is idle, warps 4..19 are the epilogue; warp w reads TMEM lanes
+// 32 (w % 4) .. +31 (the rule of tcgen05.ld).
+//  * forward: the epilogue is two groups of eight warps that take alternate
+//    tiles (group g every tile of TMEM slot g), each warp half of a tile's
+//    columns in two pieces of 64; while one group waits for its tile, loads
+//    it or merges a row block, the other exponentiates, so the ex2 unit is
+//    not left idle between tiles.  A row block's partial sums meet in shared
+//    memory, completed by the group that took its last tile, without a
+//    CTA-wide barrier.
+//  * adjoint: each warp takes a quarter of every tile's columns, all 64 of
+//    its values into registers before it hands the slot back, so the next
+//    tile's MMAs run while it exponentiates; the four quarters of a row are
+//    merged through shared memory once per pass.
 //
 // Every wait is bounded; an expired wait sets the CTA's abort flag, every
 // role stops at its next wait, the producers wait (bounded, ignoring the
@@ -78,16 +84,17 @@ struct ResSmem {
   uint64_t* t_full;   // [2]
   uint64_t* t_empty;  // [2]
   uint64_t* done;
+  uint64_t* m_full;  // [2] a row block's partials written (one arrival per producing thread)
+  uint64_t* m_free;  // [2] a row block's partials read (one arrival per completing thread)
   uint32_t* tmem_base;
   volatile int* abort_flag;
-  volatile int* stop_flag;
-  float2* merge;     // [kRows][4] partial (max, sum) of every row
+  float2* merge;     // [2][kRows][4] partial (max, sum) of every row, per (group, half)
 };
 
 __host__ __device__ inline size_t res_smem_bytes(int frow, int fcol, int K) {
   const size_t a = (size_t)kRows * frow * 2, b = (size_t)imin(K, kMaxN) * fcol * 2;
   const int C = (K + kMaxN - 1) / kMaxN;
-  return 1024 + 2 * a + (size_t)C * b + 32 * 8 + 16 + kRows * 4 * sizeof(float2);
+  return 1024 + 2 * a + (size_t)C * b + 32 * 8 + 16 + 2 * kRows * 4 * sizeof(float2);
 }
 
 __device__ __forceinline__ ResSmem res_carve(uint8_t* raw, int frow, int fcol, int K) {
@@ -108,10 +115,11 @@ __device__ __forceinline__ ResSmem res_carve(uint8_t* raw, int frow, int fcol, i
   s.t_full = bars + 4 + 2 * kResMaxChunks;
   s.t_empty = s.t_full + 2;
   s.done = s.t_empty + 2;
+  s.m_full = s.done + 1;
+  s.m_free = s.m_full + 2;
   p += 32 * 8;
   s.tmem_base = reinterpret_cast<uint32_t*>(p);
   s.abort_flag = reinterpret_cast<volatile int*>(p + 4);
-  s.stop_flag = reinterpret_cast<volatile int*>(p + 8);
   p += 16;
   s.merge = reinterpret_cast<float2*>(p);
   return s;
@@ -119,57 +127,56 @@ __device__ __forceinline__ ResSmem res_carve(uint8_t* raw, int frow, int fcol, i
 
 // Roles of the forward: warp 0 loads the parent's row blocks, warp 1 the
 // element's column chunks, warp 2 issues the MMAs and owns TMEM, warp 3 is
-// idle, warps 4..19 are the epilogue (640 threads: up to 96 registers per
-// thread, room for a warp to hold its 64 values of a tile at once).
+// idle, warps 4..19 are the epilogue in two groups of 8 (640 threads: up to
+// 96 registers per thread, room for a warp to hold 64 values at once).
 constexpr int kFwdThreads = 640;
-constexpr int kFwdMmaWarp = 2, kFwdEpiWarp0 = 4;
+constexpr int kFwdMmaWarp = 2, kFwdEpiWarp0 = 4, kFwdGroupWarps = 8;
 
-// The 64 values of one row in one warp's part of a tile, already in
-// registers, folded into the row's online log-sum-exp: shift by the running
-// maximum (set from the tile's first group when still -inf), 2^, summed as
-// they are produced; a partial sum above 2^32 (values far above the shift)
-// is redone from the registers at the exact maximum.
-__device__ __forceinline__ void lse_regs64(const uint32_t (&va)[32], const uint32_t (&vb)[32], float& m, float& sacc) {
-  if (m == -INFINITY) {
-    float mx = __uint_as_float(va[0]);
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// The 64 values of one row in one warp's piece of a tile, already in
+// registers, folded into the row's online log-sum-exp in two passes: the
+// exact maximum of the piece and the running one (four chains of
+// three-input max), then every value shifted and exponentiated in place,
+// then summed.  No exponential waits on another's sum, so all 64 can be in
+// flight in the ex2 unit at once, and every term is at most 1 (no overflow).
+// The values' registers are overwritten.
+__device__ __forceinline__ void lse_regs64(uint32_t (&va)[32], uint32_t (&vb)[32], float& m, float& sacc) {
+  const auto F = [](uint32_t x) { return __uint_as_float(x); };
+  float c0 = fmaxf(F(va[0]), F(va[1])), c1 = fmaxf(F(va[16]), F(va[17]));
+  float c2 = fmaxf(F(vb[0]), F(vb[1])), c3 = fmaxf(F(vb[16]), F(vb[17]));
 #pragma unroll
-    for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(va[j]));
-    m = mx;
+  for (int j = 2; j < 16; j += 2) {
+    c0 = max3f(c0, F(va[j]), F(va[j + 1]));
+    c1 = max3f(c1, F(va[16 + j]), F(va[17 + j]));
+    c2 = max3f(c2, F(vb[j]), F(vb[j + 1]));
+    c3 = max3f(c3, F(vb[16 + j]), F(vb[17 + j]));
+  }
+  const float mn = max3f(max3f(c0, c1, m), c2, c3);
+  if (mn != m) sacc *= ex2f(m - mn);  // the running sum moves to the new maximum (0 while m is -inf)
+  m = mn;
+#pragma unroll
+  for (int j = 0; j < 32; j += 2) {
+    float x0 = F(va[j]), x1 = F(va[j + 1]), y0 = F(vb[j]), y1 = F(vb[j + 1]);
+    sub2(x0, x1, m);
+    sub2(y0, y1, m);
+    va[j] = __float_as_uint(ex2f(x0));
+    va[j + 1] = __float_as_uint(ex2f(x1));
+    vb[j] = __float_as_uint(ex2f(y0));
+    vb[j + 1] = __float_as_uint(ex2f(y1));
   }
   float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
-  for (int j = 0; j < 32; j += 4) {
-    float x0 = __uint_as_float(va[j]), x1 = __uint_as_float(va[j + 1]);
-    float x2 = __uint_as_float(va[j + 2]), x3 = __uint_as_float(va[j + 3]);
-    sub2(x0, x1, m);
-    sub2(x2, x3, m);
-    const float e0 = ex2f(x0), e1 = ex2f(x1), e2 = ex2f(x2), e3 = ex2f(x3);
-    add2(p0, p1, e0, e1);
-    add2(p2, p3, e2, e3);
-  }
-#pragma unroll
-  for (int j = 0; j < 32; j += 4) {
-    float x0 = __uint_as_float(vb[j]), x1 = __uint_as_float(vb[j + 1]);
-    float x2 = __uint_as_float(vb[j + 2]), x3 = __uint_as_float(vb[j + 3]);
-    sub2(x0, x1, m);
-    sub2(x2, x3, m);
-    const float e0 = ex2f(x0), e1 = ex2f(x1), e2 = ex2f(x2), e3 = ex2f(x3);
-    add2(p0, p1, e0, e1);
-    add2(p2, p3, e2, e3);
+  for (int j = 0; j < 32; j += 2) {
+    add2(p0, p1, F(va[j]), F(va[j + 1]));
+    add2(p2, p3, F(vb[j]), F(vb[j + 1]));
   }
   add2(p0, p1, p2, p3);
-  float pt = p0 + p1;
-  if (!(pt <= 4294967296.0f)) {  // per thread: the values are in its own registers
-    float mx = m;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fmaxf(__uint_as_float(va[j]), __uint_as_float(vb[j])));
-    sacc *= ex2f(m - mx);
-    m = mx;
-    pt = 0.f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) pt += ex2f(__uint_as_float(va[j]) - m) + ex2f(__uint_as_float(vb[j]) - m);
-  }
-  sacc += pt;
+  sacc += p0 + p1;
 }
 
 template <bool TF32>
@@ -187,7 +194,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_res(ResArgs a) {
       mbar_init(&s.a_full[i], 1);
       mbar_init(&s.a_empty[i], 1);
       mbar_init(&s.t_full[i], 1);
-      mbar_init(&s.t_empty[i], kEpiWarps);
+      mbar_init(&s.t_empty[i], kFwdGroupWarps);
+      // a row block's partials come from both groups when it has two tiles or more
+      mbar_init(&s.m_full[i], 32 * kFwdGroupWarps * (C >= 2 ? 2 : 1));
+      mbar_init(&s.m_free[i], kRows);
     }
     for (int c = 0; c < C; ++c) {
       mbar_init(&s.b_full[c], 1);
@@ -195,7 +205,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_res(ResArgs a) {
     }
     mbar_init(s.done, 1);
     *s.abort_flag = 0;
-    *s.stop_flag = 0;
     fence_barrier_init();
   }
   if (warp == kFwdMmaWarp) {
@@ -265,8 +274,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_res(ResArgs a) {
         if (armed & (1u << c)) mbar_wait(&s.b_full[c], (last >> c) & 1u, drain_bound(lim), &never);
     }
   } else if (warp == kFwdMmaWarp) {
-    // ------------------------------------------------------------ MMA issuer (one thread)
-    if (lane == 0) {
+    // ------------------------------------------------------------ MMA issuer (one elected lane)
+    {
       const int nks = a.ksteps;
       const uint64_t adesc0 = smem_desc(s.a0, 128, sbo_a), bdesc0 = smem_desc(s.b0, 128, sbo_b);
       const uint32_t a_step = s.a_stride >> 4, b_step = s.b_stride >> 4;
@@ -276,33 +285,37 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_res(ResArgs a) {
       bool ok = true;
       // test hook (qem_test_expire_wait): a wait on the teardown barrier, which
       // nothing completes before the teardown, runs out and aborts the CTA
-      if (a.expire_test) ok = mbar_spin(s.done, 0, lim, s.abort_flag);
+      if (a.expire_test) ok = mbar_spin_warp(s.done, 0, lim, s.abort_flag);
       for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x, ++i) {
         const uint32_t bph = (uint32_t)i & 1u;
         for (int rb = 0; rb < R && ok; ++rb) {
-          ok = mbar_spin(&s.a_full[as], aph, lim, s.abort_flag);
+          ok = mbar_spin_warp(&s.a_full[as], aph, lim, s.abort_flag);
           if (!ok) break;
           for (int c = 0; c < C; ++c) {
             const int nc = imin(kMaxN, K - c * kMaxN);
-            if (rb == 0) ok = mbar_spin(&s.b_full[c], bph, lim, s.abort_flag);
-            if (ok) ok = mbar_spin(&s.t_empty[ts], tph ^ 1u, lim, s.abort_flag);
+            if (rb == 0) ok = mbar_spin_warp(&s.b_full[c], bph, lim, s.abort_flag);
+            if (ok) ok = mbar_spin_warp(&s.t_empty[ts], tph ^ 1u, lim, s.abort_flag);
             if (!ok) break;
             tc_fence_after();
             const uint32_t idesc = idesc_fmt(nc, fmt);
             const uint32_t d_tmem = tmem + (uint32_t)(ts * kMaxN);
             const uint64_t ad = adesc0 + (uint64_t)(as * a_step), bd = bdesc0 + (uint64_t)(c * b_step);
+            if (elect_one()) {
 #pragma unroll
-            for (int ks = 0; ks < 16; ++ks)
-              if (ks < nks)  // k-step offsets read from the kernel parameters (constant bank)
-                mma_kind<TF32>(d_tmem, ad + (uint32_t)a.koff_row[ks], bd + (uint32_t)a.koff_col[ks], idesc,
-                               ks > 0 ? 1u : 0u);
-            mma_commit(&s.t_full[ts]);
-            if (rb == R - 1) mma_commit(&s.b_empty[c]);  // the element's last use of chunk c
+              for (int ks = 0; ks < 16; ++ks)
+                if (ks < nks)  // k-step offsets read from the kernel parameters (constant bank)
+                  mma_kind<TF32>(d_tmem, ad + (uint32_t)a.koff_row[ks], bd + (uint32_t)a.koff_col[ks], idesc,
+                                 ks > 0 ? 1u : 0u);
+              mma_commit(&s.t_full[ts]);
+              if (rb == R - 1) mma_commit(&s.b_empty[c]);  // the element's last use of chunk c
+            }
+            __syncwarp();
             ts ^= 1;
             if (ts == 0) tph ^= 1u;
           }
           if (!ok) break;
-          mma_commit(&s.a_empty[as]);
+          if (elect_one()) mma_commit(&s.a_empty[as]);
+          __syncwarp();
           if (++as == 2) {
             as = 0;
             aph ^= 1u;
@@ -310,78 +323,90 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_res(ResArgs a) {
         }
       }
       // every issued MMA has completed before the teardown (bounded, ignores abort)
-      mma_commit(s.done);
+      if (elect_one()) mma_commit(s.done);
+      __syncwarp();
       volatile int never = 0;
       mbar_wait(s.done, 0, drain_bound(lim), &never);
     }
     __syncwarp();
   } else if (warp >= kFwdEpiWarp0) {
-    // ------------------------------------------------------------ epilogue (16 warps)
-    // Warp w reads TMEM lanes 32 (w % 4) .. +31 (tcgen05.ld's lane-quarter
-    // rule) and a quarter of each tile's columns, all of them into registers
-    // before it hands the slot back, so the next tile's MMAs start while it
-    // exponentiates.  The four quarters of a row are merged through shared
-    // memory between two named barriers that every epilogue warp executes
-    // for every row block it enters, and the decision to stop is read from a
-    // flag written between them.
-    const int quarter = warp & 3;
-    const int part = (warp - kFwdEpiWarp0) >> 2;
+    // ------------------------------------------------------------ epilogue (two groups of 8 warps)
+    // The CTA's tiles form one sequence t over its elements, row blocks and
+    // column chunks (the MMA issuer's order); tile t is in TMEM slot t % 2
+    // and group g takes the tiles of slot g.  Warp (g, half, quarter) reads
+    // TMEM lanes 32 quarter .. +31 and columns half * nc / 2 .. +nc / 2 of
+    // the tile, 64 at a time, and hands the slot back after its last load.
+    // At the end of a row block every producing thread writes its partial
+    // (max, sum) to merge buffer n % 2 (n: the CTA's row-block count), and
+    // the half-0 warps of the group that took the block's last tile combine
+    // the partials into lt.  A group with no tile in the block (one column
+    // chunk: the groups alternate row blocks) skips it.
+    const int ew = warp - kFwdEpiWarp0;
+    const int g = ew >> 3, half = (ew >> 2) & 1, quarter = warp & 3;
     const int row = quarter * 32 + lane;
     const float lnK = logf((float)K);
-    int ts = 0;
-    uint32_t tph = 0;
-    bool stop = false;
-    for (long long e = blockIdx.x; e < a.n_elts && !stop; e += gridDim.x) {
+    const int j0 = C >= 2 ? 0 : 2 * g, j1 = C >= 2 ? 4 : 2 * g + 2;  // the producing (group, half) pairs
+    uint32_t tph = 0, n = 0;
+    int t0 = 0;  // the row block's first tile in the sequence
+    bool ok = true;
+    for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x) {
       const long long p = a.parent[e];
-      for (int rb = 0; rb < R; ++rb) {
-        float m = -INFINITY, sacc = 0.f;
-        bool ok = true;
+      for (int rb = 0; rb < R && ok; ++rb, ++n, t0 += C) {
+        const int first = t0 + ((g - t0) & 1);
+        if (first >= t0 + C) continue;
+        const bool fin = half == 0 && ((t0 + C - 1) & 1) == g;
         const long long k = (long long)rb * kRows + row;
-        // the row constant, read now so that its latency is spent under this row block's tiles
-        const float rc = part == 0 ? a.rowc[p * K + k] : 0.f;
-        for (int c = 0; c < C && ok; ++c) {
-          const int nc = imin(kMaxN, K - c * kMaxN);
-          ok = mbar_wait(&s.t_full[ts], tph, lim, s.abort_flag);
+        // the row constant, read now so that its latency is spent under the block's tiles
+        const float rc = fin ? a.rowc[p * K + k] : 0.f;
+        float m = -INFINITY, sacc = 0.f;
+        for (int t = first; t < t0 + C; t += 2) {
+          const int w = imin(kMaxN, K - (t - t0) * kMaxN) >> 1;  // 128, or 64 in a 128-column last chunk
+          ok = mbar_wait(&s.t_full[g], tph, lim, s.abort_flag);
           ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
           if (!ok) break;
           tc_fence_after();
-          const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ts * kMaxN + part * (nc >> 2));
-          if (nc == kMaxN) {
-            uint32_t va[32], vb[32];
-            tmem_ld32_issue(tbase, va);
-            tmem_ld32_issue(tbase + 32u, vb);
+          uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * kMaxN + half * w);
+          uint32_t va[32], vb[32];
+          if (w == 128) {
+            tmem_ld32_issue(tb, va);
+            tmem_ld32_issue(tb + 32u, vb);
             tmem_wait32(va);
             tmem_wait32(vb);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s.t_empty[ts]);
             lse_regs64(va, vb, m, sacc);
-          } else {  // a 128-column last chunk: 32 columns per warp
-            lse_group32(tbase, m, sacc);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s.t_empty[ts]);
+            tb += 64u;
           }
-          ts ^= 1;
-          if (ts == 0) tph ^= 1u;
+          tmem_ld32_issue(tb, va);
+          tmem_ld32_issue(tb + 32u, vb);
+          tmem_wait32(va);
+          tmem_wait32(vb);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&s.t_empty[g]);
+          tph ^= 1u;
+          lse_regs64(va, vb, m, sacc);
         }
-        s.merge[row * 4 + part] = make_float2(m, sacc);
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
-        if (threadIdx.x == 32 * kFwdEpiWarp0) *s.stop_flag = *s.abort_flag;
-        if (part == 0 && ok) {
+        if (!ok) break;
+        const uint32_t bsel = n & 1u, use = n >> 1;
+        float2* mb = s.merge + (size_t)bsel * kRows * 4;
+        // buffer bsel is free once row block n - 2 has been combined
+        if (use > 0) ok = mbar_wait(&s.m_free[bsel], (use - 1) & 1u, lim, s.abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        mb[row * 4 + 2 * g + half] = make_float2(m, sacc);
+        mbar_arrive(&s.m_full[bsel]);
+        if (fin) {
+          ok = mbar_wait(&s.m_full[bsel], use & 1u, lim, s.abort_flag);
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
           float M = -INFINITY;
-          for (int j = 0; j < 4; ++j) M = fmaxf(M, s.merge[row * 4 + j].x);
+          for (int j = j0; j < j1; ++j) M = fmaxf(M, mb[row * 4 + j].x);
           float S = 0.f;
-          for (int j = 0; j < 4; ++j) {
-            const float2 o = s.merge[row * 4 + j];
+          for (int j = j0; j < j1; ++j) {
+            const float2 o = mb[row * 4 + j];
             if (o.x != -INFINITY) S += o.y * ex2f(o.x - M);
           }
           a.lt[e * K + k] = rc + (M + log2f(S)) * kLn2 - lnK;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
-        if (*s.stop_flag) {
-          stop = true;
-          break;
+          mbar_arrive(&s.m_free[bsel]);
         }
       }
     }
@@ -481,20 +506,29 @@ __device__ __forceinline__ AdjSmem adj_carve(uint8_t* raw, int frow, int fcol, i
   return s;
 }
 
-// Sum of 2^(v + d) over 32 values already in registers, shifts d from
-// shared memory (the same addresses across the warp).
-__device__ __forceinline__ float adj_sum_f32(const float (&v)[32], const float* d) {
+// sum_j 2^(v_j + d_j) over one warp's 64 columns of a tile row, in two
+// passes: every value shifted and exponentiated in place, then summed, so
+// that no exponential waits on another's sum.
+__device__ __forceinline__ float adj_sum64(float (&va)[32], float (&vb)[32], const float* d) {
   const float4* d4 = reinterpret_cast<const float4*>(d);
-  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
   for (int j = 0; j < 32; j += 4) {
-    const float4 dv = d4[j >> 2];
-    float x0 = v[j], x1 = v[j + 1], x2 = v[j + 2], x3 = v[j + 3];
-    add2(x0, x1, dv.x, dv.y);
-    add2(x2, x3, dv.z, dv.w);
-    const float e0 = ex2f(x0), e1 = ex2f(x1), e2 = ex2f(x2), e3 = ex2f(x3);
-    add2(p0, p1, e0, e1);
-    add2(p2, p3, e2, e3);
+    const float4 da = d4[j >> 2], db = d4[8 + (j >> 2)];
+    add2(va[j], va[j + 1], da.x, da.y);
+    add2(va[j + 2], va[j + 3], da.z, da.w);
+    add2(vb[j], vb[j + 1], db.x, db.y);
+    add2(vb[j + 2], vb[j + 3], db.z, db.w);
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    va[j] = ex2f(va[j]);
+    vb[j] = ex2f(vb[j]);
+  }
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 32; j += 2) {
+    add2(p0, p1, va[j], va[j + 1]);
+    add2(p2, p3, vb[j], vb[j + 1]);
   }
   add2(p0, p1, p2, p3);
   return p0 + p1;
@@ -609,8 +643,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_adj_res(AdjResArgs a) {
       }
     }
   } else if (warp == kFwdMmaWarp) {
-    // ------------------------------------------------------------ MMA issuer (one thread)
-    if (lane == 0) {
+    // ------------------------------------------------------------ MMA issuer (one elected lane)
+    {
       const int nks = a.ksteps;
       const uint64_t adesc0 = smem_desc(s.a0, 128, sbo_a), bdesc0 = smem_desc(s.b0, 128, sbo_b);
       const uint32_t a_step = s.a_stride >> 4, b_step = s.b_stride >> 4;
@@ -621,7 +655,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_adj_res(AdjResArgs a) {
       bool ok = true;
       // test hook (qem_test_expire_wait): a wait on the teardown barrier, which
       // nothing completes before the teardown, runs out and aborts the CTA
-      if (a.expire_test) ok = mbar_spin(s.done, 0, lim, s.abort_flag);
+      if (a.expire_test) ok = mbar_spin_warp(s.done, 0, lim, s.abort_flag);
       long long g = 0;
       for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x) {
         const int n_eff = kept_of(e);
@@ -634,35 +668,40 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_adj_res(AdjResArgs a) {
             const uint32_t bph = (uint32_t)((g / NS) & 1);
             const int nc = imin(kMaxN, npad - c0);
             const bool last_chunk = c0 + kMaxN >= npad;
-            ok = mbar_spin(&s.b_full[st], bph, lim, s.abort_flag);
+            ok = mbar_spin_warp(&s.b_full[st], bph, lim, s.abort_flag);
             if (!ok) break;
             const uint32_t idesc = idesc_fmt(nc, fmt);
             const uint64_t bd = bdesc0 + (uint64_t)(st * b_step);
             for (int j = 0; j < nrb; ++j) {
-              if (c0 == 0) ok = mbar_spin(&s.a_full[j], (uses >> j) & 1u, lim, s.abort_flag);
-              if (ok) ok = mbar_spin(&s.t_empty[ts], tph ^ 1u, lim, s.abort_flag);
+              if (c0 == 0) ok = mbar_spin_warp(&s.a_full[j], (uses >> j) & 1u, lim, s.abort_flag);
+              if (ok) ok = mbar_spin_warp(&s.t_empty[ts], tph ^ 1u, lim, s.abort_flag);
               if (!ok) break;
               tc_fence_after();
               const uint32_t d_tmem = tmem + (uint32_t)(ts * kMaxN);
               const uint64_t ad = adesc0 + (uint64_t)(j * a_step);
+              if (elect_one()) {
 #pragma unroll
-              for (int ks = 0; ks < 16; ++ks)
-                if (ks < nks)
-                  mma_kind<TF32>(d_tmem, ad + (uint32_t)a.koff_row[ks], bd + (uint32_t)a.koff_col[ks], idesc,
-                                 ks > 0 ? 1u : 0u);
-              mma_commit(&s.t_full[ts]);
+                for (int ks = 0; ks < 16; ++ks)
+                  if (ks < nks)
+                    mma_kind<TF32>(d_tmem, ad + (uint32_t)a.koff_row[ks], bd + (uint32_t)a.koff_col[ks], idesc,
+                                   ks > 0 ? 1u : 0u);
+                mma_commit(&s.t_full[ts]);
+                if (last_chunk) mma_commit(&s.a_empty[j]);
+              }
+              __syncwarp();
               ts ^= 1;
               if (ts == 0) tph ^= 1u;
-              if (last_chunk) {
-                mma_commit(&s.a_empty[j]);
-                uses ^= 1u << j;
-              }
+              if (last_chunk) uses ^= 1u << j;
             }
-            if (ok) mma_commit(&s.b_empty[st]);
+            if (ok) {
+              if (elect_one()) mma_commit(&s.b_empty[st]);
+              __syncwarp();
+            }
           }
         }
       }
-      mma_commit(s.done);
+      if (elect_one()) mma_commit(s.done);
+      __syncwarp();
       volatile int never = 0;
       mbar_wait(s.done, 0, drain_bound(lim), &never);
     }
@@ -714,7 +753,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_adj_res(AdjResArgs a) {
               tc_fence_before();
               __syncwarp();
               if (lane == 0) mbar_arrive(&s.t_empty[ts]);
-              acc[j] += adj_sum_f32(va, dsm) + adj_sum_f32(vb, dsm + 32);
+              acc[j] += adj_sum64(va, vb, dsm);
             } else {
               float sum = 0.f;
               for (int c = 0; c < ncp; c += 16) {
