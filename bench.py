@@ -277,12 +277,12 @@ NCU_TRAFFIC = {
     # of this workload: their traffic is per element (the element's rows
     # once, its output row written once; the parent's rows stay in L2)
     ("forward", "hier_logistic_M5000_N10_K1024", "bf16x3"): {
-        "bytes": 5 * (164132864 + 5216512), "source": "paper_2503_08264_gb300/csrc/qem_tc_res.cu",
-        "blob": "094144963c8e839857c3dbd9c6f37c9d9fc1db7f",
+        "bytes": 5 * (164162304 + 4952064), "source": "paper_2503_08264_gb300/csrc/qem_tc_res.cu",
+        "blob": "43d2408ea249832ce023fd0f37d3de37c1c2b225",
         "profile": "profiles/fwd_res_bf16x3_hier_logistic_M1000_K1024.md"},
     ("adjoint", "hier_logistic_M5000_N10_K1024", "bf16x3"): {
-        "bytes": 5 * (167698432 + 5387776), "source": "paper_2503_08264_gb300/csrc/qem_tc_res.cu",
-        "blob": "094144963c8e839857c3dbd9c6f37c9d9fc1db7f",
+        "bytes": 5 * (167880704 + 5359104), "source": "paper_2503_08264_gb300/csrc/qem_tc_res.cu",
+        "blob": "43d2408ea249832ce023fd0f37d3de37c1c2b225",
         "profile": "profiles/adj_res_bf16x3_hier_logistic_M1000_K1024.md"},
 }
 

@@ -24,20 +24,17 @@
 // Tiles are 128 x 256 (the MMA's full rate; a narrower N is bound by the MMA
 // issue rate) in two TMEM slots of 256 columns.  Roles (640 threads, one CTA
 // per SM): warp 0 loads the row side, warp 1 the column side (and the
-// adjoint's column shifts), warp 2 issues the MMAs (one thread) and owns
+// adjoint's column shifts), warp 2 issues the MMAs (one lane) and owns
 // TMEM, warp 3 is idle, warps 4..19 are the epilogue; warp w reads TMEM lanes
 // 32 (w % 4) .. +31 (the rule of tcgen05.ld).
-//  * forward: the epilogue is two groups of eight warps that take alternate
-//    tiles (group g every tile of TMEM slot g), each warp half of a tile's
-//    columns in two pieces of 64; while one group waits for its tile, loads
-//    it or merges a row block, the other exponentiates, so the ex2 unit is
-//    not left idle between tiles.  A row block's partial sums meet in shared
-//    memory, completed by the group that took its last tile, without a
-//    CTA-wide barrier.
-//  * adjoint: each warp takes a quarter of every tile's columns, all 64 of
-//    its values into registers before it hands the slot back, so the next
-//    tile's MMAs run while it exponentiates; the four quarters of a row are
-//    merged through shared memory once per pass.
+// The epilogue is two groups of eight warps that take alternate tiles
+// (group g every tile of TMEM slot g), each warp half of a tile's columns in
+// two pieces of 64; while one group waits for its tile, loads it or merges,
+// the other exponentiates, so the ex2 unit is not left idle between tiles.
+// Partial sums meet in shared memory (per row block in the forward, per pass
+// of four row blocks in the adjoint), completed by the group that took the
+// last tile, without a CTA-wide barrier.  The MMA warp runs converged and one
+// elected lane issues.
 //
 // Every wait is bounded; an expired wait sets the CTA's abort flag, every
 // role stops at its next wait, the producers wait (bounded, ignoring the
@@ -455,7 +452,7 @@ struct AdjSmem {
   uint8_t* a0;       // kAdjPassRows row blocks, a_stride apart
   uint8_t* b0;       // nst column chunks of 256 rows, b_stride apart
   float* d0;         // nst column-shift rows of 256 floats
-  float* merge;      // [kAdjPassRows][kRows][4] partial row sums of a pass
+  float* merge;      // [2][kAdjPassRows][kRows][4] partial row sums of a pass, per (group, half)
   uint32_t a_stride, b_stride;
   uint64_t* a_full;   // [kAdjPassRows]
   uint64_t* a_empty;  // [kAdjPassRows]
@@ -466,14 +463,15 @@ struct AdjSmem {
   uint64_t* t_full;   // [2]
   uint64_t* t_empty;  // [2]
   uint64_t* done;
+  uint64_t* m_full;   // [2] a pass's partials written (one arrival per epilogue thread)
+  uint64_t* m_free;   // [2] a pass's partials read (one arrival per completing thread)
   uint32_t* tmem_base;
   volatile int* abort_flag;
-  volatile int* stop_flag;
 };
 
 __host__ __device__ inline size_t adj_res_smem_bytes(int frow, int fcol, int nst) {
   return 1024 + (size_t)kAdjPassRows * kRows * frow * 2 + (size_t)nst * kMaxN * fcol * 2 + (size_t)nst * kMaxN * 4 +
-         (size_t)kAdjPassRows * kRows * 4 * 4 + 32 * 8 + 16;
+         2 * (size_t)kAdjPassRows * kRows * 4 * 4 + 40 * 8 + 16;
 }
 
 __device__ __forceinline__ AdjSmem adj_carve(uint8_t* raw, int frow, int fcol, int nst) {
@@ -488,7 +486,7 @@ __device__ __forceinline__ AdjSmem adj_carve(uint8_t* raw, int frow, int fcol, i
   s.d0 = reinterpret_cast<float*>(p);
   p += (size_t)nst * kMaxN * 4;
   s.merge = reinterpret_cast<float*>(p);
-  p += (size_t)kAdjPassRows * kRows * 4 * 4;
+  p += 2 * (size_t)kAdjPassRows * kRows * 4 * 4;
   uint64_t* bars = reinterpret_cast<uint64_t*>(p);
   s.a_full = bars;
   s.a_empty = bars + kAdjPassRows;
@@ -499,10 +497,11 @@ __device__ __forceinline__ AdjSmem adj_carve(uint8_t* raw, int frow, int fcol, i
   s.t_full = s.d_empty + 4;
   s.t_empty = s.t_full + 2;
   s.done = s.t_empty + 2;
-  p += 32 * 8;
+  s.m_full = s.done + 1;
+  s.m_free = s.m_full + 2;
+  p += 40 * 8;
   s.tmem_base = reinterpret_cast<uint32_t*>(p);
   s.abort_flag = reinterpret_cast<volatile int*>(p + 4);
-  s.stop_flag = reinterpret_cast<volatile int*>(p + 8);
   return s;
 }
 
@@ -555,15 +554,16 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_adj_res(AdjResArgs a) {
       mbar_init(&s.b_full[i], 1);
       mbar_init(&s.b_empty[i], 1);
       mbar_init(&s.d_full[i], 1);
-      mbar_init(&s.d_empty[i], kEpiWarps);
+      mbar_init(&s.d_empty[i], kEpiWarps);  // every epilogue warp, with or without tiles on the chunk
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&s.t_full[i], 1);
-      mbar_init(&s.t_empty[i], kEpiWarps);
+      mbar_init(&s.t_empty[i], kFwdGroupWarps);
+      mbar_init(&s.m_full[i], 32 * kEpiWarps);
+      mbar_init(&s.m_free[i], kRows);
     }
     mbar_init(s.done, 1);
     *s.abort_flag = 0;
-    *s.stop_flag = 0;
     fence_barrier_init();
   }
   if (warp == kFwdMmaWarp) {
@@ -707,83 +707,108 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_adj_res(AdjResArgs a) {
     }
     __syncwarp();
   } else if (warp >= kFwdEpiWarp0) {
-    // ------------------------------------------------------------ epilogue (16 warps)
-    // Warp w takes TMEM lanes 32 (w % 4) .. +31 and column quarter `part` of
-    // every tile (loaded into registers before the slot is handed back) and
-    // keeps one partial sum per row block of the pass; at the pass's end the
-    // four quarters of every row are added through shared memory between two
-    // named barriers that every epilogue warp executes, and the decision to
-    // stop is read from a flag written between them.
-    const int quarter = warp & 3;
-    const int part = (warp - kFwdEpiWarp0) >> 2;
+    // ------------------------------------------------------------ epilogue (two groups of 8 warps)
+    // The CTA's tiles form one sequence T over its elements, passes, chunks
+    // and row blocks (the MMA issuer's order); tile T is in TMEM slot T % 2
+    // and group g takes the tiles of slot g.  Warp (g, half, quarter) reads
+    // TMEM lanes 32 quarter .. +31 and its half of each tile's columns (in
+    // 16-column groups, the first half taking the odd one; 128 columns as two
+    // pieces of 64 for a full chunk) and keeps one partial sum per row block
+    // of the pass.  Every warp waits for every chunk's column shifts and
+    // releases them after its tiles of the chunk, also where it has none, so
+    // that neither group gets a stage ahead of the other.  At the end of a
+    // pass every thread writes its partials to merge buffer np % 2 (np: the
+    // CTA's pass count), and the half-0 warps of the group with the pass's
+    // last tile add the four partials of every row.
+    const int ew = warp - kFwdEpiWarp0;
+    const int g = ew >> 3, half = (ew >> 2) & 1, quarter = warp & 3;
     const int row = quarter * 32 + lane;
-    int ts = 0;
-    uint32_t tph = 0;
-    long long g = 0;
-    bool stop = false;
-    for (long long e = blockIdx.x; e < a.n_elts && !stop; e += gridDim.x) {
+    uint32_t tph = 0, np = 0;
+    int T = 0;
+    long long gc = 0;
+    bool ok = true;
+    for (long long e = blockIdx.x; e < a.n_elts && ok; e += gridDim.x) {
       const int n_eff = kept_of(e);
       if (n_eff <= a.small) continue;
       const int npad = imin(K, (n_eff + 15) & ~15);
-      for (int h = 0; h < passes && !stop; ++h) {
+      const int nch = (npad + kMaxN - 1) / kMaxN;
+      for (int h = 0; h < passes && ok; ++h, ++np) {
         const int nrb = imin(kAdjPassRows, R - h * kAdjPassRows);
+        const bool fin = half == 0 && ((T + nch * nrb - 1) & 1) == g;
         float acc[kAdjPassRows] = {0.f, 0.f, 0.f, 0.f};
-        bool ok = true;
-        for (int c0 = 0; c0 < npad && ok; c0 += kMaxN, ++g) {
-          const int st = (int)(g % NS);
-          const uint32_t dph = (uint32_t)((g / NS) & 1);
-          const int nc = imin(kMaxN, npad - c0);
-          const int ncp = imin(64, nc - part * 64);  // this warp's columns of the chunk (a multiple of 16; <= 0: none)
+        for (int c0 = 0; c0 < npad && ok; c0 += kMaxN, ++gc) {
+          const int st = (int)(gc % NS);
+          const uint32_t dph = (uint32_t)((gc / NS) & 1);
+          const int n16 = imin(kMaxN, npad - c0) >> 4;
+          const int cbase = half ? ((n16 + 1) >> 1) << 4 : 0;  // this warp's columns of the chunk
+          const int ncw = (half ? n16 >> 1 : (n16 + 1) >> 1) << 4;
           ok = mbar_wait(&s.d_full[st], dph, lim, s.abort_flag);
-          const float* dsm = s.d0 + st * kMaxN + part * 64;
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
+          const float* dsm = s.d0 + st * kMaxN + cbase;
 #pragma unroll
           for (int j = 0; j < kAdjPassRows; ++j) {
-            if (j >= nrb || !ok) break;
-            ok = mbar_wait(&s.t_full[ts], tph, lim, s.abort_flag);
+            if (j >= nrb) break;
+            if (((T + j) & 1) != g) continue;
+            ok = mbar_wait(&s.t_full[g], tph, lim, s.abort_flag);
             ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
             if (!ok) break;
             tc_fence_after();
-            const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ts * kMaxN + part * 64);
-            if (ncp == 64) {
+            const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * kMaxN + cbase);
+            float sum = 0.f;
+            if (ncw == 128) {
               // each load completes inside its own asm block (this kernel spills a
               // few registers; no spill may fall between a load and its wait)
               float va[32], vb[32];
               tmem_ld32(tb, va);
               tmem_ld32(tb + 32u, vb);
+              sum = adj_sum64(va, vb, dsm);
+              tmem_ld32(tb + 64u, va);
+              tmem_ld32(tb + 96u, vb);
               tc_fence_before();
               __syncwarp();
-              if (lane == 0) mbar_arrive(&s.t_empty[ts]);
-              acc[j] += adj_sum64(va, vb, dsm);
+              if (lane == 0) mbar_arrive(&s.t_empty[g]);
+              sum += adj_sum64(va, vb, dsm + 64);
             } else {
-              float sum = 0.f;
-              for (int c = 0; c < ncp; c += 16) {
+              for (int c = 0; c < ncw; c += 16) {
                 float v[16];
                 tmem_ld16(tb + (uint32_t)c, v);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) sum += ex2f(v[q] + dsm[c + q]);
+                for (int q = 0; q < 16; ++q) v[q] = ex2f(v[q] + dsm[c + q]);
+#pragma unroll
+                for (int q = 0; q < 16; q += 4) sum += (v[q] + v[q + 1]) + (v[q + 2] + v[q + 3]);
               }
-              acc[j] += sum;
               tc_fence_before();
               __syncwarp();
-              if (lane == 0) mbar_arrive(&s.t_empty[ts]);
+              if (lane == 0) mbar_arrive(&s.t_empty[g]);
             }
-            ts ^= 1;
-            if (ts == 0) tph ^= 1u;
+            acc[j] += sum;
+            tph ^= 1u;
           }
+          T += nrb;
           __syncwarp();
           if (lane == 0 && ok) mbar_arrive(&s.d_empty[st]);
         }
-        // add the four column quarters of every row of the pass's row blocks
+        if (!ok) break;
+        const uint32_t bsel = np & 1u, use = np >> 1;
+        float* mb = s.merge + (size_t)bsel * kAdjPassRows * kRows * 4;
+        // buffer bsel is free once pass np - 2 has been added up
+        if (use > 0) ok = mbar_wait(&s.m_free[bsel], (use - 1) & 1u, lim, s.abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
 #pragma unroll
-        for (int j = 0; j < kAdjPassRows; ++j) s.merge[(j * kRows + row) * 4 + part] = acc[j];
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
-        if (threadIdx.x == 32 * kFwdEpiWarp0) *s.stop_flag = *s.abort_flag;
-        if (ok && part < nrb) {  // warp part p writes row block p of the pass
-          const float* mr = s.merge + (part * kRows + row) * 4;
-          a.w_out[e * K + (long long)(h * kAdjPassRows + part) * kRows + row] = (mr[0] + mr[1]) + (mr[2] + mr[3]);
+        for (int j = 0; j < kAdjPassRows; ++j) mb[(j * kRows + row) * 4 + 2 * g + half] = acc[j];
+        mbar_arrive(&s.m_full[bsel]);
+        if (fin) {
+          ok = mbar_wait(&s.m_full[bsel], use & 1u, lim, s.abort_flag);
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
+          for (int j = 0; j < nrb; ++j) {
+            const float* mr = mb + (j * kRows + row) * 4;
+            a.w_out[e * K + (long long)(h * kAdjPassRows + j) * kRows + row] = (mr[0] + mr[1]) + (mr[2] + mr[3]);
+          }
+          mbar_arrive(&s.m_free[bsel]);
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
-        if (*s.stop_flag) stop = true;
       }
     }
   }
