@@ -695,8 +695,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       }
     }
   } else if (warp == kMmaWarp) {
-    // ------------------------------------------------------------ MMA issuer (one thread)
-    if (lane == 0) {
+    // ------------------------------------------------------------ MMA issuer (one elected lane)
+    // The whole warp runs the loop (its waits are warp votes, so control flow
+    // and descriptors stay warp-uniform); one elected lane issues.
+    {
       int as = NA - 1, bs = 0, ts = 0;   // as: slot of the current row block (advanced on each new block)
       uint32_t aph = 1, bph = 0, tph = 0;
       // Descriptors are built once: a k-step at column c of a slot adds c to
@@ -716,37 +718,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       bool ok = true;
       // test hook (qem_test_expire_wait): a wait on the teardown barrier, which
       // nothing completes before the teardown, runs out and aborts the CTA
-      if (a.expire_test) ok = mbar_spin(s.done, 0, lim, s.abort_flag);
+      if (a.expire_test) ok = mbar_spin_warp(s.done, 0, lim, s.abort_flag);
       Walker<ADJ> wk(a);
       Unit x;
       while (ok && wk.next(x)) {
         const long long row_key = (ADJ ? x.e : x.p) * a.units_per_elt + x.rb;
         if (row_key != prev_row) {
-          if (prev_row >= 0) mma_commit(&s.a_empty[as]);  // the previous block's last MMA has been issued
+          if (prev_row >= 0) {  // the previous block's last MMA has been issued
+            if (elect_one()) mma_commit(&s.a_empty[as]);
+            __syncwarp();
+          }
           if (++as == NA) {
             as = 0;
             aph ^= 1;
           }
-          ok = mbar_spin(&s.a_full[as], aph, lim, s.abort_flag);
+          ok = mbar_spin_warp(&s.a_full[as], aph, lim, s.abort_flag);
           if (!ok) break;
           prev_row = row_key;
         }
         for (int c0 = 0; c0 < x.ncols; c0 += kNB) {
           const int nc = min(kNB, x.ncols - c0);
-          ok = mbar_spin(&s.b_full[bs], bph, lim, s.abort_flag) && mbar_spin(&s.t_empty[ts], tph ^ 1, lim, s.abort_flag);
+          ok = mbar_spin_warp(&s.b_full[bs], bph, lim, s.abort_flag) &&
+               mbar_spin_warp(&s.t_empty[ts], tph ^ 1, lim, s.abort_flag);
           if (!ok) break;
           tc_fence_after();
           const uint32_t idesc = idesc_fmt(nc, TF32 ? 2u : 1u);
           const uint64_t bd = bdesc0 + (uint64_t)(bs * b_step);
-          for (int r = 0; r < RT; ++r) {
-            const uint32_t d_tmem = tmem + (uint32_t)(ts * 256 + r * kNB);
-            const uint64_t ad = adesc0 + (uint64_t)(as * a_step + r * t_step);
+          if (elect_one()) {
+            for (int r = 0; r < RT; ++r) {
+              const uint32_t d_tmem = tmem + (uint32_t)(ts * 256 + r * kNB);
+              const uint64_t ad = adesc0 + (uint64_t)(as * a_step + r * t_step);
 #pragma unroll
-            for (int ks = 0; ks < 16; ++ks)
-              if (ks < nks) mma_kind<TF32>(d_tmem, ad + kro[ks], bd + kco[ks], idesc, ks > 0 ? 1u : 0u);
+              for (int ks = 0; ks < 16; ++ks)
+                if (ks < nks) mma_kind<TF32>(d_tmem, ad + kro[ks], bd + kco[ks], idesc, ks > 0 ? 1u : 0u);
+            }
+            mma_commit(&s.b_empty[bs]);
+            mma_commit(&s.t_full[ts]);
           }
-          mma_commit(&s.b_empty[bs]);
-          mma_commit(&s.t_full[ts]);
+          __syncwarp();
           if (++bs == NS) {
             bs = 0;
             bph ^= 1;
@@ -757,7 +766,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract(ContractArgs a) {
       }
       // every issued MMA has completed before the teardown, also after an
       // abort (the wait ignores the abort flag; it is still bounded)
-      mma_commit(s.done);
+      if (elect_one()) mma_commit(s.done);
+      __syncwarp();
       volatile int never = 0;
       mbar_wait(s.done, 0, drain_bound(lim), &never);
     }
