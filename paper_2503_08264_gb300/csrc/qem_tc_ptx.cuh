@@ -367,45 +367,5 @@ __device__ __forceinline__ void lse_group32(uint32_t taddr, float& m, float& sac
   sacc += pt;
 }
 
-// lse_group32 on 32 values already in registers (taddr: their TMEM address,
-// re-read only by the overflow path).
-__device__ __forceinline__ void lse_regs32(const uint32_t (&r)[32], uint32_t taddr, float& m, float& sacc) {
-  float v[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-  if (m == -INFINITY) {
-    float mx = v[0];
-#pragma unroll
-    for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
-    m = mx;
-  }
-#pragma unroll
-  for (int j = 0; j < 32; j += 2) sub2(v[j], v[j + 1], m);
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = ex2f(v[j]);
-#pragma unroll
-  for (int w = 16; w >= 2; w >>= 1)
-#pragma unroll
-    for (int j = 0; j < w; j += 2) add2(v[j], v[j + 1], v[j + w], v[j + w + 1]);
-  float pt = v[0] + v[1];
-  const bool redo = !(pt <= 4294967296.0f);
-  if (__any_sync(0xffffffffu, redo)) {
-    tmem_ld32(taddr, v);
-    if (redo) {
-      float mx = v[0];
-#pragma unroll
-      for (int j = 1; j < 32; ++j) mx = fmaxf(mx, v[j]);
-      if (mx > m) {
-        sacc *= ex2f(m - mx);
-        m = mx;
-      }
-      pt = 0.f;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) pt += ex2f(v[j] - m);
-    }
-  }
-  sacc += pt;
-}
-
 }  // namespace tc
 }  // namespace qem
