@@ -150,12 +150,15 @@ def test_schedules_agree(precision, M, K):
     assert max(moment_errors(model, plan_q, split_r, split_s)) < 1e-5
 
 
-@pytest.mark.parametrize("K", [512, 1024])
+@pytest.mark.parametrize("K", [384, 512, 640, 1024])
 def test_resident_adjoint_dense_root_weights(K):
     """Flat root weights (the root's proposal equal to its prior, few users):
     the root keeps most of its K samples, so every element's resident adjoint
     (tc_sched 3) runs over full chunks of 256 and a ragged last one; against
-    the oracle at the mixed-precision tolerance."""
+    the oracle at the mixed-precision tolerance.  K = 384 (three row blocks
+    in a pass) and 640 (passes of four and one) give odd row-block counts,
+    where a row block's tiles alternate between the two epilogue groups from
+    chunk to chunk."""
     model = S.hier_logistic(M=3, N=2, seed=65)
     q = S.random_q(model, seed=66, loc_scale=0.1, sd_lo=0.9, sd_hi=1.1)
     q[0][:, 0, :] = 0.0
