@@ -78,3 +78,23 @@ def test_traffic_gate_follows_the_source_hash():
     same = bench.git_blob_hash(e["source"]) == e["blob"]
     assert (bench.ncu_traffic("forward", "hier_logistic_M5000_N10_K1024", "bf16x3") is not None) == same
     assert bench.ncu_traffic("forward", "hier_logistic_M300_N5_K128", "fp32") is None
+
+
+def test_profile_summaries_name_committed_commands():
+    """Every summary under profiles/ gives the command that made it, through
+    committed files (bench.py or a committed probe), never scratch paths, and
+    every traffic figure the bench reports names an existing summary."""
+    prof = os.path.join(ROOT, "profiles")
+    names = sorted(f for f in os.listdir(prof) if f.endswith((".md", ".txt")))
+    assert names
+    for f in names:
+        text = open(os.path.join(prof, f)).read()
+        assert "bench.py" in text, f
+        assert "_work" not in text and "/root/" not in text, f
+        # commands continue over lines ending in a backslash
+        for cmd in text.replace("\\\n", " ").splitlines():
+            if cmd.lstrip().startswith("ncu "):
+                assert "--clock-control none" in cmd, (f, cmd)
+    for e in bench.NCU_TRAFFIC.values():
+        assert os.path.exists(os.path.join(ROOT, e["profile"])), e["profile"]
+        assert os.path.exists(os.path.join(ROOT, e["source"])), e["source"]
